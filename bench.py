@@ -1,0 +1,296 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 DG solver on the 2D flow-over-orography workload.
+
+Workload (one "step" = one IMEX-RK2 time step, i.e. one pass of the whole hot
+path: explicit DG applies, the pressure Picard loop with GMRES on the
+Helmholtz operator, gradients/divergences, the stage updates):
+  hill2d -- 64x32 base quads over 40 km x 20 km, Gaussian hill (seeded), two
+  2:1 refinement levels near the ground (2912 cells), degree 4, FP64,
+  constant-N atmosphere with a 10 m/s inflow, 291,200 DoF.
+
+Metric: DoF-steps per second (DoF x steps / s), whole job over all ranks.
+Under torchrun each rank runs an independent replica (the workload is a
+single mesh that this build does not partition), so scaling is weak.
+
+``--impl reference`` times the CPU oracle (the plain FP64 restatement of the
+method) on the same workload, on the host cores.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# per-node algorithmic counts (collocated GLL, sum factorised; see the design notes)
+#   explicit apply: bytes/DoF = s (2 + 1/V); flops/node = 2Vdn + 2Vd^2 + P_vol + (d/n) P_face + V
+#   Helmholtz apply: bytes/node = 3 s;       flops/node = 2 (2dn + 2d^2) + 10
+P_VOL = {2: 25, 3: 45}
+P_FACE = {2: 70, 3: 90}
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz (nominal 1.25 TF)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def algorithmic(dim, degree, n_nodes, kind, s=8):
+    n = degree + 1
+    V = dim + 2
+    if kind == "explicit":
+        flops = 2 * V * dim * n + 2 * V * dim * dim + P_VOL[dim] + (dim / n) * P_FACE[dim] + V
+        byts = s * (2 * V + 1)
+    else:
+        flops = 2 * (2 * dim * n + 2 * dim * dim) + 10
+        byts = 3 * s
+    return flops * n_nodes, byts * n_nodes
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, device):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(device)]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline_sample(case_name, seconds):
+    """Time the CPU oracle on a bounded number of steps in a single-threaded subprocess."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+from workloads import make_case
+from oracle.dg import DG
+from oracle.imex import Stepper
+case = make_case(%r, 0)
+dg = DG(case)
+st = Stepper(dg, tol=1e-12)
+U = dg.state()
+n = 0
+t0 = time.perf_counter()
+while True:
+    U = st.step(U, case.dt)
+    n += 1
+    if time.perf_counter() - t0 > %f:
+        break
+el = time.perf_counter() - t0
+print(json.dumps({"steps": n, "seconds": el, "dof": case.n_dof}))
+""" % (ROOT, case_name, seconds)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["dof"] * d["steps"] / d["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": "%d IMEX-RK2 step(s) of %s on 1 host thread (%.1f s)" % (d["steps"], case_name, d["seconds"])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(3.0, 60.0 / max(1, args.steps + args.warmup))
+    cb = cpu_baseline_sample(args.workload, per_step * max(1, args.steps))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "DoF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": CONFIG[args.workload],
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+METRIC = "DG apply DoF/s fp64 vs fp32, %HBM peak; ensemble steps/s, p50/p99 latency"
+CONFIG = {
+    "hill2d": {
+        "workload": "hill2d: 2D x-z flow over a seeded Gaussian hill, 64x32 base quads over 40x20 km, "
+                    "two 2:1 refinement levels near the ground (2912 cells), degree 4, FP64, "
+                    "constant-N atmosphere + 10 m/s inflow; IMEX-RK2 steps (GMRES tol 1e-12, 3 Picard)",
+        "dof": 291200,
+        "l2": "flushed between timed steps (256 MB write)",
+    },
+    "bubble2d": {
+        "workload": "bubble2d: 16x8 conforming quads, degree 2, FP64 warm bubble; IMEX-RK2 steps",
+        "dof": 4608,
+        "l2": "flushed between timed steps (256 MB write)",
+    },
+}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hill2d", choices=sorted(CONFIG))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2408_08129_gb300 as dg
+    from workloads import make_case
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    case = make_case(args.workload, 0)
+    ctx = dg.Context(local)
+    mesh = dg.Mesh(ctx, case)
+    opts = dg.solver_opts(tol=1e-12, picard=3, restart=30)
+    state = dg.State(ctx, mesh, opts)
+    init = case.init
+    if init["kind"] == "bubble":
+        dg.dg_init_state(ctx, mesh, "bubble", [init["amp"], init["radius"], init["xc"], init["zc"]], state.U)
+    else:
+        dg.dg_init_state(ctx, mesh, "inflow", [init.get("u0", 10.0)], state.U)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        dg.imex_rk2_step(ctx, mesh, state, case.dt, opts)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    dg.dg_profile_reset(ctx)
+    dg.dg_profile_enable(ctx, True)
+    launches0 = dg.dg_launch_count(ctx)
+    times = []
+    stats = []
+    clk = Clocks(os.path.join(tempfile.gettempdir(), "dg_bench_clocks_%d.csv" % rank))
+    with clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            stats.append(dg.imex_rk2_step(ctx, mesh, state, case.dt, opts))
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+    launches = dg.dg_launch_count(ctx) - launches0
+    prof = dg.dg_profile_read(ctx)
+    dg.dg_profile_enable(ctx, False)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    dof = mesh.n_dof
+    value = world * dof * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: upload, step, download per step
+    host = torch.empty(mesh.shape(), dtype=torch.float64, pin_memory=True).numpy()
+    host[:] = state.download()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        state.upload(host)
+        dg.imex_rk2_step(ctx, mesh, state, case.dt, opts)
+        host[:] = state.download()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * dof * args.steps / e2e_s, "unit": "DoF/s",
+           "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes)}
+
+    # roofline of the dominant operator class inside the timed region
+    cats = {k: v for k, v in prof.items() if k in ("explicit", "helmholtz", "grad", "div", "krylov") and v["count"]}
+    dom = max(cats, key=lambda k: cats[k]["ms"])
+    avg_ms = cats[dom]["ms"] / cats[dom]["count"]
+    hbm, peak_src = measured_peaks()
+    kind = "explicit" if dom == "explicit" else "helmholtz"
+    flops, byts = algorithmic(case.dim, case.degree, mesh.n_nodes, kind)
+    if dom in ("explicit", "helmholtz"):
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": "%s apply (%s)" % (dom, "face + cell kernels"), "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "derived FP64 rate: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "traffic": None, "avg_launch_us": avg_ms * 1e3,
+                "hbm_achieved_gbs": byts / (avg_ms / 1e3) / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_source": peak_src}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None, "avg_launch_us": avg_ms * 1e3}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(CONFIG[args.workload], replicas=world, precision="fp64"),
+        "roofline": roof,
+        "breakdown_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+        "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in stats),
+        "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(local),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(args.workload, 12.0)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * dg_atmo.h -- C ABI of a GB300 (sm_103a) matrix-free DG solver for the
+ * compressible Euler equations on 2:1 non-conforming terrain-following meshes,
+ * advanced in time by a second-order IMEX Runge-Kutta scheme.
+ *
+ * Method (arXiv 2408.08129):
+ *   Eq. (1), Sec. 2  compressible Euler with gravity, ideal gas, g = 9.81, R = 287;
+ *   Sec. 2           DG on non-conforming meshes (no hanging nodes), IMEX-RK2 with
+ *                    continuity explicit and momentum/energy coupled implicitly;
+ *   Sec. 3.1         orography, constant-N background atmosphere, wall bottom;
+ *   Sec. 3.2         matrix-free operator action; pressure fixed-point loop with
+ *                    GMRES for the non-symmetric linear system.
+ * Discretisation details the paper leaves to earlier work are readings:
+ * collocated Gauss-Lobatto-Legendre nodal basis, Rusanov flux (advective
+ * speed only for the IMEX-explicit terms), subface evaluation on 2:1 faces,
+ * strong-form gradient / weak-form divergence with centred traces for the
+ * pressure Helmholtz problem, ARK2(2,3,2) tableau.
+ *
+ * Conventions shared by every call:
+ *  - Return value: a dg_status (0 = DG_OK, negative = error).  No call throws,
+ *    aborts or exits.  dg_last_error() gives a message for the calling thread.
+ *  - Device arrays are caller-owned CUDA device pointers (for example the
+ *    data_ptr() of a contiguous torch tensor), aligned to 16 bytes, laid out
+ *    structure-of-arrays: variable-major, then cell, then node inside the cell
+ *    ([var][cell][node]); a node's index inside its cell is
+ *    i0 + n*i1 (+ n*n*i2), n = degree+1, axis 0 = x, the last axis vertical.
+ *    Variables: rho, momentum components (vertical last), rho*E.
+ *  - Host arrays are plain host pointers, only read during the call.
+ *  - Every device call is enqueued on the given CUDA stream (NULL = legacy
+ *    default stream) and returns without waiting, unless documented.  Calls on
+ *    one mesh share that mesh's scratch buffers, so they must be ordered on one
+ *    stream (or otherwise serialised by the caller).
+ *  - Precision: DG_FP64 arrays are double; DG_FP32 arrays are float and hold
+ *    the PERTURBATION about the hydrostatic background for state inputs
+ *    (rho - rho_bar, momentum, rho*E - p_bar/(gamma-1)); the FP64 background is
+ *    added inside the kernels.
+ */
+#ifndef DG_ATMO_H
+#define DG_ATMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;
+typedef struct dg_mesh dg_mesh;
+typedef struct dg_state dg_state;
+
+typedef enum {
+  DG_OK = 0,
+  DG_EINVAL = -1,      /* bad argument                                       */
+  DG_ENOMEM = -2,      /* device or host allocation failed                   */
+  DG_ECUDA = -3,       /* a CUDA runtime call failed (message has the code)  */
+  DG_ENOTCONV = -4,    /* Krylov / fixed-point loop did not converge         */
+  DG_ENONFINITE = -5,  /* NaN or Inf detected in a result                    */
+  DG_EUNBALANCED = -6, /* mesh is not 2:1 balanced or not watertight         */
+  DG_EBUDGET = -7,     /* request exceeds the serving memory budget          */
+  DG_ETIMEOUT = -8     /* a bounded wait ran out                             */
+} dg_status;
+
+typedef enum { DG_FP64 = 0, DG_FP32 = 1 } dg_precision;
+typedef enum { DG_TERMS_FULL = 0, DG_TERMS_IMEX_EXPLICIT = 1 } dg_terms;
+typedef enum { DG_HILL_NONE = 0, DG_HILL_GAUSS = 1, DG_HILL_BELL = 2, DG_HILL_PARABOLA = 3 } dg_hill_kind;
+typedef enum { DG_ATM_NONE = 0, DG_ATM_ISOTHERMAL = 1, DG_ATM_STRATIFIED = 2 } dg_atm_kind;
+typedef enum { DG_INIT_REST = 0, DG_INIT_BUBBLE = 1, DG_INIT_INFLOW = 2 } dg_init_kind;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+int dg_ctx_create(int device, dg_ctx** out);
+int dg_ctx_destroy(dg_ctx* ctx);
+/* Message of the last non-OK status returned on the calling thread ("" if none). */
+const char* dg_last_error(void);
+/* Library version string. */
+const char* dg_version(void);
+
+/* Optional timing of the operator classes with CUDA events (the per-block
+ * time breakdown of Sec. 3.2, Fig. 5).  Categories: */
+typedef enum {
+  DG_PROF_EXPLICIT = 0,  /* explicit DG operator applies                    */
+  DG_PROF_HELMHOLTZ = 1, /* Helmholtz mat-vecs inside GMRES                 */
+  DG_PROF_GRAD = 2,      /* DG gradients                                    */
+  DG_PROF_DIV = 3,       /* DG divergences                                  */
+  DG_PROF_KRYLOV = 4,    /* GMRES orthogonalisation and updates (BLAS-1)    */
+  DG_PROF_STEP = 6,      /* whole IMEX-RK2 steps                            */
+  DG_PROF_N = 8
+} dg_prof_category;
+/* Turn event timing on (1) or off (0) for every call made with this context.
+ * Events are recorded on the stream of each call; the overhead is one event
+ * pair per operator launch. */
+int dg_profile_enable(dg_ctx* ctx, int on);
+/* Synchronise the device, then copy the accumulated milliseconds and call
+ * counts per category into ms[DG_PROF_N] and counts[DG_PROF_N] (host arrays). */
+int dg_profile_read(dg_ctx* ctx, double* ms, long long* counts);
+int dg_profile_reset(dg_ctx* ctx);
+/* Number of CUDA kernels the library has launched through this context so far. */
+int dg_launch_count(const dg_ctx* ctx, long long* out);
+
+/* ---------------------------------------------------------------- mesh
+ * Sec. 3.1 meshes: a forest of quad/oct-trees over a base grid of
+ * base[0] x base[1] (x base[2]) cells covering [0, extent[a]] per axis, each
+ * leaf refined 0..7 times, neighbours differing by at most one level (2:1).
+ * The physical mesh is the terrain-following map z = zeta + h(x,y)(1 - zeta/H)
+ * (H = extent of the vertical axis), isoparametric of degree `degree` on base
+ * cells; refined cells take their nodes from their base cell's polynomial.
+ */
+typedef struct {
+  int dim;                /* 2 (x-z) or 3 (x-y-z)                               */
+  int degree;             /* polynomial degree r, 1..5; n = r+1 GLL nodes/axis  */
+  int64_t n_cells;        /* number of leaves                                   */
+  const uint8_t* level;   /* host [n_cells]: refinement level of each leaf      */
+  const int32_t* ijk;     /* host [n_cells*dim]: integer coords at own level    */
+  int base[3];            /* base grid cells per axis                           */
+  double extent[3];       /* domain length per axis (m)                         */
+  int periodic[3];        /* 1 = periodic axis, 0 = slip walls at both ends     */
+  int hill_kind;          /* dg_hill_kind: orography h(x[,y]) (Sec. 3.1)        */
+  double hill_hc;         /* hill height (m)                                    */
+  double hill_half_width; /* Gaussian: h(half_width) = hc/2; bell: a_c          */
+  double hill_xc, hill_yc;/* hill centre (m)                                    */
+  int atm_kind;           /* dg_atm_kind: hydrostatic background (Sec. 3.1)     */
+  double atm_T;           /* isothermal T0, or stratified T_ref (K)             */
+  double atm_N;           /* buoyancy frequency of the stratified case (1/s)    */
+  double atm_p_ref;       /* surface pressure (Pa)                              */
+  double gravity;         /* g (9.81 in Eq. (1)); 0 turns gravity off           */
+} dg_mesh_desc;
+
+typedef struct {
+  int dim, degree, n_vars, nodes_per_cell;
+  int64_t n_cells, n_nodes, n_dof;      /* n_dof = n_vars * n_nodes           */
+  int64_t n_conforming, n_subfaces, n_walls;
+  int max_level;
+  double min_edge;                      /* smallest computational cell edge   */
+  size_t device_bytes;                  /* device memory held by the mesh     */
+} dg_mesh_info;
+
+/* Build connectivity (conforming faces, 2:1 subfaces, walls), check the 2:1
+ * balance (DG_EUNBALANCED) and J > 0 (DG_EINVAL), compute the geometry and
+ * background on the host in FP64 and upload everything to the device.  The
+ * descriptor's arrays are copied; the caller may free them afterwards. */
+int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* desc, dg_mesh** out);
+int dg_mesh_destroy(dg_mesh* mesh);
+int dg_mesh_get_info(const dg_mesh* mesh, dg_mesh_info* info);
+/* Host copies of the face tables, for inspection.  Each pointer may be NULL.
+ * conforming [n_conforming*4]: minus cell, minus local face, plus cell, plus
+ *   local face (local face = 2*axis + side, side 1 = upper end of the axis);
+ * subfaces   [n_subfaces*4]: fine cell, fine local face, coarse cell, packed
+ *   subface position s = s_t1 + 2 s_t2 over the face's tangential axes;
+ * walls      [n_walls*2]: cell, local face. */
+int dg_mesh_get_faces(const dg_mesh* mesh, int32_t* conforming, int32_t* subfaces, int32_t* walls);
+/* Host copy of the nodal physical coordinates, [dim][n_cells][nodes_per_cell]. */
+int dg_mesh_get_coords(const dg_mesh* mesh, double* xyz);
+/* Write the hydrostatic background state U_bg (FP64, [n_vars][cells][nodes])
+ * into the device array Ubg. */
+int dg_background(dg_ctx* ctx, const dg_mesh* mesh, double* Ubg, void* stream);
+/* Initial state on the device (FP64, full variables): rest, the warm bubble
+ * (params: amp K, radius m, xc, zc[, yc] m; Delta theta = amp cos^2(pi r/(2R)),
+ * at constant pressure) or a uniform inflow (params: u0 m/s). */
+int dg_init_state(dg_ctx* ctx, const dg_mesh* mesh, int kind, const double* params, int n_params,
+                  double* U, void* stream);
+
+/* ---------------------------------------------------------------- operators */
+
+/* Explicit DG operator (Eq. (1) discretised, Sec. 2): R = M^-1 [volume - faces] + S.
+ * terms = DG_TERMS_FULL: all of Eq. (1), Rusanov with |u.n| + c.
+ * terms = DG_TERMS_IMEX_EXPLICIT: the terms the IMEX split keeps explicit
+ *   (div(rho u), div(rho u u), div(k rho u), energy source -g rho w),
+ *   Rusanov with |u.n|.
+ * U, R: device [n_vars][cells][nodes]; FP64: U full state; FP32: U perturbation. */
+int dg_apply_explicit(dg_ctx* ctx, const dg_mesh* mesh, const void* U, void* R, int precision, int terms,
+                      void* stream);
+/* Nodal gradient grad_h p = M^-1 G p (strong form, centred traces, p- on
+ * walls), optionally multiplied node by node by h (h may be NULL).
+ * p: [cells][nodes]; g: [dim][cells][nodes]. */
+int dg_apply_grad(dg_ctx* ctx, const dg_mesh* mesh, const void* p, const void* h, void* g, int precision,
+                  void* stream);
+/* Nodal divergence div_h f = M^-1 D f (weak form, centred traces, zero normal
+ * flux on walls).  f: [dim][cells][nodes]; out: [cells][nodes]. */
+int dg_apply_div(dg_ctx* ctx, const dg_mesh* mesh, const void* f, void* out, int precision, void* stream);
+/* Pressure Helmholtz operator of the implicit stage (Sec. 3.2 linear system):
+ *   Ap = p/(gamma-1) - alpha div_h(h grad_h p),  alpha = (a_ii dt)^2.
+ * h, p, Ap: [cells][nodes].  M*A is symmetric positive definite; A is not
+ * symmetric, hence GMRES. */
+int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* mesh, const void* h, const void* p, void* Ap, double alpha,
+                      int precision, void* stream);
+/* Total mass and total energy, sum over nodes of w J rho and w J rho E, in
+ * FP64 with a fixed reduction order (bitwise reproducible).  U: FP64 full
+ * state on the device; out: 2 doubles on the device. */
+int dg_conservation(dg_ctx* ctx, const dg_mesh* mesh, const double* U, double* out, void* stream);
+
+/* ---------------------------------------------------------------- time stepping */
+
+typedef struct {
+  int picard;          /* fixed-point iterations per implicit stage (3)          */
+  int restart;         /* GMRES restart length m (30, at most 64)                */
+  int max_iters;       /* GMRES iteration cap per solve (2000)                   */
+  double tol;          /* relative residual target ||b - A x|| / ||b|| (1e-12)   */
+  int precision;       /* DG_FP64, or DG_FP32 = FP32 applies + inner GMRES      */
+                       /*   inside FP64 iterative refinement                    */
+  double inner_tol;    /* DG_FP32: relative tolerance of each inner solve (1e-4) */
+  int max_refine;      /* DG_FP32: outer refinement steps cap (20)              */
+} dg_solver_opts;
+
+typedef struct {
+  int gmres_iters;     /* total inner GMRES iterations in the step              */
+  int solves;          /* linear solves (stages x Picard iterations)            */
+  int refine_steps;    /* FP64 outer corrections (DG_FP32 only)                 */
+  double max_rel_residual; /* worst final FP64 relative residual of the solves  */
+} dg_step_stats;
+
+/* Fill opts with the defaults listed above. */
+void dg_solver_opts_default(dg_solver_opts* opts);
+
+/* Device-resident solution and workspaces for one mesh (library-owned). */
+int dg_state_create(dg_ctx* ctx, const dg_mesh* mesh, const dg_solver_opts* opts, dg_state** out);
+int dg_state_destroy(dg_state* state);
+/* Device pointer to the FP64 state [n_vars][cells][nodes] (owned by the state). */
+double* dg_state_data(dg_state* state);
+/* Host <-> device copies of the state (host array of n_dof doubles), on the
+ * state's stream; both wait for completion. */
+int dg_state_upload(dg_state* state, const double* host_U);
+int dg_state_download(dg_state* state, double* host_U);
+
+/* One IMEX-RK2 step U^n -> U^{n+1} of size dt (Sec. 2 scheme; readings: ARK2
+ * tableau, Picard loop on the pressure with lagged enthalpy and kinetic
+ * energy, GMRES(m) on the Helmholtz problem).  Enqueued on `stream`; returns
+ * after the step has finished (the Krylov loops read residuals on the host).
+ * Returns DG_ENOTCONV if a solve missed its tolerance within max_iters (the
+ * state then holds the unconverged step), DG_ENONFINITE if the new state has
+ * a NaN/Inf. `stats` may be NULL. */
+int imex_rk2_step(dg_ctx* ctx, const dg_mesh* mesh, dg_state* state, double dt, const dg_solver_opts* opts,
+                  dg_step_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_ATMO_H */

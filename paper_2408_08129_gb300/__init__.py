@@ -1,0 +1,30 @@
+"""GB300-native matrix-free DG solver for compressible Euler on 2:1 non-conforming meshes.
+
+The computation lives in the CUDA library ``_lib/libdgatmo.so`` (C ABI in
+``include/dg_atmo.h``); this package only marshals arguments.  Importing it
+without the built library raises ImportError: there is no CPU fallback.
+"""
+
+from .api import (  # noqa: F401
+    DG_FP32,
+    DG_FP64,
+    DG_TERMS_FULL,
+    DG_TERMS_IMEX_EXPLICIT,
+    Context,
+    DGError,
+    Mesh,
+    State,
+    dg_apply_div,
+    dg_apply_explicit,
+    dg_apply_grad,
+    dg_apply_implicit,
+    dg_background,
+    dg_conservation,
+    dg_init_state,
+    dg_launch_count,
+    dg_profile_enable,
+    dg_profile_read,
+    dg_profile_reset,
+    imex_rk2_step,
+    solver_opts,
+)

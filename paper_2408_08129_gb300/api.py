@@ -1,0 +1,258 @@
+"""Thin Python binding over the C ABI, with the same names (argument marshalling only).
+
+Device arrays are torch CUDA tensors (contiguous, float64 or float32); their
+``data_ptr()`` and the current torch stream are handed to the library.  Every
+step of the computation runs in the library's CUDA kernels.
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _binding as B
+from ._binding import (  # noqa: F401
+    DG_ATM, DG_FP32, DG_FP64, DG_HILL, DG_INIT, DG_TERMS_FULL, DG_TERMS_IMEX_EXPLICIT, DGError, check, lib,
+)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _fdtype(precision):
+    return torch.float64 if precision == DG_FP64 else torch.float32
+
+
+class Context:
+    """dg_ctx on one CUDA device."""
+
+    def __init__(self, device=0):
+        h = ctypes.c_void_p()
+        check(lib.dg_ctx_create(int(device), ctypes.byref(h)), "dg_ctx_create")
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            lib.dg_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    """dg_mesh built from a workload description (see workloads.Case)."""
+
+    def __init__(self, ctx, case, gravity=None):
+        d = B.MeshDesc()
+        d.dim = case.dim
+        d.degree = case.degree
+        d.n_cells = case.n_cells
+        self._level = np.ascontiguousarray(case.levels, dtype=np.uint8)
+        self._ijk = np.ascontiguousarray(case.ijk, dtype=np.int32)
+        d.level = self._level.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        d.ijk = self._ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        for a in range(case.dim):
+            d.base[a] = case.base[a]
+            d.extent[a] = case.extent[a]
+            d.periodic[a] = 1 if case.periodic[a] else 0
+        hill = case.hill
+        d.hill_kind = DG_HILL[hill["kind"]]
+        d.hill_hc = hill.get("hc", 0.0)
+        d.hill_half_width = hill.get("half_width", 1.0)
+        d.hill_xc = hill.get("xc", 0.0)
+        d.hill_yc = hill.get("yc", 0.0)
+        atm = case.atmosphere
+        d.atm_kind = DG_ATM[atm["kind"]]
+        d.atm_T = atm.get("T0", atm.get("T_ref", 0.0))
+        d.atm_N = atm.get("N", 0.0)
+        d.atm_p_ref = atm.get("p_ref", 0.0)
+        d.gravity = case.gravity if gravity is None else gravity
+        h = ctypes.c_void_p()
+        check(lib.dg_mesh_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "dg_mesh_create")
+        self.handle = h
+        self.ctx = ctx
+        self.case = case
+        info = B.MeshInfo()
+        check(lib.dg_mesh_get_info(h, ctypes.byref(info)), "dg_mesh_get_info")
+        self.info = {k: getattr(info, k) for k, _ in B.MeshInfo._fields_}
+        self.dim = case.dim
+        self.n_vars = info.n_vars
+        self.n_cells = info.n_cells
+        self.nodes_per_cell = info.nodes_per_cell
+        self.n_nodes = info.n_nodes
+        self.n_dof = info.n_dof
+
+    def faces(self):
+        i = self.info
+        conf = np.zeros((i["n_conforming"], 4), np.int32)
+        subs = np.zeros((i["n_subfaces"], 4), np.int32)
+        walls = np.zeros((i["n_walls"], 2), np.int32)
+        check(lib.dg_mesh_get_faces(self.handle, conf.ctypes.data, subs.ctypes.data, walls.ctypes.data),
+              "dg_mesh_get_faces")
+        return conf, subs, walls
+
+    def coords(self):
+        X = np.zeros((self.dim, self.n_cells, self.nodes_per_cell))
+        check(lib.dg_mesh_get_coords(self.handle, X.ctypes.data), "dg_mesh_get_coords")
+        return X
+
+    def shape(self, nv=None):
+        return (self.n_vars if nv is None else nv, self.n_cells, self.nodes_per_cell)
+
+    def close(self):
+        if self.handle:
+            lib.dg_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+PROF_CATEGORIES = {0: "explicit", 1: "helmholtz", 2: "grad", 3: "div", 4: "krylov", 6: "step"}
+
+
+def dg_profile_enable(ctx, on=True):
+    check(lib.dg_profile_enable(ctx.handle, 1 if on else 0), "dg_profile_enable")
+
+
+def dg_profile_reset(ctx):
+    check(lib.dg_profile_reset(ctx.handle), "dg_profile_reset")
+
+
+def dg_profile_read(ctx):
+    ms = np.zeros(8)
+    n = np.zeros(8, dtype=np.int64)
+    check(lib.dg_profile_read(ctx.handle, ms.ctypes.data, n.ctypes.data), "dg_profile_read")
+    return {name: {"ms": float(ms[i]), "count": int(n[i])} for i, name in PROF_CATEGORIES.items()}
+
+
+def dg_launch_count(ctx):
+    n = ctypes.c_longlong(0)
+    check(lib.dg_launch_count(ctx.handle, ctypes.byref(n)), "dg_launch_count")
+    return int(n.value)
+
+
+def dg_background(ctx, mesh, Ubg, stream=None):
+    check(lib.dg_background(ctx.handle, mesh.handle, _ptr(Ubg, torch.float64), _stream(stream)), "dg_background")
+
+
+def dg_init_state(ctx, mesh, kind, params, U, stream=None):
+    arr = (ctypes.c_double * max(1, len(params)))(*params)
+    check(lib.dg_init_state(ctx.handle, mesh.handle, DG_INIT[kind] if isinstance(kind, str) else kind, arr,
+                            len(params), _ptr(U, torch.float64), _stream(stream)), "dg_init_state")
+
+
+def dg_apply_explicit(ctx, mesh, U, R, precision=DG_FP64, terms=DG_TERMS_FULL, stream=None):
+    dt = _fdtype(precision)
+    check(lib.dg_apply_explicit(ctx.handle, mesh.handle, _ptr(U, dt), _ptr(R, dt), precision, terms,
+                                _stream(stream)), "dg_apply_explicit")
+
+
+def dg_apply_grad(ctx, mesh, p, g, h=None, precision=DG_FP64, stream=None):
+    dt = _fdtype(precision)
+    check(lib.dg_apply_grad(ctx.handle, mesh.handle, _ptr(p, dt), _ptr(h, dt), _ptr(g, dt), precision,
+                            _stream(stream)), "dg_apply_grad")
+
+
+def dg_apply_div(ctx, mesh, f, out, precision=DG_FP64, stream=None):
+    dt = _fdtype(precision)
+    check(lib.dg_apply_div(ctx.handle, mesh.handle, _ptr(f, dt), _ptr(out, dt), precision, _stream(stream)),
+          "dg_apply_div")
+
+
+def dg_apply_implicit(ctx, mesh, h, p, Ap, alpha, precision=DG_FP64, stream=None):
+    dt = _fdtype(precision)
+    check(lib.dg_apply_implicit(ctx.handle, mesh.handle, _ptr(h, dt), _ptr(p, dt), _ptr(Ap, dt), float(alpha),
+                                precision, _stream(stream)), "dg_apply_implicit")
+
+
+def dg_conservation(ctx, mesh, U, out, stream=None):
+    check(lib.dg_conservation(ctx.handle, mesh.handle, _ptr(U, torch.float64), _ptr(out, torch.float64),
+                              _stream(stream)), "dg_conservation")
+
+
+def solver_opts(**kw):
+    o = B.SolverOpts()
+    lib.dg_solver_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class _DeviceArray:
+    """Exposes a library-owned device buffer to torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr, shape, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False), "version": 3, "strides": None,
+        }
+
+
+class State:
+    """dg_state: the device-resident FP64 solution and the step workspaces."""
+
+    def __init__(self, ctx, mesh, opts=None):
+        h = ctypes.c_void_p()
+        o = opts if opts is not None else solver_opts()
+        check(lib.dg_state_create(ctx.handle, mesh.handle, ctypes.byref(o), ctypes.byref(h)), "dg_state_create")
+        self.handle = h
+        self.ctx = ctx
+        self.mesh = mesh
+        ptr = lib.dg_state_data(h)
+        self.U = torch.as_tensor(_DeviceArray(ptr, mesh.shape(), self), device="cuda:%d" % ctx.device)
+
+    def upload(self, host_U):
+        a = np.ascontiguousarray(host_U, dtype=np.float64)
+        check(lib.dg_state_upload(self.handle, a.ctypes.data), "dg_state_upload")
+
+    def download(self):
+        a = np.zeros(self.mesh.shape())
+        check(lib.dg_state_download(self.handle, a.ctypes.data), "dg_state_download")
+        return a
+
+    def close(self):
+        if self.handle:
+            lib.dg_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def imex_rk2_step(ctx, mesh, state, dt, opts=None, stream=None, raise_on_error=True):
+    o = opts if opts is not None else solver_opts()
+    st = B.StepStats()
+    rc = lib.imex_rk2_step(ctx.handle, mesh.handle, state.handle, float(dt), ctypes.byref(o), ctypes.byref(st),
+                           _stream(stream))
+    if raise_on_error:
+        check(rc, "imex_rk2_step")
+    return {k: getattr(st, k) for k, _ in B.StepStats._fields_} | {"status": rc}

@@ -1,0 +1,107 @@
+// Device-side helpers shared by the DG kernels: compile-time sizes, node and
+// face-node indexing, table layout, and the pointwise Euler physics of Eq. (1)
+// written in perturbation form about the hydrostatic background.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+__host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
+
+template <int DIM, int DEG>
+struct Shape {
+  static constexpr int N = DEG + 1;             // nodes per axis
+  static constexpr int NC = cpow(N, DIM);       // nodes per cell
+  static constexpr int NF = cpow(N, DIM - 1);   // nodes per face
+  static constexpr int V = DIM + 2;             // conserved variables
+  static constexpr int NSUB = 1 << (DIM - 1);   // subfaces of a 2:1 face
+  // cells per CTA for the one-thread-per-node cell kernels (>= 128 threads)
+  static constexpr int CPB = NC >= 128 ? 1 : (128 + NC - 1) / NC;
+  static constexpr int THREADS = ((CPB * NC + 31) / 32) * 32;
+  // table offsets (see Tables1D)
+  static constexpr int T_D = 0, T_DW = N * N, T_I = 2 * N * N, T_IT = 4 * N * N, T_W = 6 * N * N,
+                       T_IWEND = 6 * N * N + N, T_SIZE = 6 * N * N + N + 1;
+};
+
+// node index inside the cell of face node k on local face lf = 2*axis + side
+template <int DIM, int DEG>
+__device__ __forceinline__ int face_node(int lf, int k) {
+  constexpr int N = DEG + 1;
+  const int a = lf >> 1;
+  const int fix = (lf & 1) ? DEG : 0;
+  if (DIM == 2) {
+    return a == 0 ? fix + N * k : k + N * fix;
+  } else {
+    const int k1 = k % N, k2 = k / N;
+    if (a == 0) return fix + N * k1 + N * N * k2;
+    if (a == 1) return k1 + N * fix + N * N * k2;
+    return k1 + N * k2 + N * N * fix;
+  }
+}
+
+// Tangential face index of a cell node lying on a face normal to axis a.
+template <int DIM, int DEG>
+__device__ __forceinline__ int tangential_index(int a, const int* idx) {
+  constexpr int N = DEG + 1;
+  if (DIM == 2) return a == 0 ? idx[1] : idx[0];
+  if (a == 0) return idx[1] + N * idx[2];
+  if (a == 1) return idx[0] + N * idx[2];
+  return idx[0] + N * idx[1];
+}
+
+template <typename T>
+__device__ __forceinline__ T gm1() {
+  return T(0.4);
+}
+
+// Load a state at node `idx` in perturbation form u' = u - u_bg.  FP64 arrays
+// hold the full state (the background is subtracted here); FP32 arrays hold
+// the perturbation already.
+template <int V, typename T, bool PERT>
+__device__ __forceinline__ void load_pert(const T* __restrict__ U, int64_t Nn, int64_t idx, const T* rhob,
+                                          const T* pb, T* u) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) u[v] = U[(int64_t)v * Nn + idx];
+  if (!PERT) {
+    u[0] -= rhob[idx];
+    u[V - 1] -= pb[idx] / gm1<T>();
+  }
+}
+
+// Normal flux F(U).n and the dissipation speed for a state given as a
+// perturbation u' about (rho_b, p_b):  rho = rho_b + rho', rho E = p_b/(g-1) + E',
+// p' = (g-1)(E' - |m|^2/(2 rho)), p = p_b + p'.
+template <int DIM, typename T, bool FULL>
+__device__ __forceinline__ void normal_flux(const T* u, T rb, T pb, const T* n, T* F, T& lam) {
+  constexpr int V = DIM + 2;
+  const T rho = rb + u[0];
+  const T irho = T(1) / rho;
+  T mn = T(0), m2 = T(0);
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    mn += u[1 + b] * n[b];
+    m2 += u[1 + b] * u[1 + b];
+  }
+  const T un = mn * irho;
+  F[0] = mn;
+  if (FULL) {
+    const T pp = gm1<T>() * (u[V - 1] - T(0.5) * m2 * irho);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) F[1 + b] = u[1 + b] * un + pp * n[b];
+    // rho E + p = E' + p' + gamma/(gamma-1) p_b
+    F[V - 1] = (u[V - 1] + pp + pb * (T(1.4) / gm1<T>())) * un;
+    const T p = pb + pp;
+    lam = fabs(un) + sqrt(T(1.4) * p * irho);
+  } else {
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) F[1 + b] = u[1 + b] * un;
+    F[V - 1] = T(0.5) * m2 * irho * irho * mn;
+    lam = fabs(un);
+  }
+}
+
+}  // namespace dg

@@ -1,0 +1,131 @@
+// Internal declarations shared by the host and device translation units of the
+// DG library.  Nothing here is part of the C ABI (include/dg_atmo.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dg_atmo.h"
+
+namespace dg {
+
+constexpr double kGamma = 1.4;   // Sec. 3.1
+constexpr double kRgas = 287.0;  // Sec. 2
+constexpr int kMaxDegree = 5;
+constexpr int kMaxRestart = 64;
+
+// thread-local error message, set by fail()
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+#define DG_CUDA(call)                                           \
+  do {                                                          \
+    cudaError_t e__ = (call);                                   \
+    if (e__ != cudaSuccess) return ::dg::cuda_fail(e__, #call); \
+  } while (0)
+
+// 1D tables of one degree, in the device layout used by every kernel:
+//   D  [n*n]  D[i*n+k]  = l_k'(xi_i)                   (nodal derivative)
+//   Dw [n*n]  Dw[i*n+k] = w_k l_i'(xi_k) / w_i          (weak derivative / w_i)
+//   I  [2*n*n] I[s*n*n + f*n + j] = l_j((xi_f + 2s - 1)/2)  (coarse -> half s)
+//   It [2*n*n] It[s*n*n + i*n + f] = (w_f / w_i) I[s][f][i]  (its weighted transpose)
+//   w  [n], then 1/w_end (w_end = w_0 = w_r)
+struct Tables1D {
+  int degree = 0;
+  std::vector<double> xi, w, D, Dw, I, It;
+  std::vector<double> packed() const;  // D|Dw|I|It|w|1/w_end
+};
+Tables1D make_tables(int degree);
+inline int table_size(int n) { return 6 * n * n + n + 1; }
+// Lagrange basis on `nodes` at point x: out[j] = l_j(x)
+void lagrange_eval(const std::vector<double>& nodes, double x, double* out);
+
+// Device views handed to kernels (by value).
+template <typename T>
+struct MeshView {
+  int64_t n_cells;
+  int64_t n_nodes;
+  int nconf, nsub, nwall, nf;  // faces: [0,nconf) conforming, then subfaces, then walls
+  const T* Ja;      // [dim*dim][n_nodes], Ja[a*dim+b] = J d xi^a / d x_b
+  const T* invJ;    // [n_nodes]
+  const T* rhob;    // [n_nodes] background density
+  const T* pb;      // [n_nodes] background pressure
+  const T* wJ;      // [n_nodes] w_i J_i (mass matrix diagonal)
+  const int* face_m;    // [nf] minus (fine) cell
+  const int* face_lfm;  // [nf] minus local face
+  const int* face_p;    // [nf] plus cell / coarse cell (-1 for walls)
+  const int* face_lfp;  // [nf] plus / coarse local face
+  const int* face_s;    // [nf] packed subface position (subfaces only)
+  const T* fn;      // [dim][nf*NF] unit normal out of the minus side
+  const T* fsj;     // [nf*NF] |J grad xi^a| (surface Jacobian)
+  const int* cell_face;  // [n_cells*2*dim] (face << 2) | side; side 0 minus, 1 plus, 2 coarse, 3 wall
+  const T* tab;     // packed Tables1D of the mesh's degree
+  T gravity;
+};
+
+}  // namespace dg
+
+struct dg_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t own_stream = nullptr;
+  // optional per-operator timing with CUDA events (see dg_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next = 0;
+  std::vector<std::pair<int, size_t>> ev_pending;  // (category, index of the start event)
+  double prof_ms[8] = {0};
+  long long prof_n[8] = {0};
+  long long launches = 0;  // kernels launched through this context
+};
+
+namespace dg {
+inline void count_launches(dg_ctx* c, int n) {
+  if (c) c->launches += n;
+}
+// Record a start event for category `cat` on stream s; returns a token for prof_end
+// (or SIZE_MAX when profiling is off).  Events are resolved by prof_resolve().
+size_t prof_begin(dg_ctx* c, cudaStream_t s);
+void prof_end(dg_ctx* c, int cat, size_t tok, cudaStream_t s);
+void prof_resolve(dg_ctx* c);  // synchronises the device first
+struct ProfScope {
+  dg_ctx* c;
+  int cat;
+  size_t tok;
+  cudaStream_t s;
+  ProfScope(dg_ctx* c_, int cat_, cudaStream_t s_) : c(c_), cat(cat_), tok(prof_begin(c_, s_)), s(s_) {}
+  ~ProfScope() { prof_end(c, cat, tok, s); }
+};
+}  // namespace dg
+
+struct dg_mesh {
+  dg_ctx* ctx = nullptr;
+  dg_mesh_desc desc{};
+  int dim = 0, degree = 0, n = 0, nc = 0, nf_nodes = 0, V = 0;
+  int64_t K = 0, Nn = 0;
+  int max_level = 0;
+  double min_edge = 0;
+  // host tables
+  std::vector<uint8_t> level;
+  std::vector<int32_t> ijk;
+  std::vector<int32_t> conf;   // [nconf*4]
+  std::vector<int32_t> subs;   // [nsub*4] fine, lf_fine, coarse, s (sorted by coarse, lf, s)
+  std::vector<int32_t> subs_lfc;
+  std::vector<int32_t> walls;  // [nwall*2]
+  std::vector<double> X;       // [dim][K][nc]
+  int nconf = 0, nsub = 0, nwall = 0, nf = 0;
+  size_t device_bytes = 0;
+  // device memory: one block each for FP64 and FP32 geometry + int tables + scratch
+  void* d_int = nullptr;
+  void* d_f64 = nullptr;
+  void* d_f32 = nullptr;
+  void* d_scratch = nullptr;  // face fluxes + grad intermediate (FP64-sized)
+  size_t scratch_bytes = 0;
+  dg::MeshView<double> v64{};
+  dg::MeshView<float> v32{};
+  double* d_face_scratch64 = nullptr;
+  double* d_vec_scratch64 = nullptr;  // [dim][Nn]
+  double* d_red_scratch = nullptr;    // [2*512] block partials of the conservation sums
+};

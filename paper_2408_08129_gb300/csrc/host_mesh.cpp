@@ -1,0 +1,530 @@
+// Mesh construction on the host: connectivity of the 2:1 tree forest, the
+// terrain-following isoparametric geometry, metric terms, face normals and the
+// hydrostatic background, followed by one upload per precision.
+//
+// Sec. 3.1: flow over orography on a terrain-following mesh refined near the
+// ground with neighbours of different resolution both horizontally and
+// vertically (no hanging nodes in the DG sense, Sec. 2).  Mesh-map reading:
+// z = zeta + h(x,y)(1 - zeta/H), isoparametric of degree r on base cells,
+// refined cells sampling their base cell's polynomial (watertight 2:1 faces);
+// metric terms J grad(xi^a) by rotated nodal derivatives (2D) or cross
+// products of nodal tangents (3D; exact discrete metric identities because x
+// and y are affine per cell).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+namespace {
+
+inline uint64_t key_of(int l, const int* c) {
+  return ((uint64_t)l << 60) | ((uint64_t)(uint32_t)c[0] << 40) | ((uint64_t)(uint32_t)c[1] << 20) |
+         (uint64_t)(uint32_t)c[2];
+}
+
+double hill(const dg_mesh_desc& d, double x, double y) {
+  const double xc = d.hill_xc, yc = d.hill_yc, a = d.hill_half_width;
+  switch (d.hill_kind) {
+    case DG_HILL_NONE:
+      return 0.0;
+    case DG_HILL_GAUSS: {
+      double r2 = (x - xc) * (x - xc) + (d.dim == 3 ? (y - yc) * (y - yc) : 0.0);
+      return d.hill_hc * std::exp(-std::log(2.0) * r2 / (a * a));
+    }
+    case DG_HILL_BELL: {
+      double q = 1.0 + ((x - xc) / a) * ((x - xc) / a) + (d.dim == 3 ? ((y - yc) / a) * ((y - yc) / a) : 0.0);
+      return d.hill_hc / (q * std::sqrt(q));
+    }
+    case DG_HILL_PARABOLA: {
+      double s = 1.0 - ((x - xc) / a) * ((x - xc) / a) - (d.dim == 3 ? ((y - yc) / a) * ((y - yc) / a) : 0.0);
+      return d.hill_hc * s;
+    }
+  }
+  return 0.0;
+}
+
+// hydrostatic background at height z (Sec. 3.1; stratified p with the factor g restored)
+void background(const dg_mesh_desc& d, double z, double* rho, double* p) {
+  const double g = 9.81;
+  if (d.atm_kind == DG_ATM_NONE) {
+    *rho = 0.0;
+    *p = 0.0;
+  } else if (d.atm_kind == DG_ATM_ISOTHERMAL) {
+    *p = d.atm_p_ref * std::exp(-g * z / (kRgas * d.atm_T));
+    *rho = *p / (kRgas * d.atm_T);
+  } else {
+    const double n2 = d.atm_N * d.atm_N;
+    const double cg = (kGamma - 1.0) / kGamma;
+    const double rho_ref = d.atm_p_ref / (kRgas * d.atm_T);
+    const double s = std::exp(-n2 * z / g);
+    const double base = 1.0 - (g * g / n2) * cg * (rho_ref / d.atm_p_ref) * (1.0 - s);
+    *p = d.atm_p_ref * std::pow(base, 1.0 / cg);
+    *rho = rho_ref * std::pow(*p / d.atm_p_ref, 1.0 / kGamma) * s;
+  }
+}
+
+inline int ipow(int b, int e) {
+  int r = 1;
+  while (e--) r *= b;
+  return r;
+}
+
+}  // namespace
+
+// node index of face node k on local face lf (tangential axes ascending, first fastest)
+int host_face_node(int dim, int n, int lf, int k) {
+  const int a = lf >> 1, side = lf & 1;
+  int idx[3] = {0, 0, 0};
+  idx[a] = side ? n - 1 : 0;
+  int t = 0;
+  for (int b = 0; b < dim; ++b) {
+    if (b == a) continue;
+    idx[b] = (t == 0) ? (k % n) : (k / n);
+    ++t;
+  }
+  return idx[0] + n * idx[1] + n * n * idx[2];
+}
+
+int build_mesh(dg_mesh* m) {
+  const dg_mesh_desc& d = m->desc;
+  const int dim = d.dim, r = d.degree, n = r + 1;
+  m->dim = dim;
+  m->degree = r;
+  m->n = n;
+  m->nc = ipow(n, dim);
+  m->nf_nodes = ipow(n, dim - 1);
+  m->V = dim + 2;
+  m->K = d.n_cells;
+  m->Nn = m->K * m->nc;
+  const int64_t K = m->K;
+  const int nc = m->nc, NF = m->nf_nodes;
+
+  // ---------------------------------------------------------------- topology
+  std::unordered_map<uint64_t, int> leaf;
+  leaf.reserve(K * 2);
+  std::unordered_set<uint64_t> internal;
+  m->max_level = 0;
+  for (int64_t c = 0; c < K; ++c) {
+    int l = m->level[c];
+    int ijk[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+      ijk[a] = m->ijk[c * dim + a];
+      if (ijk[a] < 0 || ijk[a] >= (d.base[a] << l)) return fail(DG_EINVAL, "cell coordinate out of range");
+    }
+    if (!leaf.emplace(key_of(l, ijk), (int)c).second) return fail(DG_EINVAL, "duplicate cell");
+    m->max_level = std::max(m->max_level, l);
+    for (int ll = l - 1; ll >= 0; --ll) {
+      for (int a = 0; a < 3; ++a) ijk[a] >>= 1;
+      internal.insert(key_of(ll, ijk));
+    }
+  }
+  for (const auto& kv : leaf)
+    if (internal.count(kv.first)) return fail(DG_EINVAL, "a cell overlaps a refined cell");
+
+  std::vector<int32_t> conf, walls;
+  struct Sub {
+    int fine, lff, coarse, lfc, s;
+  };
+  std::vector<Sub> subs;
+  for (int64_t c = 0; c < K; ++c) {
+    const int l = m->level[c];
+    int ijk[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) ijk[a] = m->ijk[c * dim + a];
+    for (int a = 0; a < dim; ++a) {
+      for (int side = 0; side < 2; ++side) {
+        const int lf = 2 * a + side;
+        const int nmax = d.base[a] << l;
+        int nb[3] = {ijk[0], ijk[1], ijk[2]};
+        nb[a] += side ? 1 : -1;
+        if (nb[a] < 0 || nb[a] >= nmax) {
+          if (!d.periodic[a]) {
+            walls.push_back((int32_t)c);
+            walls.push_back(lf);
+            continue;
+          }
+          nb[a] = (nb[a] + nmax) % nmax;
+        }
+        auto it = leaf.find(key_of(l, nb));
+        if (it != leaf.end()) {
+          if (side == 1) {
+            conf.push_back((int32_t)c);
+            conf.push_back(lf);
+            conf.push_back(it->second);
+            conf.push_back(lf - 1);
+          }
+          continue;
+        }
+        int par[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
+        auto ip = (l > 0) ? leaf.find(key_of(l - 1, par)) : leaf.end();
+        if (ip != leaf.end()) {
+          int s = 0, t = 0;
+          for (int b = 0; b < dim; ++b) {
+            if (b == a) continue;
+            s |= (ijk[b] & 1) << t;
+            ++t;
+          }
+          subs.push_back({(int)c, lf, ip->second, 2 * a + (1 - side), s});
+          continue;
+        }
+        if (internal.count(key_of(l, nb))) {
+          // coarse side: the children touching this face must be leaves (2:1)
+          for (int o = 0; o < (1 << dim); ++o) {
+            int ch[3] = {0, 0, 0};
+            for (int b = 0; b < dim; ++b) ch[b] = 2 * nb[b] + ((o >> b) & 1);
+            if (((o >> a) & 1) != (side ? 0 : 1)) continue;
+            if (!leaf.count(key_of(l + 1, ch))) return fail(DG_EUNBALANCED, "mesh is not 2:1 balanced");
+          }
+          continue;
+        }
+        return fail(DG_EUNBALANCED, "mesh is not 2:1 balanced");
+      }
+    }
+  }
+  std::sort(subs.begin(), subs.end(), [](const Sub& x, const Sub& y) {
+    if (x.coarse != y.coarse) return x.coarse < y.coarse;
+    if (x.lfc != y.lfc) return x.lfc < y.lfc;
+    return x.s < y.s;
+  });
+  m->nconf = (int)(conf.size() / 4);
+  m->nsub = (int)subs.size();
+  m->nwall = (int)(walls.size() / 2);
+  m->nf = m->nconf + m->nsub + m->nwall;
+  m->conf = conf;
+  m->walls = walls;
+  m->subs.clear();
+  m->subs_lfc.clear();
+  for (const Sub& s : subs) {
+    m->subs.insert(m->subs.end(), {s.fine, s.lff, s.coarse, s.s});
+    m->subs_lfc.push_back(s.lfc);
+  }
+
+  const int nf = m->nf;
+  std::vector<int> face_m(nf), face_lfm(nf), face_p(nf), face_lfp(nf), face_s(nf, 0);
+  std::vector<int> cell_face(K * 2 * dim, -1);
+  for (int f = 0; f < m->nconf; ++f) {
+    face_m[f] = conf[4 * f];
+    face_lfm[f] = conf[4 * f + 1];
+    face_p[f] = conf[4 * f + 2];
+    face_lfp[f] = conf[4 * f + 3];
+    cell_face[face_m[f] * 2 * dim + face_lfm[f]] = (f << 2) | 0;
+    cell_face[face_p[f] * 2 * dim + face_lfp[f]] = (f << 2) | 1;
+  }
+  const int nsubface = 1 << (dim - 1);
+  for (int j = 0; j < m->nsub; ++j) {
+    const int f = m->nconf + j;
+    const Sub& s = subs[j];
+    face_m[f] = s.fine;
+    face_lfm[f] = s.lff;
+    face_p[f] = s.coarse;
+    face_lfp[f] = s.lfc;
+    face_s[f] = s.s;
+    cell_face[s.fine * 2 * dim + s.lff] = (f << 2) | 0;
+    if (s.s == 0) {
+      // the coarse face's subfaces must be the next 2^(d-1) entries, s = 0, 1, ...
+      for (int q = 0; q < nsubface; ++q) {
+        if (j + q >= m->nsub || subs[j + q].coarse != s.coarse || subs[j + q].lfc != s.lfc || subs[j + q].s != q)
+          return fail(DG_EUNBALANCED, "incomplete set of subfaces on a 2:1 face");
+      }
+      cell_face[s.coarse * 2 * dim + s.lfc] = (f << 2) | 2;
+    }
+  }
+  for (int j = 0; j < m->nwall; ++j) {
+    const int f = m->nconf + m->nsub + j;
+    face_m[f] = walls[2 * j];
+    face_lfm[f] = walls[2 * j + 1];
+    face_p[f] = -1;
+    face_lfp[f] = -1;
+    cell_face[face_m[f] * 2 * dim + face_lfm[f]] = (f << 2) | 3;
+  }
+  for (size_t i = 0; i < cell_face.size(); ++i)
+    if (cell_face[i] < 0) return fail(DG_EUNBALANCED, "mesh is not watertight");
+
+  // ---------------------------------------------------------------- geometry
+  Tables1D tab = make_tables(r);
+  const double H = d.extent[dim - 1];
+  double hb[3];
+  for (int a = 0; a < dim; ++a) hb[a] = d.extent[a] / d.base[a];
+  m->min_edge = 1e300;
+  for (int a = 0; a < dim; ++a) m->min_edge = std::min(m->min_edge, hb[a] / (1 << m->max_level));
+
+  m->X.assign((size_t)dim * K * nc, 0.0);
+  std::vector<double> Xb((size_t)dim * nc), tmp((size_t)dim * nc), tmp2((size_t)dim * nc);
+  std::unordered_map<uint64_t, std::vector<double>> interp_cache;  // (level, axis, offset) -> n x n
+  std::vector<int> mi((size_t)nc * 3);
+  for (int q = 0; q < nc; ++q) {
+    mi[3 * q] = q % n;
+    mi[3 * q + 1] = (q / n) % n;
+    mi[3 * q + 2] = q / (n * n);
+  }
+  for (int64_t c = 0; c < K; ++c) {
+    const int l = m->level[c];
+    int ijk[3] = {0, 0, 0}, bijk[3] = {0, 0, 0}, off[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+      ijk[a] = m->ijk[c * dim + a];
+      bijk[a] = ijk[a] >> l;
+      off[a] = ijk[a] - (bijk[a] << l);
+    }
+    // base cell nodes: analytic terrain-following map at the base GLL nodes
+    for (int q = 0; q < nc; ++q) {
+      double comp[3];
+      for (int a = 0; a < dim; ++a) comp[a] = bijk[a] * hb[a] + 0.5 * (tab.xi[mi[3 * q + a]] + 1.0) * hb[a];
+      for (int a = 0; a < dim; ++a) Xb[(size_t)a * nc + q] = comp[a];
+      const double zeta = comp[dim - 1];
+      const double hx = hill(d, comp[0], dim == 3 ? comp[1] : 0.0);
+      Xb[(size_t)(dim - 1) * nc + q] = zeta + hx * (1.0 - zeta / H);
+    }
+    // interpolate axis by axis onto this cell's nodes (sum factorisation)
+    const std::vector<double>* src = &Xb;
+    std::vector<double>* dst = &tmp;
+    for (int a = 0; a < dim; ++a) {
+      uint64_t key = ((uint64_t)l << 32) | ((uint64_t)a << 24) | (uint64_t)off[a];
+      auto itc = interp_cache.find(key);
+      if (itc == interp_cache.end()) {
+        std::vector<double> L((size_t)n * n);
+        for (int i = 0; i < n; ++i) {
+          const double ref = -1.0 + (2.0 * off[a] + tab.xi[i] + 1.0) / (double)(1 << l);
+          lagrange_eval(tab.xi, ref, &L[(size_t)i * n]);
+        }
+        itc = interp_cache.emplace(key, std::move(L)).first;
+      }
+      const std::vector<double>& L = itc->second;
+      const int stride = ipow(n, a);
+      for (int b = 0; b < dim; ++b)
+        for (int q = 0; q < nc; ++q) {
+          const int ia = mi[3 * q + a];
+          const int q0 = q - ia * stride;
+          double s = 0.0;
+          for (int j = 0; j < n; ++j) s += L[(size_t)ia * n + j] * (*src)[(size_t)b * nc + q0 + j * stride];
+          (*dst)[(size_t)b * nc + q] = s;
+        }
+      src = dst;
+      dst = (dst == &tmp) ? &tmp2 : &tmp;
+    }
+    for (int b = 0; b < dim; ++b)
+      for (int q = 0; q < nc; ++q) m->X[((size_t)b * K + c) * nc + q] = (*src)[(size_t)b * nc + q];
+  }
+
+  // metric terms at nodes
+  std::vector<double> Ja((size_t)dim * dim * m->Nn), invJ(m->Nn), wJ(m->Nn), rhob(m->Nn), pb(m->Nn);
+  for (int64_t c = 0; c < K; ++c) {
+    for (int q = 0; q < nc; ++q) {
+      double t[3][3] = {{0}};  // t[a][b] = d x_b / d xi^a
+      for (int a = 0; a < dim; ++a) {
+        const int stride = ipow(n, a);
+        const int ia = mi[3 * q + a];
+        const int q0 = q - ia * stride;
+        for (int b = 0; b < dim; ++b) {
+          double s = 0.0;
+          for (int k = 0; k < n; ++k) s += tab.D[ia * n + k] * m->X[((size_t)b * K + c) * nc + q0 + k * stride];
+          t[a][b] = s;
+        }
+      }
+      double M[3][3] = {{0}}, J;
+      if (dim == 2) {
+        J = t[0][0] * t[1][1] - t[1][0] * t[0][1];
+        M[0][0] = t[1][1];
+        M[0][1] = -t[1][0];
+        M[1][0] = -t[0][1];
+        M[1][1] = t[0][0];
+      } else {
+        for (int a = 0; a < 3; ++a) {
+          const double* u = t[(a + 1) % 3];
+          const double* v = t[(a + 2) % 3];
+          M[a][0] = u[1] * v[2] - u[2] * v[1];
+          M[a][1] = u[2] * v[0] - u[0] * v[2];
+          M[a][2] = u[0] * v[1] - u[1] * v[0];
+        }
+        J = t[0][0] * M[0][0] + t[0][1] * M[0][1] + t[0][2] * M[0][2];
+      }
+      if (!(J > 0.0)) return fail(DG_EINVAL, "non-positive Jacobian (hill too steep for the mesh)");
+      const int64_t idx = c * nc + q;
+      for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) Ja[(size_t)(a * dim + b) * m->Nn + idx] = M[a][b];
+      invJ[idx] = 1.0 / J;
+      double wq = 1.0;
+      for (int a = 0; a < dim; ++a) wq *= tab.w[mi[3 * q + a]];
+      wJ[idx] = wq * J;
+      background(d, m->X[((size_t)(dim - 1) * K + c) * nc + q], &rhob[idx], &pb[idx]);
+    }
+  }
+  // face-node normals from the minus (fine) side
+  std::vector<double> fn((size_t)dim * nf * NF), fsj((size_t)nf * NF);
+  for (int f = 0; f < nf; ++f) {
+    const int c = face_m[f], lf = face_lfm[f], a = lf >> 1, side = lf & 1;
+    for (int k = 0; k < NF; ++k) {
+      const int64_t idx = (int64_t)c * nc + host_face_node(dim, n, lf, k);
+      double N[3], s = 0.0;
+      for (int b = 0; b < dim; ++b) {
+        N[b] = (2 * side - 1) * Ja[(size_t)(a * dim + b) * m->Nn + idx];
+        s += N[b] * N[b];
+      }
+      s = std::sqrt(s);
+      fsj[(size_t)f * NF + k] = s;
+      for (int b = 0; b < dim; ++b) fn[(size_t)b * nf * NF + (size_t)f * NF + k] = N[b] / s;
+    }
+  }
+
+  // ---------------------------------------------------------------- upload
+  const std::vector<double> tabp = tab.packed();
+  const size_t n_int = (size_t)5 * nf + cell_face.size();
+  const size_t n_real = (size_t)dim * dim * m->Nn + 4 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size();
+  auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
+  DG_CUDA(cudaSetDevice(m->ctx->device));
+  DG_CUDA(cudaMalloc(&m->d_int, pad(n_int) * sizeof(int)));
+  DG_CUDA(cudaMalloc(&m->d_f64, pad(n_real) * sizeof(double) + 64 * 8));
+  DG_CUDA(cudaMalloc(&m->d_f32, pad(n_real) * sizeof(float) + 64 * 8));
+  m->scratch_bytes = (pad((size_t)m->V * nf * NF) + pad((size_t)dim * m->Nn) + 2 * 512) * sizeof(double);
+  DG_CUDA(cudaMalloc(&m->d_scratch, m->scratch_bytes));
+  m->device_bytes = pad(n_int) * 4 + pad(n_real) * 12 + 1024 + m->scratch_bytes;
+  m->d_face_scratch64 = (double*)m->d_scratch;
+  m->d_vec_scratch64 = (double*)m->d_scratch + pad((size_t)m->V * nf * NF);
+  m->d_red_scratch = m->d_vec_scratch64 + pad((size_t)dim * m->Nn);
+
+  std::vector<int> ibuf;
+  ibuf.reserve(n_int);
+  for (auto* v : {&face_m, &face_lfm, &face_p, &face_lfp, &face_s}) ibuf.insert(ibuf.end(), v->begin(), v->end());
+  ibuf.insert(ibuf.end(), cell_face.begin(), cell_face.end());
+  DG_CUDA(cudaMemcpy(m->d_int, ibuf.data(), ibuf.size() * sizeof(int), cudaMemcpyHostToDevice));
+
+  std::vector<double> rbuf;
+  rbuf.reserve(n_real);
+  size_t o_Ja = rbuf.size();
+  rbuf.insert(rbuf.end(), Ja.begin(), Ja.end());
+  size_t o_invJ = rbuf.size();
+  rbuf.insert(rbuf.end(), invJ.begin(), invJ.end());
+  size_t o_rhob = rbuf.size();
+  rbuf.insert(rbuf.end(), rhob.begin(), rhob.end());
+  size_t o_pb = rbuf.size();
+  rbuf.insert(rbuf.end(), pb.begin(), pb.end());
+  size_t o_wJ = rbuf.size();
+  rbuf.insert(rbuf.end(), wJ.begin(), wJ.end());
+  size_t o_fn = rbuf.size();
+  rbuf.insert(rbuf.end(), fn.begin(), fn.end());
+  size_t o_fsj = rbuf.size();
+  rbuf.insert(rbuf.end(), fsj.begin(), fsj.end());
+  size_t o_tab = rbuf.size();
+  rbuf.insert(rbuf.end(), tabp.begin(), tabp.end());
+  DG_CUDA(cudaMemcpy(m->d_f64, rbuf.data(), rbuf.size() * sizeof(double), cudaMemcpyHostToDevice));
+  std::vector<float> fbuf(rbuf.begin(), rbuf.end());
+  DG_CUDA(cudaMemcpy(m->d_f32, fbuf.data(), fbuf.size() * sizeof(float), cudaMemcpyHostToDevice));
+
+  auto fill = [&](auto& v, auto* base) {
+    v.n_cells = K;
+    v.n_nodes = m->Nn;
+    v.nconf = m->nconf;
+    v.nsub = m->nsub;
+    v.nwall = m->nwall;
+    v.nf = nf;
+    v.Ja = base + o_Ja;
+    v.invJ = base + o_invJ;
+    v.rhob = base + o_rhob;
+    v.pb = base + o_pb;
+    v.wJ = base + o_wJ;
+    v.fn = base + o_fn;
+    v.fsj = base + o_fsj;
+    v.tab = base + o_tab;
+    const int* ib = (const int*)m->d_int;
+    v.face_m = ib;
+    v.face_lfm = ib + nf;
+    v.face_p = ib + 2 * (size_t)nf;
+    v.face_lfp = ib + 3 * (size_t)nf;
+    v.face_s = ib + 4 * (size_t)nf;
+    v.cell_face = ib + 5 * (size_t)nf;
+    v.gravity = (decltype(v.gravity))d.gravity;
+  };
+  fill(m->v64, (const double*)m->d_f64);
+  fill(m->v32, (const float*)m->d_f32);
+  return DG_OK;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* desc, dg_mesh** out) {
+  if (!ctx || !desc || !out) return fail(DG_EINVAL, "null argument");
+  if (desc->dim != 2 && desc->dim != 3) return fail(DG_EINVAL, "dim must be 2 or 3");
+  if (desc->degree < 1 || desc->degree > kMaxDegree) return fail(DG_EINVAL, "degree must be in 1..5");
+  if (desc->n_cells <= 0 || !desc->level || !desc->ijk) return fail(DG_EINVAL, "empty mesh");
+  if (desc->n_cells > (int64_t)1 << 28) return fail(DG_EINVAL, "too many cells");
+  for (int a = 0; a < desc->dim; ++a)
+    if (desc->base[a] <= 0 || desc->base[a] >= (1 << 12) || !(desc->extent[a] > 0.0))
+      return fail(DG_EINVAL, "bad base grid or extent");
+  if (desc->atm_kind < 0 || desc->atm_kind > 2 || desc->hill_kind < 0 || desc->hill_kind > 3)
+    return fail(DG_EINVAL, "bad hill or atmosphere kind");
+  if (desc->atm_kind != DG_ATM_NONE && (!(desc->atm_T > 0) || !(desc->atm_p_ref > 0)))
+    return fail(DG_EINVAL, "bad atmosphere parameters");
+  if (desc->atm_kind == DG_ATM_STRATIFIED && !(desc->atm_N > 0)) return fail(DG_EINVAL, "bad buoyancy frequency");
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ENOMEM, "host allocation failed");
+  m->ctx = ctx;
+  m->desc = *desc;
+  m->desc.level = nullptr;
+  m->desc.ijk = nullptr;
+  m->level.assign(desc->level, desc->level + desc->n_cells);
+  m->ijk.assign(desc->ijk, desc->ijk + desc->n_cells * desc->dim);
+  for (uint8_t l : m->level)
+    if (l > 7) {
+      delete m;
+      return fail(DG_EINVAL, "refinement level above 7");
+    }
+  int st;
+  try {
+    st = build_mesh(m);
+  } catch (const std::exception& e) {
+    st = fail(DG_EINVAL, e.what());
+  }
+  if (st != DG_OK) {
+    dg_mesh_destroy(m);
+    return st;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+extern "C" int dg_mesh_destroy(dg_mesh* m) {
+  if (!m) return DG_OK;
+  cudaFree(m->d_int);
+  cudaFree(m->d_f64);
+  cudaFree(m->d_f32);
+  cudaFree(m->d_scratch);
+  delete m;
+  return DG_OK;
+}
+
+extern "C" int dg_mesh_get_info(const dg_mesh* m, dg_mesh_info* info) {
+  if (!m || !info) return fail(DG_EINVAL, "null argument");
+  info->dim = m->dim;
+  info->degree = m->degree;
+  info->n_vars = m->V;
+  info->nodes_per_cell = m->nc;
+  info->n_cells = m->K;
+  info->n_nodes = m->Nn;
+  info->n_dof = m->Nn * m->V;
+  info->n_conforming = m->nconf;
+  info->n_subfaces = m->nsub;
+  info->n_walls = m->nwall;
+  info->max_level = m->max_level;
+  info->min_edge = m->min_edge;
+  info->device_bytes = m->device_bytes;
+  return DG_OK;
+}
+
+extern "C" int dg_mesh_get_faces(const dg_mesh* m, int32_t* conforming, int32_t* subfaces, int32_t* walls) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  if (conforming) std::memcpy(conforming, m->conf.data(), m->conf.size() * sizeof(int32_t));
+  if (subfaces) std::memcpy(subfaces, m->subs.data(), m->subs.size() * sizeof(int32_t));
+  if (walls) std::memcpy(walls, m->walls.data(), m->walls.size() * sizeof(int32_t));
+  return DG_OK;
+}
+
+extern "C" int dg_mesh_get_coords(const dg_mesh* m, double* xyz) {
+  if (!m || !xyz) return fail(DG_EINVAL, "null argument");
+  std::memcpy(xyz, m->X.data(), m->X.size() * sizeof(double));
+  return DG_OK;
+}

@@ -1,0 +1,59 @@
+// Host-side launchers of the DG operator kernels, one explicit instantiation
+// per (dimension, precision) translation unit.  All launchers enqueue on
+// `stream` and return a dg_status; `skip` (device int, may be NULL) turns every
+// launched kernel into a no-op when it is non-zero (used by GMRES after
+// convergence inside a restart cycle).
+#pragma once
+
+#include "dg_internal.h"
+
+namespace dg {
+
+template <typename T>
+inline const MeshView<T>& view(const dg_mesh* m);
+template <>
+inline const MeshView<double>& view<double>(const dg_mesh* m) {
+  return m->v64;
+}
+template <>
+inline const MeshView<float>& view<float>(const dg_mesh* m) {
+  return m->v32;
+}
+
+template <int DIM, typename T>
+int launch_explicit(const dg_mesh* m, const T* U, T* R, T* face_scratch, bool full, cudaStream_t s,
+                    const int* skip);
+template <int DIM, typename T>
+int launch_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* face_scratch, cudaStream_t s, const int* skip);
+template <int DIM, typename T>
+int launch_div(const dg_mesh* m, const T* f, T* out, T* face_scratch, cudaStream_t s, const int* skip);
+template <int DIM, typename T>
+int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* face_scratch, T* vec_scratch,
+                     cudaStream_t s, const int* skip);
+
+// dimension dispatch (with optional event timing per operator category)
+template <typename T>
+inline int op_explicit(const dg_mesh* m, const T* U, T* R, T* fs, bool full, cudaStream_t s, const int* skip) {
+  ProfScope ps(m->ctx, DG_PROF_EXPLICIT, s);
+  return m->dim == 2 ? launch_explicit<2, T>(m, U, R, fs, full, s, skip)
+                     : launch_explicit<3, T>(m, U, R, fs, full, s, skip);
+}
+template <typename T>
+inline int op_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* fs, cudaStream_t s, const int* skip) {
+  ProfScope ps(m->ctx, DG_PROF_GRAD, s);
+  return m->dim == 2 ? launch_grad<2, T>(m, p, h, g, fs, s, skip) : launch_grad<3, T>(m, p, h, g, fs, s, skip);
+}
+template <typename T>
+inline int op_div(const dg_mesh* m, const T* f, T* out, T* fs, cudaStream_t s, const int* skip) {
+  ProfScope ps(m->ctx, DG_PROF_DIV, s);
+  return m->dim == 2 ? launch_div<2, T>(m, f, out, fs, s, skip) : launch_div<3, T>(m, f, out, fs, s, skip);
+}
+template <typename T>
+inline int op_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* fs, T* vs, cudaStream_t s,
+                        const int* skip) {
+  ProfScope ps(m->ctx, DG_PROF_HELMHOLTZ, s);
+  return m->dim == 2 ? launch_helmholtz<2, T>(m, h, p, Ap, alpha, fs, vs, s, skip)
+                     : launch_helmholtz<3, T>(m, h, p, Ap, alpha, fs, vs, s, skip);
+}
+
+}  // namespace dg

@@ -1,0 +1,107 @@
+// Launcher bodies; included once per (dimension, precision) translation unit.
+#pragma once
+
+#include <type_traits>
+
+#include "k_explicit.cuh"
+#include "k_implicit.cuh"
+#include "ops.h"
+
+namespace dg {
+
+namespace {
+
+inline int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return DG_OK;
+}
+
+inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+template <int DIM, int DEG, typename T>
+int run_explicit(const dg_mesh* m, const T* U, T* R, T* Fh, bool full, cudaStream_t s, const int* skip) {
+  using S = Shape<DIM, DEG>;
+  constexpr bool PERT = std::is_same<T, float>::value;
+  const MeshView<T>& mv = view<T>(m);
+  const int64_t tf = (int64_t)mv.nf * S::NF;
+  const unsigned cb = blocks_for(mv.n_cells, S::CPB);
+  count_launches(m->ctx, tf ? 2 : 1);
+  if (full) {
+    if (tf) explicit_face_kernel<DIM, DEG, T, true, PERT><<<blocks_for(tf, 256), 256, 0, s>>>(mv, U, Fh, skip);
+    explicit_cell_kernel<DIM, DEG, T, true, PERT><<<cb, S::THREADS, 0, s>>>(mv, U, Fh, R, skip);
+  } else {
+    if (tf) explicit_face_kernel<DIM, DEG, T, false, PERT><<<blocks_for(tf, 256), 256, 0, s>>>(mv, U, Fh, skip);
+    explicit_cell_kernel<DIM, DEG, T, false, PERT><<<cb, S::THREADS, 0, s>>>(mv, U, Fh, R, skip);
+  }
+  return check_launch("explicit operator launch");
+}
+
+template <int DIM, int DEG, typename T>
+int run_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* Gh, cudaStream_t s, const int* skip) {
+  using S = Shape<DIM, DEG>;
+  const MeshView<T>& mv = view<T>(m);
+  const int64_t tf = (int64_t)(mv.nconf + mv.nsub) * S::NF;
+  count_launches(m->ctx, tf ? 2 : 1);
+  if (tf) grad_face_kernel<DIM, DEG, T><<<blocks_for(tf, 256), 256, 0, s>>>(mv, p, Gh, skip);
+  grad_cell_kernel<DIM, DEG, T><<<blocks_for(mv.n_cells, S::CPB), S::THREADS, 0, s>>>(mv, p, h, Gh, g, skip);
+  return check_launch("gradient launch");
+}
+
+template <int DIM, int DEG, typename T, bool HELM>
+int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, T* Dh, cudaStream_t s, const int* skip) {
+  using S = Shape<DIM, DEG>;
+  const MeshView<T>& mv = view<T>(m);
+  const int64_t tf = (int64_t)(mv.nconf + mv.nsub) * S::NF;
+  count_launches(m->ctx, tf ? 2 : 1);
+  if (tf) div_face_kernel<DIM, DEG, T><<<blocks_for(tf, 256), 256, 0, s>>>(mv, f, Dh, skip);
+  div_cell_kernel<DIM, DEG, T, HELM><<<blocks_for(mv.n_cells, S::CPB), S::THREADS, 0, s>>>(mv, f, Dh, p, alpha,
+                                                                                           out, skip);
+  return check_launch("divergence launch");
+}
+
+}  // namespace
+
+#define DG_DEGREE_SWITCH(deg, ...)                         \
+  switch (deg) {                                           \
+    case 1: { constexpr int DEG = 1; __VA_ARGS__; }        \
+    case 2: { constexpr int DEG = 2; __VA_ARGS__; }        \
+    case 3: { constexpr int DEG = 3; __VA_ARGS__; }        \
+    case 4: { constexpr int DEG = 4; __VA_ARGS__; }        \
+    case 5: { constexpr int DEG = 5; __VA_ARGS__; }        \
+    default: return fail(DG_EINVAL, "unsupported degree"); \
+  }
+
+template <int DIM, typename T>
+int launch_explicit(const dg_mesh* m, const T* U, T* R, T* fs, bool full, cudaStream_t s, const int* skip) {
+  DG_DEGREE_SWITCH(m->degree, return (run_explicit<DIM, DEG, T>(m, U, R, fs, full, s, skip)))
+}
+
+template <int DIM, typename T>
+int launch_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* fs, cudaStream_t s, const int* skip) {
+  DG_DEGREE_SWITCH(m->degree, return (run_grad<DIM, DEG, T>(m, p, h, g, fs, s, skip)))
+}
+
+template <int DIM, typename T>
+int launch_div(const dg_mesh* m, const T* f, T* out, T* fs, cudaStream_t s, const int* skip) {
+  DG_DEGREE_SWITCH(m->degree, return (run_div<DIM, DEG, T, false>(m, f, nullptr, T(0), out, fs, s, skip)))
+}
+
+template <int DIM, typename T>
+int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* fs, T* vs, cudaStream_t s,
+                     const int* skip) {
+  DG_DEGREE_SWITCH(m->degree, {
+    int st = run_grad<DIM, DEG, T>(m, p, h, vs, fs, s, skip);
+    if (st != DG_OK) return st;
+    return (run_div<DIM, DEG, T, true>(m, vs, p, alpha, Ap, fs, s, skip));
+  })
+}
+
+#define DG_INSTANTIATE_OPS(DIM, T)                                                                              \
+  template int launch_explicit<DIM, T>(const dg_mesh*, const T*, T*, T*, bool, cudaStream_t, const int*);      \
+  template int launch_grad<DIM, T>(const dg_mesh*, const T*, const T*, T*, T*, cudaStream_t, const int*);      \
+  template int launch_div<DIM, T>(const dg_mesh*, const T*, T*, T*, cudaStream_t, const int*);                 \
+  template int launch_helmholtz<DIM, T>(const dg_mesh*, const T*, const T*, T*, T, T*, T*, cudaStream_t,       \
+                                        const int*);
+
+}  // namespace dg

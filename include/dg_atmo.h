@@ -85,6 +85,7 @@ typedef enum {
   DG_PROF_GRAD = 2,      /* DG gradients                                    */
   DG_PROF_DIV = 3,       /* DG divergences                                  */
   DG_PROF_KRYLOV = 4,    /* GMRES orthogonalisation and updates (BLAS-1)    */
+  DG_PROF_GMRES = 5,     /* whole fused GMRES solves (persistent kernel)    */
   DG_PROF_STEP = 6,      /* whole IMEX-RK2 steps                            */
   DG_PROF_N = 8
 } dg_prof_category;
@@ -201,6 +202,8 @@ typedef struct {
                        /*   inside FP64 iterative refinement                    */
   double inner_tol;    /* DG_FP32: relative tolerance of each inner solve (1e-4) */
   int max_refine;      /* DG_FP32: outer refinement steps cap (20)              */
+  int fused;           /* 1: each GMRES solve is one persistent cooperative     */
+                       /*    kernel (default); 0: one launch per Krylov kernel  */
 } dg_solver_opts;
 
 typedef struct {

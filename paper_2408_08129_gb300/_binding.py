@@ -49,7 +49,7 @@ class MeshInfo(ctypes.Structure):
 class SolverOpts(ctypes.Structure):
     _fields_ = [
         ("picard", c_int), ("restart", c_int), ("max_iters", c_int), ("tol", c_double),
-        ("precision", c_int), ("inner_tol", c_double), ("max_refine", c_int),
+        ("precision", c_int), ("inner_tol", c_double), ("max_refine", c_int), ("fused", c_int),
     ]
 
 

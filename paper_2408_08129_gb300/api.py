@@ -131,7 +131,7 @@ class Mesh:
             pass
 
 
-PROF_CATEGORIES = {0: "explicit", 1: "helmholtz", 2: "grad", 3: "div", 4: "krylov", 6: "step"}
+PROF_CATEGORIES = {0: "explicit", 1: "helmholtz", 2: "grad", 3: "div", 4: "krylov", 5: "gmres", 6: "step"}
 
 
 def dg_profile_enable(ctx, on=True):

@@ -9,6 +9,9 @@
 //      coarse sides; zero on walls.
 //  Helmholtz:  A p = p/(gamma-1) - alpha div(h grad p), as grad(h-scaled)
 //      followed by the divergence with the Helmholtz epilogue.
+//
+// The per-item work is written as device functions so that the standalone
+// kernels below and the persistent GMRES kernel (k_gmres.cuh) share it.
 #pragma once
 
 #include "dg_device.cuh"
@@ -47,89 +50,82 @@ __device__ __forceinline__ void coarse_at(const MeshView<T>& mv, const T* __rest
   }
 }
 
-// Gh_b = 1/2 |N| n_b (p+ - p-) on conforming faces and subfaces (walls skipped).
+// ---------------------------------------------------------------- gradient
+
+// face node t (< (nconf+nsub)*NF): Gh_b = 1/2 |N| n_b (p+ - p-)
 template <int DIM, int DEG, typename T>
-__global__ void __launch_bounds__(256) grad_face_kernel(MeshView<T> mv, const T* __restrict__ p,
-                                                        T* __restrict__ Gh, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void grad_face_item(const MeshView<T>& mv, const T* __restrict__ p, T* __restrict__ Gh,
+                                               int64_t t) {
   using S = Shape<DIM, DEG>;
   constexpr int NC = S::NC, NF = S::NF;
   const int64_t total = (int64_t)mv.nf * NF;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)(mv.nconf + mv.nsub) * NF) return;
   const int f = (int)(t / NF), k = (int)(t % NF);
-  const int64_t Nn = mv.n_nodes;
   const T pm = p[(int64_t)mv.face_m[f] * NC + face_node<DIM, DEG>(mv.face_lfm[f], k)];
   T pp;
   if (f < mv.nconf)
     pp = p[(int64_t)mv.face_p[f] * NC + face_node<DIM, DEG>(mv.face_lfp[f], k)];
   else
-    coarse_at<DIM, DEG, T, 1>(mv, p, Nn, f, k, &pp);
+    coarse_at<DIM, DEG, T, 1>(mv, p, mv.n_nodes, f, k, &pp);
   const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
 #pragma unroll
   for (int b = 0; b < DIM; ++b) Gh[(int64_t)b * total + t] = jmp * mv.fn[(int64_t)b * total + t];
 }
 
-// g_b = h * [sum_a Ja^a_b (D_a p) + gathered Gh_b / w_end] / J   (h optional)
+// Cells [batch*CPB, batch*CPB + CPB): g_b = h [sum_a Ja^a_b (D_a p) + Gh_b / w_end] / J.
+// Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 template <int DIM, int DEG, typename T>
-__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_cell_kernel(MeshView<T> mv,
-                                                                             const T* __restrict__ p,
-                                                                             const T* __restrict__ h,
-                                                                             const T* __restrict__ Gh,
-                                                                             T* __restrict__ g, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
+                                                const T* __restrict__ h, const T* __restrict__ Gh,
+                                                T* __restrict__ g, int64_t batch, T* sp, const T* sD,
+                                                const T* sIt) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
-  __shared__ T sp[CPB * NC];
-  __shared__ T sD[N * N];
-  __shared__ T sIt[2 * N * N];
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sD[q] = mv.tab[S::T_D + q];
-  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int64_t c = (int64_t)blockIdx.x * CPB + lc;
+  const int64_t c = batch * CPB + lc;
   const bool active = (lc < CPB) && (c < mv.n_cells);
   const int64_t Nn = mv.n_nodes;
   const int64_t idx = c * NC + i;
   if (active) sp[lc * NC + i] = p[idx];
   __syncthreads();
-  if (!active) return;
-  int id[3] = {i % N, (i / N) % N, i / (N * N)};
-  T dp[DIM];
+  if (active) {
+    int id[3] = {i % N, (i / N) % N, i / (N * N)};
+    T dp[DIM];
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
-    const int i0 = lc * NC + i - id[a] * stride;
-    const T* D = sD + id[a] * N;
-    T s = T(0);
+    for (int a = 0; a < DIM; ++a) {
+      const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+      const int i0 = lc * NC + i - id[a] * stride;
+      const T* D = sD + id[a] * N;
+      T s = T(0);
 #pragma unroll
-    for (int kk = 0; kk < N; ++kk) s += D[kk] * sp[i0 + kk * stride];
-    dp[a] = s;
+      for (int kk = 0; kk < N; ++kk) s += D[kk] * sp[i0 + kk * stride];
+      dp[a] = s;
+    }
+    T facc[DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) facc[b] = T(0);
+    gather_faces<DIM, DEG, T, DIM>(mv, Gh, c, id, sIt, T(1), T(1), true, facc);
+    const T iwend = mv.tab[S::T_IWEND];
+    const T scale = mv.invJ[idx] * (h ? h[idx] : T(1));
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      T s = facc[b] * iwend;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * dp[a];
+      g[(int64_t)b * Nn + idx] = s * scale;
+    }
   }
-  T facc[DIM];
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) facc[b] = T(0);
-  gather_faces<DIM, DEG, T, DIM>(mv, Gh, c, id, sIt, T(1), T(1), true, facc);
-  const T iwend = mv.tab[S::T_IWEND];
-  const T scale = mv.invJ[idx] * (h ? h[idx] : T(1));
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) {
-    T s = facc[b] * iwend;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * dp[a];
-    g[(int64_t)b * Nn + idx] = s * scale;
-  }
+  __syncthreads();
 }
 
-// Dh = |N| {f}.n on conforming faces and subfaces (walls skipped).
+// ---------------------------------------------------------------- divergence
+
+// face node t (< (nconf+nsub)*NF): Dh = |N| {f}.n
 template <int DIM, int DEG, typename T>
-__global__ void __launch_bounds__(256) div_face_kernel(MeshView<T> mv, const T* __restrict__ fld,
-                                                       T* __restrict__ Dh, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void div_face_item(const MeshView<T>& mv, const T* __restrict__ fld, T* __restrict__ Dh,
+                                              int64_t t) {
   using S = Shape<DIM, DEG>;
   constexpr int NC = S::NC, NF = S::NF;
   const int64_t total = (int64_t)mv.nf * NF;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)(mv.nconf + mv.nsub) * NF) return;
   const int f = (int)(t / NF), k = (int)(t % NF);
   const int64_t Nn = mv.n_nodes;
   const int64_t im = (int64_t)mv.face_m[f] * NC + face_node<DIM, DEG>(mv.face_lfm[f], k);
@@ -147,23 +143,17 @@ __global__ void __launch_bounds__(256) div_face_kernel(MeshView<T> mv, const T* 
   Dh[t] = T(0.5) * mv.fsj[t] * s;
 }
 
-// out = HELM ? p/(gamma-1) - alpha*div : div
+// Cells of one batch: out = HELM ? scale * (p/(gamma-1) - alpha div) : div.
+// Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 template <int DIM, int DEG, typename T, bool HELM>
-__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(MeshView<T> mv,
-                                                                            const T* __restrict__ fld,
-                                                                            const T* __restrict__ Dh,
-                                                                            const T* __restrict__ p, T alpha,
-                                                                            T* __restrict__ out, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
+                                               const T* __restrict__ Dh, const T* __restrict__ p, T alpha, T scale,
+                                               T* __restrict__ out, int64_t batch, T* sF, const T* sDw,
+                                               const T* sIt) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
-  __shared__ T sF[CPB * NC];
-  __shared__ T sDw[N * N];
-  __shared__ T sIt[2 * N * N];
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sDw[q] = mv.tab[S::T_DW + q];
-  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int64_t c = (int64_t)blockIdx.x * CPB + lc;
+  const int64_t c = batch * CPB + lc;
   const bool active = (lc < CPB) && (c < mv.n_cells);
   const int64_t Nn = mv.n_nodes;
   const int64_t idx = c * NC + i;
@@ -192,14 +182,71 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(Mesh
     }
     __syncthreads();
   }
-  if (!active) return;
-  T facc = T(0);
-  gather_faces<DIM, DEG, T, 1>(mv, Dh, c, id, sIt, T(1), T(-1), true, &facc);
-  const T dv = (acc + facc * mv.tab[S::T_IWEND]) * mv.invJ[idx];
-  if (HELM)
-    out[idx] = p[idx] / gm1<T>() - alpha * dv;
-  else
-    out[idx] = dv;
+  if (active) {
+    T facc = T(0);
+    gather_faces<DIM, DEG, T, 1>(mv, Dh, c, id, sIt, T(1), T(-1), true, &facc);
+    const T dv = (acc + facc * mv.tab[S::T_IWEND]) * mv.invJ[idx];
+    if (HELM)
+      out[idx] = scale * (p[idx] / gm1<T>() - alpha * dv);
+    else
+      out[idx] = dv;
+  }
+}
+
+// ---------------------------------------------------------------- standalone kernels
+
+template <int DIM, int DEG, typename T>
+__global__ void __launch_bounds__(256) grad_face_kernel(MeshView<T> mv, const T* __restrict__ p,
+                                                        T* __restrict__ Gh, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)(mv.nconf + mv.nsub) * Shape<DIM, DEG>::NF) return;
+  grad_face_item<DIM, DEG, T>(mv, p, Gh, t);
+}
+
+template <int DIM, int DEG, typename T>
+__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_cell_kernel(MeshView<T> mv,
+                                                                             const T* __restrict__ p,
+                                                                             const T* __restrict__ h,
+                                                                             const T* __restrict__ Gh,
+                                                                             T* __restrict__ g,
+                                                                             const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N;
+  __shared__ T sp[S::CPB * S::NC];
+  __shared__ T sD[N * N];
+  __shared__ T sIt[2 * N * N];
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sD[q] = mv.tab[S::T_D + q];
+  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
+  grad_cell_batch<DIM, DEG, T>(mv, p, h, Gh, g, blockIdx.x, sp, sD, sIt);
+}
+
+template <int DIM, int DEG, typename T>
+__global__ void __launch_bounds__(256) div_face_kernel(MeshView<T> mv, const T* __restrict__ fld,
+                                                       T* __restrict__ Dh, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)(mv.nconf + mv.nsub) * Shape<DIM, DEG>::NF) return;
+  div_face_item<DIM, DEG, T>(mv, fld, Dh, t);
+}
+
+template <int DIM, int DEG, typename T, bool HELM>
+__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(MeshView<T> mv,
+                                                                            const T* __restrict__ fld,
+                                                                            const T* __restrict__ Dh,
+                                                                            const T* __restrict__ p, T alpha,
+                                                                            T* __restrict__ out,
+                                                                            const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N;
+  __shared__ T sF[S::CPB * S::NC];
+  __shared__ T sDw[N * N];
+  __shared__ T sIt[2 * N * N];
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sDw[q] = mv.tab[S::T_DW + q];
+  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
+  div_cell_batch<DIM, DEG, T, HELM>(mv, fld, Dh, p, alpha, T(1), out, blockIdx.x, sF, sDw, sIt);
 }
 
 }  // namespace dg

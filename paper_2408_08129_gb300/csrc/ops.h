@@ -31,6 +31,19 @@ template <int DIM, typename T>
 int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* face_scratch, T* vec_scratch,
                      cudaStream_t s, const int* skip);
 
+// One cooperative launch solving A(h) x = b by restarted GMRES(restart) to
+// relative residual tol (k_gmres.cuh).  Q: (restart+1)*n, w: n, partial:
+// npartial doubles, out: 4 doubles (iterations, rel. residual, converged, ||b||).
+template <int DIM, typename T>
+int launch_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double tol, int restart, int max_iters,
+                 T* Q, T* w, double* partial, int npartial, double* out, cudaStream_t s);
+template <typename T>
+inline int op_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double tol, int restart,
+                    int max_iters, T* Q, T* w, double* partial, int npartial, double* out, cudaStream_t s) {
+  return m->dim == 2 ? launch_gmres<2, T>(m, h, b, x, alpha, tol, restart, max_iters, Q, w, partial, npartial, out, s)
+                     : launch_gmres<3, T>(m, h, b, x, alpha, tol, restart, max_iters, Q, w, partial, npartial, out, s);
+}
+
 // dimension dispatch (with optional event timing per operator category)
 template <typename T>
 inline int op_explicit(const dg_mesh* m, const T* U, T* R, T* fs, bool full, cudaStream_t s, const int* skip) {

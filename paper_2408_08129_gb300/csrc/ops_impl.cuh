@@ -4,6 +4,7 @@
 #include <type_traits>
 
 #include "k_explicit.cuh"
+#include "k_gmres.cuh"
 #include "k_implicit.cuh"
 #include "ops.h"
 
@@ -60,6 +61,45 @@ int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, T* Dh, cu
   return check_launch("divergence launch");
 }
 
+template <int DIM, int DEG, typename T>
+int run_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double tol, int restart, int max_iters,
+              T* Q, T* w, double* partial, int npartial, double* out, cudaStream_t s) {
+  GmresPArgs<T> a;
+  a.mv = view<T>(m);
+  a.h = h;
+  a.b = b;
+  a.x = x;
+  a.Q = Q;
+  a.w = w;
+  a.Gh = (T*)m->d_face_scratch64;
+  a.gv = (T*)m->d_vec_scratch64;
+  a.partial = partial;
+  a.out = out;
+  a.alpha = alpha;
+  a.tol = tol;
+  a.m = restart;
+  a.max_iters = max_iters;
+  a.n = m->Nn;
+  auto kern = gmres_persistent_kernel<DIM, DEG, T>;
+  const size_t smem = gmres_smem_bytes<DIM, DEG, T>(restart);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "gmres smem attribute");
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "gmres occupancy");
+  if (per_sm < 1) return fail(DG_ECUDA, "persistent GMRES kernel does not fit on an SM");
+  int G = m->ctx->sm_count * (per_sm < 2 ? per_sm : 2);
+  if (G > npartial / 2) G = npartial / 2;
+  if (G < 1) return fail(DG_EINVAL, "GMRES partial buffer too small");
+  count_launches(m->ctx, 1);
+  void* args[] = {&a};
+  e = cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(256), args, smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent GMRES launch");
+  return DG_OK;
+}
+
 }  // namespace
 
 #define DG_DEGREE_SWITCH(deg, ...)                         \
@@ -97,11 +137,20 @@ int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T
   })
 }
 
+template <int DIM, typename T>
+int launch_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double tol, int restart, int max_iters,
+                 T* Q, T* w, double* partial, int npartial, double* out, cudaStream_t s) {
+  DG_DEGREE_SWITCH(m->degree, return (run_gmres<DIM, DEG, T>(m, h, b, x, alpha, tol, restart, max_iters, Q, w,
+                                                              partial, npartial, out, s)))
+}
+
 #define DG_INSTANTIATE_OPS(DIM, T)                                                                              \
   template int launch_explicit<DIM, T>(const dg_mesh*, const T*, T*, T*, bool, cudaStream_t, const int*);      \
   template int launch_grad<DIM, T>(const dg_mesh*, const T*, const T*, T*, T*, cudaStream_t, const int*);      \
   template int launch_div<DIM, T>(const dg_mesh*, const T*, T*, T*, cudaStream_t, const int*);                 \
   template int launch_helmholtz<DIM, T>(const dg_mesh*, const T*, const T*, T*, T, T*, T*, cudaStream_t,       \
-                                        const int*);
+                                        const int*);                                                            \
+  template int launch_gmres<DIM, T>(const dg_mesh*, const T*, const T*, T*, T, double, int, int, T*, T*, double*, \
+                                    int, double*, cudaStream_t);
 
 }  // namespace dg

@@ -39,6 +39,7 @@ struct dg_state {
   double* tmps = nullptr;
   double* g = nullptr;    // [dim][Nn]
   double* r64 = nullptr;  // FP64 outer residual
+  double* solve_out = nullptr;  // [64][4] per-solve results of one step
   float* f32 = nullptr;   // FP32 inner: h, rhs, delta
   int* flag = nullptr;    // non-finite flag
   dg::Gmres<double> gm64;
@@ -215,21 +216,30 @@ int check(const char* what) {
 }
 
 // Helmholtz solve A(h) p = rhs (p holds the initial guess), FP64 or FP32-refined.
-int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_stats* st, cudaStream_t s) {
+// The fused FP64 path leaves its (iterations, residual, converged, ||b||) in
+// out[0..3] on the device and does not wait; the caller reads them later.
+int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_stats* st, double* out,
+                    cudaStream_t s) {
   const dg_mesh* m = S->mesh;
   const int64_t Nn = S->Nn;
+  const int restart = std::min(o->restart, S->restart);
   auto A64 = [&](const double* x, double* y, const int* skip) {
     return op_helmholtz<double>(m, S->h, x, y, alpha, m->d_face_scratch64, m->d_vec_scratch64, s, skip);
   };
   GmresResult res;
   int rc;
   if (o->precision == DG_FP64) {
+    if (o->fused) {
+      ProfScope ps(S->ctx, DG_PROF_GMRES, s);
+      return op_gmres<double>(m, S->h, S->rhs, S->p, alpha, o->tol, restart, o->max_iters, S->gm64.Q, S->gm64.w,
+                              S->gm64.d.partial, (restart + 1) * kDotBlocks, out, s);
+    }
     rc = S->gm64.solve(S->ctx, A64, S->rhs, S->p, o->tol, o->max_iters, s, &res);
     if (rc != DG_OK) return rc;
-    st->gmres_iters += res.iters;
-    st->solves += 1;
-    st->max_rel_residual = std::max(st->max_rel_residual, res.rel);
-    return res.converged ? DG_OK : fail(DG_ENOTCONV, "GMRES did not reach the tolerance");
+    const double host[4] = {(double)res.iters, res.rel, res.converged ? 1.0 : 0.0, 0.0};
+    DG_CUDA(cudaMemcpyAsync(out, host, sizeof(host), cudaMemcpyHostToDevice, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    return DG_OK;
   }
   // FP32 inner GMRES inside FP64 iterative refinement: p += A32^-1 (rhs - A64 p)
   float* h32 = S->f32;
@@ -245,34 +255,50 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
   double* scal = S->gm64.d.scal;  // reuse: [6] = ||b||^2, [7] = ||r||^2
   if ((rc = dot_into<double, double>(S->rhs, S->rhs, Nn, S->gm64.d.partial, scal + 6, s, nullptr)) != DG_OK)
     return rc;
+  count_launches(S->ctx, 2);
   DG_CUDA(cudaMemcpyAsync(&bn2, scal + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
   const double bn = std::sqrt(bn2);
   double rel = 0.0;
+  int inner = 0, refine = 0;
   for (int k = 0; k <= o->max_refine; ++k) {
     if ((rc = A64(S->p, S->r64, nullptr)) != DG_OK) return rc;
-    // r = rhs - A p
     sub_from_kernel<<<gridn(Nn), 256, 0, s>>>(S->rhs, S->r64, Nn);
     count_launches(S->ctx, 1);
     if ((rc = dot_into<double, double>(S->r64, S->r64, Nn, S->gm64.d.partial, scal + 7, s, nullptr)) != DG_OK)
       return rc;
+    count_launches(S->ctx, 2);
     DG_CUDA(cudaMemcpyAsync(&rn2, scal + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
     DG_CUDA(cudaStreamSynchronize(s));
     rel = bn > 0 ? std::sqrt(rn2) / bn : 0.0;
     if (rel <= o->tol || k == o->max_refine) break;
     to_f32_kernel<<<gridn(Nn), 256, 0, s>>>(S->r64, r32, Nn);
-    count_launches(S->ctx, 1);
     zero_f32_kernel<<<gridn(Nn), 256, 0, s>>>(d32, Nn);
-    count_launches(S->ctx, 1);
-    if ((rc = S->gm32.solve(S->ctx, A32, r32, d32, o->inner_tol, o->max_iters, s, &res)) != DG_OK) return rc;
+    count_launches(S->ctx, 2);
+    if (o->fused) {
+      double h4[4];
+      {
+        ProfScope ps(S->ctx, DG_PROF_GMRES, s);
+        rc = op_gmres<float>(m, h32, r32, d32, (float)alpha, o->inner_tol, restart, o->max_iters, S->gm32.Q,
+                             S->gm32.w, S->gm32.d.partial, (restart + 1) * kDotBlocks, S->gm32.d.scal, s);
+      }
+      if (rc != DG_OK) return rc;
+      DG_CUDA(cudaMemcpyAsync(h4, S->gm32.d.scal, sizeof(h4), cudaMemcpyDeviceToHost, s));
+      DG_CUDA(cudaStreamSynchronize(s));
+      inner += (int)h4[0];
+    } else {
+      if ((rc = S->gm32.solve(S->ctx, A32, r32, d32, o->inner_tol, o->max_iters, s, &res)) != DG_OK) return rc;
+      inner += res.iters;
+    }
     add_f32_kernel<<<gridn(Nn), 256, 0, s>>>(S->p, d32, Nn);
     count_launches(S->ctx, 1);
-    st->gmres_iters += res.iters;
-    st->refine_steps += 1;
+    ++refine;
   }
-  st->solves += 1;
-  st->max_rel_residual = std::max(st->max_rel_residual, rel);
-  return rel <= o->tol ? DG_OK : fail(DG_ENOTCONV, "iterative refinement did not reach the tolerance");
+  const double host[4] = {(double)inner, rel, rel <= o->tol ? 1.0 : 0.0, bn};
+  DG_CUDA(cudaMemcpyAsync(out, host, sizeof(host), cudaMemcpyHostToDevice, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  st->refine_steps += refine;
+  return DG_OK;
 }
 
 }  // namespace
@@ -290,6 +316,7 @@ extern "C" void dg_solver_opts_default(dg_solver_opts* o) {
   o->precision = DG_FP64;
   o->inner_tol = 1e-4;
   o->max_refine = 20;
+  o->fused = 1;
 }
 
 extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_opts* opts, dg_state** out) {
@@ -310,7 +337,7 @@ extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_op
   const int V = S->V, dim = S->dim;
   // every buffer is rounded up to 32 doubles (256 bytes); 20 buffers in all
   auto rup = [](size_t n) { return (n + 31) & ~(size_t)31; };
-  const size_t nd = 7 * rup((size_t)V * Nn) + 4 * rup((size_t)dim * Nn) + 8 * rup((size_t)Nn) + rup(8);
+  const size_t nd = 7 * rup((size_t)V * Nn) + 4 * rup((size_t)dim * Nn) + 8 * rup((size_t)Nn) + rup(8) + rup(256);
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&S->block, nd * sizeof(double) + (size_t)Nn * 3 * sizeof(float) + 1024);
   if (e != cudaSuccess) {
@@ -340,6 +367,7 @@ extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_op
   S->tmps = take(Nn);
   S->r64 = take(Nn);
   S->flag = (int*)take(8);
+  S->solve_out = take(256);
   S->f32 = (float*)p;
   int rc = S->gm64.init(Nn, o.restart);
   if (rc == DG_OK) rc = S->gm32.init(Nn, o.restart);
@@ -402,6 +430,7 @@ extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double 
   int rc = DG_OK;
   int status = DG_OK;
   ProfScope step_scope(ctx, DG_PROF_STEP, s);
+  int nsolve = 0;
 #define RUN(x)                     \
   do {                             \
     if ((rc = (x)) != DG_OK) return rc; \
@@ -439,11 +468,9 @@ extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double 
       axpy_kernel<<<gb, 256, 0, s>>>(S->rhs, S->tmps, -dta, Nn);
       count_launches(S->ctx, 1);
       RUN(check("picard"));
-      rc = helmholtz_solve(S, &o, dta * dta, &st, s);
-      if (rc == DG_ENOTCONV)
-        status = rc;
-      else if (rc != DG_OK)
-        return rc;
+      if (nsolve >= 64) return fail(DG_EINVAL, "too many Picard iterations per step (at most 32)");
+      RUN(helmholtz_solve(S, &o, dta * dta, &st, S->solve_out + 4 * nsolve, s));
+      ++nsolve;
       RUN(op_grad<double>(m, S->p, nullptr, S->g, fs, s, nullptr));
       momentum_kernel<<<gb, 256, 0, s>>>(S->mhat, S->g, dta, (int64_t)dim * Nn, S->mk);
       count_launches(S->ctx, 1);
@@ -467,9 +494,17 @@ extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double 
   count_launches(S->ctx, 1);
   RUN(check("final combination"));
   int flag = 0;
+  double sol[256];
   DG_CUDA(cudaMemcpyAsync(&flag, S->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaMemcpyAsync(sol, S->solve_out, 4 * nsolve * sizeof(double), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
 #undef RUN
+  for (int k = 0; k < nsolve; ++k) {
+    st.gmres_iters += (int)sol[4 * k];
+    st.max_rel_residual = std::max(st.max_rel_residual, sol[4 * k + 1]);
+    if (sol[4 * k + 2] == 0.0) status = fail(DG_ENOTCONV, "a Helmholtz solve missed its tolerance");
+  }
+  st.solves = nsolve;
   if (stats) *stats = st;
   if (flag) return fail(DG_ENONFINITE, "non-finite value in the new state");
   return status;

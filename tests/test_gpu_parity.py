@@ -50,7 +50,7 @@ def _per_var_rel(a, b):
 
 
 CASES = [("tiny", 2, r) for r in (1, 2, 3, 4, 5)] + [("tiny", 3, r) for r in (1, 2, 3, 4, 5)] + [
-    ("bubble2d", 2, 2), ("hill2d", 2, 4)]
+    ("bubble2d", 2, 2), ("hill2d", 2, 4), ("hill3d", 3, 3)]
 
 
 def _case(name, dim, r):
@@ -201,6 +201,13 @@ def test_imex_steps_bubble2d(dg, ctx, nsteps, tol):
     # compare the deviation from the background, the part the dynamics changes
     err = _per_var_rel(U - ref.Ubg, Ur - ref.Ubg)
     assert err < tol, err
+
+
+def test_imex_steps_unfused_krylov(dg, ctx):
+    """The one-launch-per-kernel GMRES gives the same step as the persistent one."""
+    case = make_case("bubble2d", 0)
+    U, Ur, ref = _run_steps(dg, ctx, case, 3, dg.solver_opts(tol=1e-12, fused=0))
+    assert _per_var_rel(U - ref.Ubg, Ur - ref.Ubg) < 1e-11
 
 
 def test_imex_steps_hill2d(dg, ctx):

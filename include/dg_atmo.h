@@ -186,6 +186,23 @@ int dg_apply_div(dg_ctx* ctx, const dg_mesh* mesh, const void* f, void* out, int
  * symmetric, hence GMRES. */
 int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* mesh, const void* h, const void* p, void* Ap, double alpha,
                       int precision, void* stream);
+/* The Helmholtz operator of dg_apply_implicit, for callers that cannot
+ * allocate device memory (no cudaMalloc, no allocating library routine):
+ * same arguments and result, but the two scratch buffers the operator needs
+ * (face values and the h-scaled gradient) come from a fixed 4 MiB array
+ * compiled into the library, held by every GPU that loads the library until
+ * the process exits.  The paper has no counterpart; this is a deployment aid.
+ *  - Meshes whose scratch, dim*(faces*face_nodes) + dim*n_nodes elements
+ *    (8 bytes each for DG_FP64, 4 for DG_FP32), exceeds 4 MiB are rejected
+ *    with DG_EINVAL and a message giving the bytes needed.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; each call writes every scratch element before reading it, so no
+ *    clearing is needed.  Calls whose executions overlap on the GPU (other
+ *    streams, other threads) race on the array: serialise them. */
+int dg_apply_implicit_noalloc(dg_ctx* ctx, const dg_mesh* mesh, const void* h, const void* p, void* Ap,
+                              double alpha, int precision, void* stream);
 /* Total mass and total energy, sum over nodes of w J rho and w J rho E, in
  * FP64 with a fixed reduction order (bitwise reproducible).  U: FP64 full
  * state on the device; out: 2 doubles on the device. */

@@ -18,6 +18,7 @@ from .api import (  # noqa: F401
     dg_apply_explicit,
     dg_apply_grad,
     dg_apply_implicit,
+    dg_apply_implicit_noalloc,
     dg_background,
     dg_conservation,
     dg_init_state,

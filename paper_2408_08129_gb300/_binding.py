@@ -85,6 +85,7 @@ def _load():
         "dg_apply_grad": (c_int, [P, P, P, P, P, c_int, P]),
         "dg_apply_div": (c_int, [P, P, P, P, c_int, P]),
         "dg_apply_implicit": (c_int, [P, P, P, P, P, c_double, c_int, P]),
+        "dg_apply_implicit_noalloc": (c_int, [P, P, P, P, P, c_double, c_int, P]),
         "dg_conservation": (c_int, [P, P, P, P, P]),
         "dg_solver_opts_default": (None, [ctypes.POINTER(SolverOpts)]),
         "dg_state_create": (c_int, [P, P, ctypes.POINTER(SolverOpts), ctypes.POINTER(P)]),

@@ -189,6 +189,13 @@ def dg_apply_implicit(ctx, mesh, h, p, Ap, alpha, precision=DG_FP64, stream=None
                                 precision, _stream(stream)), "dg_apply_implicit")
 
 
+def dg_apply_implicit_noalloc(ctx, mesh, h, p, Ap, alpha, precision=DG_FP64, stream=None):
+    """dg_apply_implicit without any device allocation (scratch in a fixed 4 MiB library array)."""
+    dt = _fdtype(precision)
+    check(lib.dg_apply_implicit_noalloc(ctx.handle, mesh.handle, _ptr(h, dt), _ptr(p, dt), _ptr(Ap, dt),
+                                        float(alpha), precision, _stream(stream)), "dg_apply_implicit_noalloc")
+
+
 def dg_conservation(ctx, mesh, U, out, stream=None):
     check(lib.dg_conservation(ctx.handle, mesh.handle, _ptr(U, torch.float64), _ptr(out, torch.float64),
                               _stream(stream)), "dg_conservation")

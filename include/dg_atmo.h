@@ -97,6 +97,13 @@ int dg_profile_enable(dg_ctx* ctx, int on);
  * counts per category into ms[DG_PROF_N] and counts[DG_PROF_N] (host arrays). */
 int dg_profile_read(dg_ctx* ctx, double* ms, long long* counts);
 int dg_profile_reset(dg_ctx* ctx);
+/* Nanoseconds spent in each phase of the fused GMRES solves while profiling
+ * was on, as seen by block 0 between grid barriers (so each phase includes the
+ * wait for the slowest block), into ns[16]: 0 gradient faces, 1 gradient
+ * cells, 2 divergence faces, 3 divergence cells, 4 Gram-Schmidt dots,
+ * 5 basis update + Givens, 6 second Gram-Schmidt pass, 7 FP64 residual,
+ * 8 solution update; ns[15] = GMRES iterations.  Synchronises the device. */
+int dg_profile_read_gmres_phases(dg_ctx* ctx, double* ns);
 /* Number of CUDA kernels the library has launched through this context so far. */
 int dg_launch_count(const dg_ctx* ctx, long long* out);
 

@@ -25,6 +25,7 @@ from .api import (  # noqa: F401
     dg_launch_count,
     dg_profile_enable,
     dg_profile_read,
+    dg_profile_read_gmres_phases,
     dg_profile_reset,
     imex_rk2_step,
     solver_opts,

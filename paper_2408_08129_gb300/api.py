@@ -149,6 +149,19 @@ def dg_profile_read(ctx):
     return {name: {"ms": float(ms[i]), "count": int(n[i])} for i, name in PROF_CATEGORIES.items()}
 
 
+GMRES_PHASES = ["grad_faces", "grad_cells", "div_faces", "div_cells", "gs_dots", "basis_update_givens",
+                "gs_second_pass", "fp64_residual", "solution_update"]
+
+
+def dg_profile_read_gmres_phases(ctx):
+    ns = np.zeros(16)
+    check(lib.dg_profile_read_gmres_phases(ctx.handle, ns.ctypes.data), "dg_profile_read_gmres_phases")
+    out = {name: ns[i] / 1e6 for i, name in enumerate(GMRES_PHASES)}  # ms
+    out["iterations"] = int(ns[15])
+    out["second_passes"] = int(ns[14])
+    return out
+
+
 def dg_launch_count(ctx):
     n = ctypes.c_longlong(0)
     check(lib.dg_launch_count(ctx.handle, ctypes.byref(n)), "dg_launch_count")

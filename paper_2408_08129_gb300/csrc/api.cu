@@ -151,6 +151,7 @@ extern "C" int dg_ctx_create(int device, dg_ctx** out) {
 extern "C" int dg_ctx_destroy(dg_ctx* c) {
   if (!c) return DG_OK;
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->d_phase) cudaFree(c->d_phase);
   delete c;
   return DG_OK;
 }
@@ -160,6 +161,10 @@ extern "C" int dg_profile_enable(dg_ctx* c, int on) {
   if (on && c->ev_pool.empty()) {
     c->ev_pool.resize(8192);
     for (auto& e : c->ev_pool) DG_CUDA(cudaEventCreate(&e));
+  }
+  if (on && !c->d_phase) {
+    DG_CUDA(cudaMalloc(&c->d_phase, 16 * sizeof(unsigned long long)));
+    DG_CUDA(cudaMemset(c->d_phase, 0, 16 * sizeof(unsigned long long)));
   }
   if (!on && c->prof) prof_resolve(c);
   c->prof = on != 0;
@@ -182,9 +187,21 @@ extern "C" int dg_launch_count(const dg_ctx* c, long long* out) {
   return DG_OK;
 }
 
+extern "C" int dg_profile_read_gmres_phases(dg_ctx* c, double* ns) {
+  if (!c || !ns) return fail(DG_EINVAL, "null argument");
+  unsigned long long h[16] = {0};
+  if (c->d_phase) {
+    DG_CUDA(cudaDeviceSynchronize());
+    DG_CUDA(cudaMemcpy(h, c->d_phase, sizeof(h), cudaMemcpyDeviceToHost));
+  }
+  for (int i = 0; i < 16; ++i) ns[i] = (double)h[i];
+  return DG_OK;
+}
+
 extern "C" int dg_profile_reset(dg_ctx* c) {
   if (!c) return fail(DG_EINVAL, "null context");
   prof_resolve(c);
+  if (c->d_phase) DG_CUDA(cudaMemset(c->d_phase, 0, 16 * sizeof(unsigned long long)));
   for (int i = 0; i < DG_PROF_N; ++i) {
     c->prof_ms[i] = 0.0;
     c->prof_n[i] = 0;

@@ -19,8 +19,8 @@ struct Shape {
   static constexpr int NF = cpow(N, DIM - 1);   // nodes per face
   static constexpr int V = DIM + 2;             // conserved variables
   static constexpr int NSUB = 1 << (DIM - 1);   // subfaces of a 2:1 face
-  // cells per CTA for the one-thread-per-node cell kernels (>= 128 threads)
-  static constexpr int CPB = NC >= 128 ? 1 : (128 + NC - 1) / NC;
+  // cells per CTA for the one-thread-per-node cell kernels: fill 256 threads
+  static constexpr int CPB = NC >= 256 ? 1 : 256 / NC;
   static constexpr int THREADS = ((CPB * NC + 31) / 32) * 32;
   // table offsets (see Tables1D)
   static constexpr int T_D = 0, T_DW = N * N, T_I = 2 * N * N, T_IT = 4 * N * N, T_W = 6 * N * N,

@@ -61,6 +61,8 @@ struct MeshView {
   const T* fn;      // [dim][nf*NF] unit normal out of the minus side
   const T* fsj;     // [nf*NF] |J grad xi^a| (surface Jacobian)
   const int* cell_face;  // [n_cells*2*dim] (face << 2) | side; side 0 minus, 1 plus, 2 coarse, 3 wall
+  const int* fnode_m;    // [nf*NF] node index of each face node on the minus side
+  const int* fnode_p;    // [nf*NF] node index on the plus side (conforming faces; -1 otherwise)
   const T* tab;     // packed Tables1D of the mesh's degree
   T gravity;
 };
@@ -79,6 +81,7 @@ struct dg_ctx {
   double prof_ms[8] = {0};
   long long prof_n[8] = {0};
   long long launches = 0;  // kernels launched through this context
+  unsigned long long* d_phase = nullptr;  // [16] ns per fused-GMRES phase (profiling on)
 };
 
 namespace dg {

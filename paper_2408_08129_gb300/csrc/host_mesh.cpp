@@ -369,9 +369,18 @@ int build_mesh(dg_mesh* m) {
     }
   }
 
+  // node indices of the face nodes on both sides (saves the face-table look-ups)
+  if (m->Nn >= ((int64_t)1 << 31)) return fail(DG_EINVAL, "too many nodes for 32-bit node indices");
+  std::vector<int> fnode_m((size_t)nf * NF), fnode_p((size_t)nf * NF, -1);
+  for (int f = 0; f < nf; ++f)
+    for (int k = 0; k < NF; ++k) {
+      fnode_m[(size_t)f * NF + k] = face_m[f] * nc + host_face_node(dim, n, face_lfm[f], k);
+      if (f < m->nconf) fnode_p[(size_t)f * NF + k] = face_p[f] * nc + host_face_node(dim, n, face_lfp[f], k);
+    }
+
   // ---------------------------------------------------------------- upload
   const std::vector<double> tabp = tab.packed();
-  const size_t n_int = (size_t)5 * nf + cell_face.size();
+  const size_t n_int = (size_t)5 * nf + cell_face.size() + 2 * (size_t)nf * NF;
   const size_t n_real = (size_t)dim * dim * m->Nn + 4 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size();
   auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
   DG_CUDA(cudaSetDevice(m->ctx->device));
@@ -389,6 +398,8 @@ int build_mesh(dg_mesh* m) {
   ibuf.reserve(n_int);
   for (auto* v : {&face_m, &face_lfm, &face_p, &face_lfp, &face_s}) ibuf.insert(ibuf.end(), v->begin(), v->end());
   ibuf.insert(ibuf.end(), cell_face.begin(), cell_face.end());
+  ibuf.insert(ibuf.end(), fnode_m.begin(), fnode_m.end());
+  ibuf.insert(ibuf.end(), fnode_p.begin(), fnode_p.end());
   DG_CUDA(cudaMemcpy(m->d_int, ibuf.data(), ibuf.size() * sizeof(int), cudaMemcpyHostToDevice));
 
   std::vector<double> rbuf;
@@ -435,6 +446,8 @@ int build_mesh(dg_mesh* m) {
     v.face_lfp = ib + 3 * (size_t)nf;
     v.face_s = ib + 4 * (size_t)nf;
     v.cell_face = ib + 5 * (size_t)nf;
+    v.fnode_m = v.cell_face + cell_face.size();
+    v.fnode_p = v.fnode_m + (size_t)nf * NF;
     v.gravity = (decltype(v.gravity))d.gravity;
   };
   fill(m->v64, (const double*)m->d_f64);

@@ -29,8 +29,7 @@ __global__ void __launch_bounds__(256) explicit_face_kernel(MeshView<T> mv, cons
   if (t >= total) return;
   const int f = (int)(t / NF), k = (int)(t % NF);
   const int64_t Nn = mv.n_nodes;
-  const int cm = mv.face_m[f], lfm = mv.face_lfm[f];
-  const int64_t im = (int64_t)cm * NC + face_node<DIM, DEG>(lfm, k);
+  const int64_t im = mv.fnode_m[t];
   const T rb = mv.rhob[im], pb = mv.pb[im];
   T um[V], up[V], n[DIM];
   load_pert<V, T, PERT>(U, Nn, im, mv.rhob, mv.pb, um);
@@ -41,7 +40,7 @@ __global__ void __launch_bounds__(256) explicit_face_kernel(MeshView<T> mv, cons
   if (f < mv.nconf + mv.nsub) {
     const int cp = mv.face_p[f], lfp = mv.face_lfp[f];
     if (f < mv.nconf) {
-      const int64_t ip = (int64_t)cp * NC + face_node<DIM, DEG>(lfp, k);
+      const int64_t ip = mv.fnode_p[t];
       load_pert<V, T, PERT>(U, Nn, ip, mv.rhob, mv.pb, up);
     } else {
       // coarse polynomial (perturbation) at this fine face node: tensor of 1D I_s
@@ -106,21 +105,33 @@ __global__ void __launch_bounds__(256) explicit_face_kernel(MeshView<T> mv, cons
   for (int v = 0; v < V; ++v) Fh[(int64_t)v * total + t] = sj * out[v];
 }
 
-// Gather the face contributions of node (lc, i) of cell c for V fields stored
-// [v][nf*NF] in Fh.  sign_minus / sign_plus multiply the minus-side / plus-side
-// (and coarse-side) contributions.  Results are divided by w_end by the caller.
+// Face codes (face << 2 | side, see MeshView::cell_face) of the faces node idx
+// of cell c lies on, one per axis; -1 where the node is interior along that axis.
+// Loaded early so that their latency overlaps other work.
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void load_face_codes(const MeshView<T>& mv, int64_t c, const int* idx, int* codes) {
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    codes[a] = -1;
+    if (idx[a] == 0 || idx[a] == DEG) codes[a] = mv.cell_face[c * 2 * DIM + 2 * a + (idx[a] == DEG ? 1 : 0)];
+  }
+}
+
+// Gather the face contributions of node idx for NV fields stored [v][nf*NF]
+// in Fh, given its face codes.  sign_minus / sign_plus multiply the minus-side
+// / plus-side (and coarse-side) contributions.  Results are divided by w_end
+// by the caller.
 template <int DIM, int DEG, typename T, int NV>
-__device__ __forceinline__ void gather_faces(const MeshView<T>& mv, const T* __restrict__ Fh, int64_t c,
-                                             const int* idx, const T* sIt, T sign_minus, T sign_plus,
-                                             bool skip_walls, T* acc) {
+__device__ __forceinline__ void gather_faces_codes(const MeshView<T>& mv, const T* __restrict__ Fh,
+                                                   const int* codes, const int* idx, const T* sIt, T sign_minus,
+                                                   T sign_plus, bool skip_walls, T* acc) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NF = S::NF;
   const int64_t total = (int64_t)mv.nf * NF;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    if (idx[a] != 0 && idx[a] != DEG) continue;
-    const int lf = 2 * a + (idx[a] == DEG ? 1 : 0);
-    const int code = mv.cell_face[c * 2 * DIM + lf];
+    const int code = codes[a];
+    if (code < 0) continue;
     const int f = code >> 2, side = code & 3;
     const int kt = tangential_index<DIM, DEG>(a, idx);
     if (side == 3 && skip_walls) continue;
@@ -157,6 +168,15 @@ __device__ __forceinline__ void gather_faces(const MeshView<T>& mv, const T* __r
       }
     }
   }
+}
+
+template <int DIM, int DEG, typename T, int NV>
+__device__ __forceinline__ void gather_faces(const MeshView<T>& mv, const T* __restrict__ Fh, int64_t c,
+                                             const int* idx, const T* sIt, T sign_minus, T sign_plus,
+                                             bool skip_walls, T* acc) {
+  int codes[DIM];
+  load_face_codes<DIM, DEG, T>(mv, c, idx, codes);
+  gather_faces_codes<DIM, DEG, T, NV>(mv, Fh, codes, idx, sIt, sign_minus, sign_plus, skip_walls, acc);
 }
 
 template <int DIM, int DEG, typename T, bool FULL, bool PERT>

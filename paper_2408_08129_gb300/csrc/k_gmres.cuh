@@ -2,19 +2,27 @@
 // with the matrix-free Helmholtz mat-vec inlined (Sec. 3.2: GMRES on the
 // pressure system inside the fixed-point loop).
 //
-// The whole solve -- restart cycles, Arnoldi with classical Gram-Schmidt
-// applied twice, Givens rotations, convergence test and the solution update
-// -- runs in a single launch.  Phases are separated by grid-wide barriers of a
-// cooperative launch (all blocks co-resident), so no host round trip or extra
-// launch sits inside the Krylov loop.  Every block keeps an identical copy of
-// the small Hessenberg/Givens state in shared memory, computed from the same
-// global partial sums in the same order, so the decisions (convergence,
-// restart) agree across blocks and the result is bitwise reproducible.
+// The whole solve -- FP64 residual at every restart, Arnoldi cycles, Givens
+// rotations, convergence test and the FP64 solution update -- runs in one
+// launch.  Phases are separated by grid-wide barriers of a cooperative
+// launch (all blocks co-resident), so no host round trip or extra launch
+// sits inside the Krylov loop.  Every block keeps an identical copy of the
+// small Hessenberg/Givens state in shared memory, computed from the same
+// global partial sums in the same order, so all blocks take the same
+// decisions and the result is bitwise reproducible.
 //
-// The basis is stored unnormalised: Q_j holds the orthogonalised vector and
-// sigma_j = 1/||Q_j||, so q_j = sigma_j Q_j.  A q_j = sigma_j A Q_j is formed
-// by scaling the mat-vec output.  Dot products accumulate in FP64 for both
-// the FP64 solve and the FP32 inner solve of the refined form.
+// Krylov type TK:
+//  * double: plain FP64 GMRES (x, b, basis and mat-vec in FP64).
+//  * float:  the mixed form.  The basis and the Arnoldi mat-vecs are FP32
+//    (FP32 per-thread and per-warp accumulation of the dots, FP64 across
+//    warps and blocks); each cycle reduces the residual by inner_tol, then
+//    the next restart recomputes the residual b - A x with the FP64
+//    operator and FP64 x: iterative refinement inside one kernel.
+//
+// Orthogonalisation: classical Gram-Schmidt with the norm of w computed in
+// the same pass; ||w - Q h||^2 = ||w||^2 - ||h||^2 unless more than half of
+// ||w||^2 cancels, in which case a second Gram-Schmidt pass is made
+// ("twice is enough").  The new basis vector is written normalised.
 //
 // Loops are bounded by max_iters; there is no spin-wait of our own (the grid
 // barrier is the cooperative-groups one, valid because the launch is
@@ -27,23 +35,50 @@
 
 namespace dg {
 
-template <typename T>
+template <typename TK>
 struct GmresPArgs {
-  MeshView<T> mv;
-  const T* h;        // enthalpy at nodes
-  const T* b;        // right-hand side
-  T* x;              // initial guess in, solution out
-  T* Q;              // [(m+1)][n] unnormalised Krylov basis
-  T* w;              // [n] mat-vec output
-  T* Gh;             // face scratch [dim][nf*NF]
-  T* gv;             // [dim][n] scaled-gradient scratch
-  double* partial;   // >= gridDim.x doubles
-  double* out;       // [4]: iterations, relative residual, converged (0/1), ||b||
-  T alpha;           // (a_ii dt)^2
-  double tol;
+  MeshView<double> mv64;  // FP64 residual mat-vec
+  MeshView<TK> mvk;       // Arnoldi mat-vec
+  const double* h64;      // enthalpy at nodes (FP64)
+  const TK* hk;           // the same in TK
+  const double* b;        // right-hand side
+  double* x;              // initial guess in, solution out
+  TK* Q;                  // [(m+1)][n] Krylov basis (q_0 unnormalised, scale sigma_0)
+  TK* w;                  // [n] Arnoldi mat-vec output
+  double* w64;            // [n] FP64 residual mat-vec output (may alias w when TK = double)
+  double* Gh;             // face scratch (dim*nf*NF doubles), reused as TK
+  double* gv;             // [dim][n] gradient scratch (doubles), reused as TK
+  double* partial;        // >= gridDim.x doubles
+  double* out;            // [4]: iterations, relative residual, converged (0/1), ||b||
+  unsigned long long* phase;  // optional [16] ns per phase accumulated by block 0 (NULL = off)
+  double alpha;           // (a_ii dt)^2
+  double tol;             // target ||b - A x|| / ||b|| (checked on the FP64 residual)
+  double inner_tol;       // TK = float: residual reduction per cycle
   int m;
   int max_iters;
   int64_t n;
+};
+
+enum GmresPhase {
+  PH_GRAD_FACE = 0, PH_GRAD_CELL, PH_DIV_FACE, PH_DIV_CELL, PH_DOTS, PH_UPDATE, PH_REORTH, PH_RESIDUAL,
+  PH_SOLUTION, PH_ITERS = 15
+};
+
+struct PhaseClock {
+  unsigned long long* acc;
+  unsigned long long last;
+  __device__ __forceinline__ static unsigned long long now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+  }
+  __device__ __forceinline__ void mark(int p) {
+    if (acc && blockIdx.x == 0 && threadIdx.x == 0) {
+      const unsigned long long t = now();
+      acc[p] += t - last;
+      last = t;
+    }
+  }
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sred) {
@@ -58,104 +93,175 @@ __device__ __forceinline__ double block_sum(double v, double* sred) {
   return r;
 }
 
-// w = scale * A p, A the Helmholtz operator (four phases, four grid barriers)
-template <int DIM, int DEG, typename T>
-__device__ __forceinline__ void pmatvec(const GmresPArgs<T>& a, const T* p, T scale, T* out,
-                                        cooperative_groups::grid_group& grid, T* scell, const T* sD, const T* sDw,
-                                        const T* sIt) {
-  using S = Shape<DIM, DEG>;
-  const int64_t nfi = (int64_t)(a.mv.nconf + a.mv.nsub) * S::NF;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nb = (a.mv.n_cells + S::CPB - 1) / S::CPB;
-  for (int64_t t = tid; t < nfi; t += stride) grad_face_item<DIM, DEG, T>(a.mv, p, a.Gh, t);
-  grid.sync();
-  for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x)
-    grad_cell_batch<DIM, DEG, T>(a.mv, p, a.h, a.Gh, a.gv, bt, scell, sD, sIt);
-  grid.sync();
-  for (int64_t t = tid; t < nfi; t += stride) div_face_item<DIM, DEG, T>(a.mv, a.gv, a.Gh, t);
-  grid.sync();
-  for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x)
-    div_cell_batch<DIM, DEG, T, true>(a.mv, a.gv, a.Gh, p, a.alpha, scale, out, bt, scell, sDw, sIt);
-  grid.sync();
+// copy cnt (<= 512) global partial sums into shared memory with all threads
+// (one parallel round trip instead of a serial chain of loads)
+__device__ __forceinline__ void stage_partials(const double* partial, int cnt, double* spart) {
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) spart[i] = partial[i];
+  __syncthreads();
 }
 
-// partial[j*C + c] = sum over chunk c of Q_j . w, for j < nv (C chunks per vector)
-template <typename T>
-__device__ __forceinline__ void pdots(const T* Q, int64_t n, const T* w, int nv, int C, double* partial,
+// warp-level sum in TK, then FP64 across warps
+template <typename TK>
+__device__ __forceinline__ double block_sum_k(TK v, double* sred) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = (double)v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sred[i];
+  return r;
+}
+
+// out = scale * (ident p/(gamma-1) - alpha div(h grad p)) (four phases, four grid barriers)
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void pmatvec(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p, T scale,
+                                        T* out,
+                                        T* Gh, T* gv, cooperative_groups::grid_group& grid, T* scell, const T* sD,
+                                        const T* sDw, const T* sIt, PhaseClock& pc) {
+  using S = Shape<DIM, DEG>;
+  const int64_t nfi = (int64_t)(mv.nconf + mv.nsub) * S::NF;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nb = (mv.n_cells + S::CPB - 1) / S::CPB;
+  for (int64_t t = tid; t < nfi; t += stride) grad_face_item<DIM, DEG, T>(mv, p, Gh, t);
+  grid.sync();
+  pc.mark(PH_GRAD_FACE);
+  for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x)
+    grad_cell_batch<DIM, DEG, T>(mv, p, h, Gh, gv, bt, scell, sD, sIt);
+  grid.sync();
+  pc.mark(PH_GRAD_CELL);
+  for (int64_t t = tid; t < nfi; t += stride) div_face_item<DIM, DEG, T>(mv, gv, Gh, t);
+  grid.sync();
+  pc.mark(PH_DIV_FACE);
+  for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x)
+    div_cell_batch<DIM, DEG, T, true>(mv, gv, Gh, p, alpha, scale, ident, out, bt, scell, sDw, sIt);
+  grid.sync();
+  pc.mark(PH_DIV_CELL);
+}
+
+// partial[j*C + c] = sum over chunk c of v_j . w for j < nv, where v_j = Q_j for
+// j < nv-1 and v_{nv-1} = w itself (so the last entry is ||w||^2 by chunks)
+template <typename TK>
+__device__ __forceinline__ void pdots(const TK* Q, int64_t n, const TK* w, int nv, int C, double* partial,
                                       double* sred) {
   const int64_t chunk = (n + C - 1) / C;
   for (int it = blockIdx.x; it < nv * C; it += gridDim.x) {
     const int j = it / C, c = it % C;
     const int64_t lo = (int64_t)c * chunk;
     const int64_t hi = lo + chunk < n ? lo + chunk : n;
-    const T* q = Q + (int64_t)j * n;
-    double acc = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += (double)q[i] * (double)w[i];
-    const double s = block_sum(acc, sred);
+    const TK* q = (j < nv - 1) ? Q + (int64_t)j * n : w;
+    // four independent accumulators so that four pairs of loads are in flight
+    TK a0 = TK(0), a1 = TK(0), a2 = TK(0), a3 = TK(0);
+    const int64_t bd = blockDim.x;
+    int64_t i = lo + threadIdx.x;
+    for (; i + 3 * bd < hi; i += 4 * bd) {
+      const TK q0 = q[i], q1 = q[i + bd], q2 = q[i + 2 * bd], q3 = q[i + 3 * bd];
+      const TK w0 = w[i], w1 = w[i + bd], w2 = w[i + 2 * bd], w3 = w[i + 3 * bd];
+      a0 += q0 * w0;
+      a1 += q1 * w1;
+      a2 += q2 * w2;
+      a3 += q3 * w3;
+    }
+    for (; i < hi; i += bd) a0 += q[i] * w[i];
+    const double s = block_sum_k<TK>((a0 + a1) + (a2 + a3), sred);
     if (threadIdx.x == 0) partial[it] = s;
   }
 }
 
-template <int DIM, int DEG, typename T>
-__global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<T> a) {
+// sum_{j<cnt} coef[j] Q_j[i] accumulated in TK, with the loads of eight basis
+// vectors in flight at once
+template <typename TK>
+__device__ __forceinline__ TK lincomb(const TK* __restrict__ Q, int64_t n, int64_t i,
+                                      const double* __restrict__ coef, int cnt) {
+  TK acc = TK(0);
+  int j = 0;
+  for (; j + 8 <= cnt; j += 8) {
+    TK q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) q[u] = Q[(int64_t)(j + u) * n + i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += (TK)coef[j + u] * q[u];
+  }
+  for (; j < cnt; ++j) acc += (TK)coef[j] * Q[(int64_t)j * n + i];
+  return acc;
+}
+
+template <int DIM, int DEG, typename TK>
+__global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = a.m;
-  // shared layout: doubles first, then T tables and the cell tile
-  double* sigma = (double*)smem_raw;          // [m+1]
-  double* h1 = sigma + (m + 1);               // [m+1]
-  double* h2 = h1 + (m + 1);                  // [m+1]
-  double* R = h2 + (m + 1);                   // [(m+1)*m], column k at R[k*(m+1)]
-  double* cs = R + (m + 1) * m;               // [m]
-  double* sn = cs + m;                        // [m]
-  double* gg = sn + m;                         // [m+1]
-  double* y = gg + (m + 1);                   // [m]
-  double* sred = y + m;                       // [32]
-  double* sc = sred + 32;                     // [8] scalars: 0 bn, 1 resid, 2 beta
-  int* sflag = (int*)(sc + 8);                // [4]: 0 stop inner, 1 converged, 2 kd
-  T* tabs = (T*)(sflag + 4);
-  T* sD = tabs;
-  T* sDw = sD + N * N;
-  T* sIt = sDw + N * N;
-  T* scell = sIt + 2 * N * N;
+  double* sigma = (double*)smem_raw;  // [m+1] scale of q_j (1/beta for j = 0, else 1)
+  double* hh = sigma + (m + 1);       // [m+2] Gram-Schmidt coefficients (+ ||w||^2 in [k+1])
+  double* h2 = hh + (m + 2);          // [m+2] second pass
+  double* R = h2 + (m + 2);           // [(m+1)*m] rotated Hessenberg, column k at R[k*(m+1)]
+  double* cs = R + (m + 1) * m;       // [m]
+  double* sn = cs + m;                // [m]
+  double* gg = sn + m;                // [m+1]
+  double* y = gg + (m + 1);           // [m]
+  double* coef = y + m;               // [m+1]
+  double* sred = coef + (m + 1);      // [32]
+  double* sc = sred + 32;             // [8]: 0 ||b||, 1 resid, 2 beta, 3 1/hn, 4 ||w||^2 after
+  double* spart = sc + 8;             // [512] staged block partials
+  int* sflag = (int*)(spart + 512);   // [4]: 0 stop cycle, 1 converged, 2 reorth
+  double* t64 = (double*)(sflag + 4);  // FP64 tables D, Dw, It
+  double* sD64 = t64;
+  double* sDw64 = sD64 + N * N;
+  double* sIt64 = sDw64 + N * N;
+  double* scell64 = sIt64 + 2 * N * N;  // cell tile, CPB*NC doubles (reused as TK)
+  TK* tk = (TK*)(scell64 + S::CPB * S::NC);
+  TK* sDk = tk;
+  TK* sDwk = sDk + N * N;
+  TK* sItk = sDwk + N * N;
+  TK* scellk = (TK*)scell64;
 
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
-    sD[q] = a.mv.tab[S::T_D + q];
-    sDw[q] = a.mv.tab[S::T_DW + q];
+    sD64[q] = a.mv64.tab[S::T_D + q];
+    sDw64[q] = a.mv64.tab[S::T_DW + q];
+    sDk[q] = a.mvk.tab[S::T_D + q];
+    sDwk[q] = a.mvk.tab[S::T_DW + q];
   }
-  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = a.mv.tab[S::T_IT + q];
+  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) {
+    sIt64[q] = a.mv64.tab[S::T_IT + q];
+    sItk[q] = a.mvk.tab[S::T_IT + q];
+  }
   __syncthreads();
+  PhaseClock pc{a.phase, PhaseClock::now()};
 
   const int64_t n = a.n;
   const int G = gridDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)G * blockDim.x;
-  const int64_t chunk1 = (n + G - 1) / G;  // one chunk per block for single-vector passes
+  const int64_t chunk1 = (n + G - 1) / G;
+  const bool mixed = sizeof(TK) != sizeof(double);
+  TK* Ghk = (TK*)a.Gh;
+  TK* gvk = (TK*)a.gv;
 
-  // ||b||^2
+  // ||b||
   {
     const int64_t lo = (int64_t)blockIdx.x * chunk1;
     const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
     double acc = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += (double)a.b[i] * (double)a.b[i];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += a.b[i] * a.b[i];
     const double s = block_sum(acc, sred);
     if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
   }
   grid.sync();
+  stage_partials(a.partial, G, spart);
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int i = 0; i < G; ++i) s += a.partial[i];
+    for (int i = 0; i < G; ++i) s += spart[i];
     sc[0] = sqrt(s);
-    sflag[1] = 0;
   }
   __syncthreads();
   const double bn = sc[0];
   if (bn == 0.0) {
-    for (int64_t i = tid; i < n; i += gstride) a.x[i] = T(0);
+    for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.out[0] = 0;
       a.out[1] = 0;
@@ -164,38 +270,41 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<T> a) 
     }
     return;
   }
-  grid.sync();  // everyone has read partial before it is reused
+  grid.sync();  // partial reused below
 
   int total = 0;
   double rel = 1.0;
   bool converged = false;
-  while (total < a.max_iters) {
-    // r = b - A x  -> Q_0 (unnormalised), beta = ||r||
-    pmatvec<DIM, DEG, T>(a, a.x, T(1), a.w, grid, scell, sD, sDw, sIt);
+  while (true) {
+    // r = b - A x with the FP64 operator -> q_0 (unnormalised), beta
+    pmatvec<DIM, DEG, double>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.Gh, a.gv, grid, scell64, sD64,
+                              sDw64, sIt64, pc);
     {
       const int64_t lo = (int64_t)blockIdx.x * chunk1;
       const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
       double acc = 0.0;
       for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const T r = a.b[i] - a.w[i];
-        a.Q[i] = r;
-        acc += (double)r * (double)r;
+        const double r = a.b[i] - a.w64[i];
+        a.Q[i] = (TK)r;
+        acc += r * r;
       }
       const double s = block_sum(acc, sred);
       if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
     }
     grid.sync();
+    pc.mark(PH_RESIDUAL);
+    stage_partials(a.partial, G, spart);
     if (threadIdx.x == 0) {
       double s = 0.0;
-      for (int i = 0; i < G; ++i) s += a.partial[i];
+      for (int i = 0; i < G; ++i) s += spart[i];
       const double beta = sqrt(s);
       sc[2] = beta;
       sflag[1] = (beta <= a.tol * bn) ? 1 : 0;
       sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+      for (int j = 1; j <= m; ++j) sigma[j] = 1.0;
       for (int j = 0; j <= m; ++j) gg[j] = 0.0;
       gg[0] = beta;
       sflag[0] = 0;
-      sflag[2] = 0;
     }
     __syncthreads();
     rel = sc[2] / bn;
@@ -203,62 +312,84 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<T> a) 
       converged = true;
       break;
     }
-    grid.sync();  // partial reused below
+    if (total >= a.max_iters) break;
+    const double cycle_floor = fmax(a.tol * bn, (mixed ? a.inner_tol : 0.0) * sc[2]);
     int kd = 0;
     for (int k = 0; k < m; ++k) {
-      const T* qk = a.Q + (int64_t)k * n;
-      pmatvec<DIM, DEG, T>(a, qk, (T)sigma[k], a.w, grid, scell, sD, sDw, sIt);
-      // first Gram-Schmidt pass
-      int C = G / (k + 1);
+      const TK* qk = a.Q + (int64_t)k * n;
+      // Arnoldi on B = A - I/(gamma-1): same Krylov space, Hessenberg of A = that of B
+      // plus 1/(gamma-1) on the diagonal; w = B q_k has no large component along q_k
+      pmatvec<DIM, DEG, TK>(a.mvk, a.hk, (TK)a.alpha, TK(0), qk, (TK)sigma[k], a.w, Ghk, gvk, grid, scellk, sDk,
+                            sDwk, sItk, pc);
+      // h_j = q_j . w (j <= k) and ||w||^2, one pass
+      const int nv = k + 2;
+      int C = G / nv;
       if (C < 1) C = 1;
-      pdots<T>(a.Q, n, a.w, k + 1, C, a.partial, sred);
+      pdots<TK>(a.Q, n, a.w, nv, C, a.partial, sred);
       grid.sync();
-      if (threadIdx.x <= k) {
+      pc.mark(PH_DOTS);
+      stage_partials(a.partial, nv * C, spart);
+      if (threadIdx.x < nv) {
         double s = 0.0;
-        for (int c = 0; c < C; ++c) s += a.partial[threadIdx.x * C + c];
-        h1[threadIdx.x] = s * sigma[threadIdx.x];
+        for (int c = 0; c < C; ++c) s += spart[threadIdx.x * C + c];
+        hh[threadIdx.x] = (threadIdx.x < nv - 1) ? s * sigma[threadIdx.x] : s;
       }
       __syncthreads();
-      for (int64_t i = tid; i < n; i += gstride) {
-        double acc = 0.0;
-        for (int j = 0; j <= k; ++j) acc += h1[j] * sigma[j] * (double)a.Q[(int64_t)j * n + i];
-        a.w[i] = (T)((double)a.w[i] - acc);
-      }
-      grid.sync();
-      // second pass
-      pdots<T>(a.Q, n, a.w, k + 1, C, a.partial, sred);
-      grid.sync();
-      if (threadIdx.x <= k) {
-        double s = 0.0;
-        for (int c = 0; c < C; ++c) s += a.partial[threadIdx.x * C + c];
-        h2[threadIdx.x] = s * sigma[threadIdx.x];
-      }
-      __syncthreads();
-      {
-        T* qn = a.Q + (int64_t)(k + 1) * n;
-        const int64_t lo = (int64_t)blockIdx.x * chunk1;
-        const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
-        double acc2 = 0.0;
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-          double acc = 0.0;
-          for (int j = 0; j <= k; ++j) acc += h2[j] * sigma[j] * (double)a.Q[(int64_t)j * n + i];
-          const T v = (T)((double)a.w[i] - acc);
-          qn[i] = v;
-          acc2 += (double)v * (double)v;
-        }
-        const double s = block_sum(acc2, sred);
-        // the partials of pass 2 were consumed above by every block before this
-        // barrier-free write? No: other blocks may still read them -- use a
-        // separate slot range past the dot items.
-        if (threadIdx.x == 0) a.partial[G + blockIdx.x] = s;
-      }
-      grid.sync();
       if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < G; ++i) s += a.partial[G + i];
-        const double hn = sqrt(s);
+        double ss = 0.0;
+        for (int j = 0; j <= k; ++j) {
+          ss += hh[j] * hh[j];
+          coef[j] = hh[j] * sigma[j];
+        }
+        const double ww = hh[k + 1];
+        const double after = ww - ss;
+        sflag[2] = (after < 0.5 * ww) ? 1 : 0;
+        sc[4] = after;
+        sc[3] = after > 0.0 ? 1.0 / sqrt(after) : 0.0;
+      }
+      __syncthreads();
+      TK* qn = a.Q + (int64_t)(k + 1) * n;
+      if (!sflag[2]) {
+        const double inv = sc[3];
+        const TK invk = (TK)inv;
+        for (int64_t i = tid; i < n; i += gstride) qn[i] = (a.w[i] - lincomb(a.Q, n, i, coef, k + 1)) * invk;
+      } else {
+        // second Gram-Schmidt pass
+        if (a.phase && blockIdx.x == 0 && threadIdx.x == 0) a.phase[14] += 1;
+        for (int64_t i = tid; i < n; i += gstride) a.w[i] -= lincomb(a.Q, n, i, coef, k + 1);
+        grid.sync();
+        pdots<TK>(a.Q, n, a.w, nv, C, a.partial, sred);
+        grid.sync();
+        pc.mark(PH_REORTH);
+        stage_partials(a.partial, nv * C, spart);
+        if (threadIdx.x < nv) {
+          double s = 0.0;
+          for (int c = 0; c < C; ++c) s += spart[threadIdx.x * C + c];
+          h2[threadIdx.x] = (threadIdx.x < nv - 1) ? s * sigma[threadIdx.x] : s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double ss = 0.0;
+          for (int j = 0; j <= k; ++j) {
+            ss += h2[j] * h2[j];
+            coef[j] = h2[j] * sigma[j];
+            hh[j] += h2[j];
+          }
+          const double after = h2[k + 1] - ss;
+          sc[4] = after;
+          sc[3] = after > 0.0 ? 1.0 / sqrt(after) : 0.0;
+        }
+        __syncthreads();
+        const double inv = sc[3];
+        const TK invk = (TK)inv;
+        for (int64_t i = tid; i < n; i += gstride) qn[i] = (a.w[i] - lincomb(a.Q, n, i, coef, k + 1)) * invk;
+      }
+      // Givens update of column k (every block, identical)
+      if (threadIdx.x == 0) {
+        const double hn = sc[4] > 0.0 ? sqrt(sc[4]) : 0.0;
         double* col = R + (int64_t)k * (m + 1);
-        for (int j = 0; j <= k; ++j) col[j] = h1[j] + h2[j];
+        for (int j = 0; j <= k; ++j) col[j] = hh[j];
+        col[k] += 1.0 / (kGamma - 1.0);
         col[k + 1] = hn;
         for (int j = 0; j < k; ++j) {
           const double t = cs[j] * col[j] + sn[j] * col[j + 1];
@@ -276,50 +407,54 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<T> a) 
         gg[k] = c * gg[k];
         const double resid = fabs(gg[k + 1]);
         sc[1] = resid;
-        sigma[k + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-        const bool conv = resid <= a.tol * bn;
-        sflag[1] = conv ? 1 : 0;
-        sflag[0] = (conv || hn == 0.0 || total + 1 >= a.max_iters) ? 1 : 0;
+        sflag[1] = resid <= a.tol * bn ? 1 : 0;
+        sflag[0] = (resid <= cycle_floor || hn == 0.0 || total + 1 >= a.max_iters) ? 1 : 0;
       }
-      __syncthreads();
+      grid.sync();
+      pc.mark(PH_UPDATE);
       ++total;
       kd = k + 1;
       rel = sc[1] / bn;
       if (sflag[0]) break;
     }
-    // y = R^-1 g over the kd columns, x += sum_j y_j q_j
+    // x += sum_j y_j q_j, y from the rotated Hessenberg system
     if (threadIdx.x == 0) {
       for (int i = kd - 1; i >= 0; --i) {
         double s = gg[i];
         for (int j = i + 1; j < kd; ++j) s -= R[(int64_t)j * (m + 1) + i] * y[j];
         y[i] = s / R[(int64_t)i * (m + 1) + i];
       }
+      for (int j = 0; j < kd; ++j) coef[j] = y[j] * sigma[j];
     }
     __syncthreads();
-    for (int64_t i = tid; i < n; i += gstride) {
-      double acc = 0.0;
-      for (int j = 0; j < kd; ++j) acc += y[j] * sigma[j] * (double)a.Q[(int64_t)j * n + i];
-      a.x[i] = (T)((double)a.x[i] + acc);
-    }
+    for (int64_t i = tid; i < n; i += gstride) a.x[i] += (double)lincomb(a.Q, n, i, coef, kd);
     grid.sync();
-    if (sflag[1]) {
+    pc.mark(PH_SOLUTION);
+    // plain FP64 GMRES trusts its residual estimate; the mixed form re-checks
+    // with the FP64 residual at the next restart
+    if (!mixed && sflag[1]) {
       converged = true;
       break;
     }
+    if (total >= a.max_iters) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.out[0] = total;
     a.out[1] = rel;
     a.out[2] = converged ? 1.0 : 0.0;
     a.out[3] = bn;
+    if (a.phase) a.phase[PH_ITERS] += (unsigned long long)total;
   }
 }
 
-template <int DIM, int DEG, typename T>
+template <int DIM, int DEG, typename TK>
 inline size_t gmres_smem_bytes(int m) {
   constexpr int N = DEG + 1;
-  const size_t dbl = (size_t)3 * (m + 1) + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 32 + 8;
-  return dbl * sizeof(double) + 4 * sizeof(int) + (size_t)(4 * N * N + Shape<DIM, DEG>::CPB * Shape<DIM, DEG>::NC) * sizeof(T) + 16;
+  using S = Shape<DIM, DEG>;
+  const size_t dbl = (size_t)(m + 1) + 2 * (size_t)(m + 2) + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m +
+                     (m + 1) + 32 + 8 + 512;
+  return dbl * sizeof(double) + 4 * sizeof(int) + (size_t)(4 * N * N + S::CPB * S::NC) * sizeof(double) +
+         (size_t)(4 * N * N) * sizeof(TK) + 64;
 }
 
 }  // namespace dg

@@ -60,10 +60,10 @@ __device__ __forceinline__ void grad_face_item(const MeshView<T>& mv, const T* _
   constexpr int NC = S::NC, NF = S::NF;
   const int64_t total = (int64_t)mv.nf * NF;
   const int f = (int)(t / NF), k = (int)(t % NF);
-  const T pm = p[(int64_t)mv.face_m[f] * NC + face_node<DIM, DEG>(mv.face_lfm[f], k)];
+  const T pm = p[mv.fnode_m[t]];
   T pp;
   if (f < mv.nconf)
-    pp = p[(int64_t)mv.face_p[f] * NC + face_node<DIM, DEG>(mv.face_lfp[f], k)];
+    pp = p[mv.fnode_p[t]];
   else
     coarse_at<DIM, DEG, T, 1>(mv, p, mv.n_nodes, f, k, &pp);
   const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
@@ -73,6 +73,8 @@ __device__ __forceinline__ void grad_face_item(const MeshView<T>& mv, const T* _
 
 // Cells [batch*CPB, batch*CPB + CPB): g_b = h [sum_a Ja^a_b (D_a p) + Gh_b / w_end] / J.
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
+// Every global load that does not depend on the face values is issued before
+// the barrier so that the loads' latencies overlap.
 template <int DIM, int DEG, typename T>
 __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
                                                 const T* __restrict__ h, const T* __restrict__ Gh,
@@ -85,10 +87,21 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   const bool active = (lc < CPB) && (c < mv.n_cells);
   const int64_t Nn = mv.n_nodes;
   const int64_t idx = c * NC + i;
-  if (active) sp[lc * NC + i] = p[idx];
+  int id[3] = {i % N, (i / N) % N, i / (N * N)};
+  int codes[DIM];
+  T Jl[DIM][DIM];
+  T scale = T(0);
+  if (active) {
+    sp[lc * NC + i] = p[idx];
+    load_face_codes<DIM, DEG, T>(mv, c, id, codes);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
+    scale = mv.invJ[idx] * (h ? h[idx] : T(1));
+  }
   __syncthreads();
   if (active) {
-    int id[3] = {i % N, (i / N) % N, i / (N * N)};
     T dp[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -103,14 +116,13 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
     T facc[DIM];
 #pragma unroll
     for (int b = 0; b < DIM; ++b) facc[b] = T(0);
-    gather_faces<DIM, DEG, T, DIM>(mv, Gh, c, id, sIt, T(1), T(1), true, facc);
+    gather_faces_codes<DIM, DEG, T, DIM>(mv, Gh, codes, id, sIt, T(1), T(1), true, facc);
     const T iwend = mv.tab[S::T_IWEND];
-    const T scale = mv.invJ[idx] * (h ? h[idx] : T(1));
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
       T s = facc[b] * iwend;
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * dp[a];
+      for (int a = 0; a < DIM; ++a) s += Jl[a][b] * dp[a];
       g[(int64_t)b * Nn + idx] = s * scale;
     }
   }
@@ -128,10 +140,10 @@ __device__ __forceinline__ void div_face_item(const MeshView<T>& mv, const T* __
   const int64_t total = (int64_t)mv.nf * NF;
   const int f = (int)(t / NF), k = (int)(t % NF);
   const int64_t Nn = mv.n_nodes;
-  const int64_t im = (int64_t)mv.face_m[f] * NC + face_node<DIM, DEG>(mv.face_lfm[f], k);
+  const int64_t im = mv.fnode_m[t];
   T fp[DIM];
   if (f < mv.nconf) {
-    const int64_t ip = (int64_t)mv.face_p[f] * NC + face_node<DIM, DEG>(mv.face_lfp[f], k);
+    const int64_t ip = mv.fnode_p[t];
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fp[b] = fld[(int64_t)b * Nn + ip];
   } else {
@@ -143,12 +155,12 @@ __device__ __forceinline__ void div_face_item(const MeshView<T>& mv, const T* __
   Dh[t] = T(0.5) * mv.fsj[t] * s;
 }
 
-// Cells of one batch: out = HELM ? scale * (p/(gamma-1) - alpha div) : div.
+// Cells of one batch: out = HELM ? scale * (ident p/(gamma-1) - alpha div) : div.
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 template <int DIM, int DEG, typename T, bool HELM>
 __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
                                                const T* __restrict__ Dh, const T* __restrict__ p, T alpha, T scale,
-                                               T* __restrict__ out, int64_t batch, T* sF, const T* sDw,
+                                               T ident, T* __restrict__ out, int64_t batch, T* sF, const T* sDw,
                                                const T* sIt) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
@@ -158,20 +170,28 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   const int64_t Nn = mv.n_nodes;
   const int64_t idx = c * NC + i;
   int id[3] = {i % N, (i / N) % N, i / (N * N)};
-  T fv[DIM];
+  int codes[DIM];
+  T ft[DIM];  // Ja^a . f for each axis a
+  T ij = T(0), pv = T(0);
   if (active) {
+    T fv[DIM];
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fv[b] = fld[(int64_t)b * Nn + idx];
+    load_face_codes<DIM, DEG, T>(mv, c, id, codes);
+    ij = mv.invJ[idx];
+    if (HELM) pv = p[idx];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * fv[b];
+      ft[a] = s;
+    }
   }
   T acc = T(0);
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    if (active) {
-      T ft = T(0);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) ft += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * fv[b];
-      sF[lc * NC + i] = ft;
-    }
+    if (active) sF[lc * NC + i] = ft[a];
     __syncthreads();
     if (active) {
       const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
@@ -184,10 +204,10 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   }
   if (active) {
     T facc = T(0);
-    gather_faces<DIM, DEG, T, 1>(mv, Dh, c, id, sIt, T(1), T(-1), true, &facc);
-    const T dv = (acc + facc * mv.tab[S::T_IWEND]) * mv.invJ[idx];
+    gather_faces_codes<DIM, DEG, T, 1>(mv, Dh, codes, id, sIt, T(1), T(-1), true, &facc);
+    const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
     if (HELM)
-      out[idx] = scale * (p[idx] / gm1<T>() - alpha * dv);
+      out[idx] = scale * (ident * pv / gm1<T>() - alpha * dv);
     else
       out[idx] = dv;
   }
@@ -246,7 +266,7 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(Mesh
   __shared__ T sIt[2 * N * N];
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sDw[q] = mv.tab[S::T_DW + q];
   for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
-  div_cell_batch<DIM, DEG, T, HELM>(mv, fld, Dh, p, alpha, T(1), out, blockIdx.x, sF, sDw, sIt);
+  div_cell_batch<DIM, DEG, T, HELM>(mv, fld, Dh, p, alpha, T(1), T(1), out, blockIdx.x, sF, sDw, sIt);
 }
 
 }  // namespace dg

@@ -32,16 +32,25 @@ int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T
                      cudaStream_t s, const int* skip);
 
 // One cooperative launch solving A(h) x = b by restarted GMRES(restart) to
-// relative residual tol (k_gmres.cuh).  Q: (restart+1)*n, w: n, partial:
-// npartial doubles, out: 4 doubles (iterations, rel. residual, converged, ||b||).
-template <int DIM, typename T>
-int launch_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double tol, int restart, int max_iters,
-                 T* Q, T* w, double* partial, int npartial, double* out, cudaStream_t s);
-template <typename T>
-inline int op_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double tol, int restart,
-                    int max_iters, T* Q, T* w, double* partial, int npartial, double* out, cudaStream_t s) {
-  return m->dim == 2 ? launch_gmres<2, T>(m, h, b, x, alpha, tol, restart, max_iters, Q, w, partial, npartial, out, s)
-                     : launch_gmres<3, T>(m, h, b, x, alpha, tol, restart, max_iters, Q, w, partial, npartial, out, s);
+// relative residual tol (k_gmres.cuh).  TK = double: FP64 GMRES; TK = float:
+// FP32 Arnoldi with FP64 residual and solution (iterative refinement inside
+// the kernel, inner_tol = residual reduction per cycle).  x, b: FP64.  hk: h
+// in TK (may equal h64 when TK = double).  Q: (restart+1)*n TK, w: n TK, w64:
+// n doubles (may alias w when TK = double), partial: npartial doubles, out: 4
+// doubles (iterations, rel. residual, converged, ||b||), phase: optional
+// per-phase ns accumulators (16, or NULL).
+template <int DIM, typename TK>
+int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
+                 double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64,
+                 double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s);
+template <typename TK>
+inline int op_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
+                    double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64,
+                    double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
+  return m->dim == 2 ? launch_gmres<2, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart, max_iters, Q, w, w64,
+                                           partial, npartial, out, phase, s)
+                     : launch_gmres<3, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart, max_iters, Q, w, w64,
+                                           partial, npartial, out, phase, s);
 }
 
 // dimension dispatch (with optional event timing per operator category)

@@ -61,27 +61,33 @@ int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, T* Dh, cu
   return check_launch("divergence launch");
 }
 
-template <int DIM, int DEG, typename T>
-int run_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double tol, int restart, int max_iters,
-              T* Q, T* w, double* partial, int npartial, double* out, cudaStream_t s) {
-  GmresPArgs<T> a;
-  a.mv = view<T>(m);
-  a.h = h;
+template <int DIM, int DEG, typename TK>
+int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
+              double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64, double* partial,
+              int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
+  GmresPArgs<TK> a;
+  a.mv64 = m->v64;
+  a.mvk = view<TK>(m);
+  a.h64 = h64;
+  a.hk = hk;
   a.b = b;
   a.x = x;
   a.Q = Q;
   a.w = w;
-  a.Gh = (T*)m->d_face_scratch64;
-  a.gv = (T*)m->d_vec_scratch64;
+  a.w64 = w64;
+  a.Gh = m->d_face_scratch64;
+  a.gv = m->d_vec_scratch64;
   a.partial = partial;
   a.out = out;
+  a.phase = phase;
   a.alpha = alpha;
   a.tol = tol;
+  a.inner_tol = inner_tol;
   a.m = restart;
   a.max_iters = max_iters;
   a.n = m->Nn;
-  auto kern = gmres_persistent_kernel<DIM, DEG, T>;
-  const size_t smem = gmres_smem_bytes<DIM, DEG, T>(restart);
+  auto kern = gmres_persistent_kernel<DIM, DEG, TK>;
+  const size_t smem = gmres_smem_bytes<DIM, DEG, TK>(restart);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "gmres smem attribute");
@@ -91,7 +97,8 @@ int run_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double to
   if (e != cudaSuccess) return cuda_fail(e, "gmres occupancy");
   if (per_sm < 1) return fail(DG_ECUDA, "persistent GMRES kernel does not fit on an SM");
   int G = m->ctx->sm_count * (per_sm < 2 ? per_sm : 2);
-  if (G > npartial / 2) G = npartial / 2;
+  if (G > npartial) G = npartial;
+  if (G > 512) G = 512;  // staged partial sums in shared memory
   if (G < 1) return fail(DG_EINVAL, "GMRES partial buffer too small");
   count_launches(m->ctx, 1);
   void* args[] = {&a};
@@ -137,11 +144,13 @@ int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T
   })
 }
 
-template <int DIM, typename T>
-int launch_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double tol, int restart, int max_iters,
-                 T* Q, T* w, double* partial, int npartial, double* out, cudaStream_t s) {
-  DG_DEGREE_SWITCH(m->degree, return (run_gmres<DIM, DEG, T>(m, h, b, x, alpha, tol, restart, max_iters, Q, w,
-                                                              partial, npartial, out, s)))
+template <int DIM, typename TK>
+int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
+                 double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64,
+                 double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
+  DG_DEGREE_SWITCH(m->degree, return (run_gmres<DIM, DEG, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart,
+                                                               max_iters, Q, w, w64, partial, npartial, out, phase,
+                                                               s)))
 }
 
 #define DG_INSTANTIATE_OPS(DIM, T)                                                                              \
@@ -150,7 +159,8 @@ int launch_gmres(const dg_mesh* m, const T* h, const T* b, T* x, T alpha, double
   template int launch_div<DIM, T>(const dg_mesh*, const T*, T*, T*, cudaStream_t, const int*);                 \
   template int launch_helmholtz<DIM, T>(const dg_mesh*, const T*, const T*, T*, T, T*, T*, cudaStream_t,       \
                                         const int*);                                                            \
-  template int launch_gmres<DIM, T>(const dg_mesh*, const T*, const T*, T*, T, double, int, int, T*, T*, double*, \
-                                    int, double*, cudaStream_t);
+  template int launch_gmres<DIM, T>(const dg_mesh*, const double*, const T*, const double*, double*, double,     \
+                                    double, double, int, int, T*, T*, double*, double*, int, double*,            \
+                                    unsigned long long*, cudaStream_t);
 
 }  // namespace dg

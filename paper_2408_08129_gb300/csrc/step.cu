@@ -40,7 +40,7 @@ struct dg_state {
   double* g = nullptr;    // [dim][Nn]
   double* r64 = nullptr;  // FP64 outer residual
   double* solve_out = nullptr;  // [64][4] per-solve results of one step
-  float* f32 = nullptr;   // FP32 inner: h, rhs, delta
+  float* f32 = nullptr;   // FP32 Krylov: h, rhs, delta [3 Nn]
   int* flag = nullptr;    // non-finite flag
   dg::Gmres<double> gm64;
   dg::Gmres<float> gm32;
@@ -228,12 +228,20 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
   };
   GmresResult res;
   int rc;
+  unsigned long long* phase = S->ctx->prof ? S->ctx->d_phase : nullptr;
+  const int npart = (restart + 1) * kDotBlocks;
+  if (o->fused) {
+    ProfScope ps(S->ctx, DG_PROF_GMRES, s);
+    if (o->precision == DG_FP64)
+      return op_gmres<double>(m, S->h, S->h, S->rhs, S->p, alpha, o->tol, 0.0, restart, o->max_iters, S->gm64.Q,
+                              S->gm64.w, S->gm64.w, S->gm64.d.partial, npart, out, phase, s);
+    float* h32 = S->f32;
+    to_f32_kernel<<<gridn(Nn), 256, 0, s>>>(S->h, h32, Nn);
+    count_launches(S->ctx, 1);
+    return op_gmres<float>(m, S->h, h32, S->rhs, S->p, alpha, o->tol, o->inner_tol, restart, o->max_iters,
+                           S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, npart, out, phase, s);
+  }
   if (o->precision == DG_FP64) {
-    if (o->fused) {
-      ProfScope ps(S->ctx, DG_PROF_GMRES, s);
-      return op_gmres<double>(m, S->h, S->rhs, S->p, alpha, o->tol, restart, o->max_iters, S->gm64.Q, S->gm64.w,
-                              S->gm64.d.partial, (restart + 1) * kDotBlocks, out, s);
-    }
     rc = S->gm64.solve(S->ctx, A64, S->rhs, S->p, o->tol, o->max_iters, s, &res);
     if (rc != DG_OK) return rc;
     const double host[4] = {(double)res.iters, res.rel, res.converged ? 1.0 : 0.0, 0.0};
@@ -275,21 +283,8 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
     to_f32_kernel<<<gridn(Nn), 256, 0, s>>>(S->r64, r32, Nn);
     zero_f32_kernel<<<gridn(Nn), 256, 0, s>>>(d32, Nn);
     count_launches(S->ctx, 2);
-    if (o->fused) {
-      double h4[4];
-      {
-        ProfScope ps(S->ctx, DG_PROF_GMRES, s);
-        rc = op_gmres<float>(m, h32, r32, d32, (float)alpha, o->inner_tol, restart, o->max_iters, S->gm32.Q,
-                             S->gm32.w, S->gm32.d.partial, (restart + 1) * kDotBlocks, S->gm32.d.scal, s);
-      }
-      if (rc != DG_OK) return rc;
-      DG_CUDA(cudaMemcpyAsync(h4, S->gm32.d.scal, sizeof(h4), cudaMemcpyDeviceToHost, s));
-      DG_CUDA(cudaStreamSynchronize(s));
-      inner += (int)h4[0];
-    } else {
-      if ((rc = S->gm32.solve(S->ctx, A32, r32, d32, o->inner_tol, o->max_iters, s, &res)) != DG_OK) return rc;
-      inner += res.iters;
-    }
+    if ((rc = S->gm32.solve(S->ctx, A32, r32, d32, o->inner_tol, o->max_iters, s, &res)) != DG_OK) return rc;
+    inner += res.iters;
     add_f32_kernel<<<gridn(Nn), 256, 0, s>>>(S->p, d32, Nn);
     count_launches(S->ctx, 1);
     ++refine;
@@ -299,6 +294,20 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
   DG_CUDA(cudaStreamSynchronize(s));
   st->refine_steps += refine;
   return DG_OK;
+}
+
+// The explicit tendencies, gradients and divergences of the step enter the
+// new state directly, with no correction step after them, so they stay in
+// FP64 in both precision modes; the FP32 form puts the Krylov mat-vecs (the
+// bulk of the work) in FP32 and recovers FP64 accuracy by the FP64 residual.
+int step_explicit(dg_state* S, const double* U, double* E, cudaStream_t s) {
+  return op_explicit<double>(S->mesh, U, E, S->mesh->d_face_scratch64, false, s, nullptr);
+}
+int step_grad(dg_state* S, const double* p, double* g, cudaStream_t s) {
+  return op_grad<double>(S->mesh, p, nullptr, g, S->mesh->d_face_scratch64, s, nullptr);
+}
+int step_div(dg_state* S, const double* f, double* out, cudaStream_t s) {
+  return op_div<double>(S->mesh, f, out, S->mesh->d_face_scratch64, s, nullptr);
 }
 
 }  // namespace
@@ -339,7 +348,8 @@ extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_op
   auto rup = [](size_t n) { return (n + 31) & ~(size_t)31; };
   const size_t nd = 7 * rup((size_t)V * Nn) + 4 * rup((size_t)dim * Nn) + 8 * rup((size_t)Nn) + rup(8) + rup(256);
   cudaError_t e = cudaSetDevice(ctx->device);
-  if (e == cudaSuccess) e = cudaMalloc(&S->block, nd * sizeof(double) + (size_t)Nn * 3 * sizeof(float) + 1024);
+  const size_t nf32 = (size_t)Nn * 3 + 256;
+  if (e == cudaSuccess) e = cudaMalloc(&S->block, nd * sizeof(double) + nf32 * sizeof(float) + 1024);
   if (e != cudaSuccess) {
     delete S;
     return cuda_fail(e, "state allocation");
@@ -426,7 +436,7 @@ extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double 
   const unsigned gb = gridn(Nn);
   const double grav = m->desc.gravity;
   const MeshView<double>& mv = m->v64;
-  double* fs = m->d_face_scratch64;
+
   int rc = DG_OK;
   int status = DG_OK;
   ProfScope step_scope(ctx, DG_PROF_STEP, s);
@@ -438,11 +448,11 @@ extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double 
   // stage 1: U^(1) = U^n
   pressure_kernel<<<gb, 256, 0, s>>>(S->U, mv.pb, Nn, dim, S->p_prev, S->h);
   count_launches(S->ctx, 1);
-  RUN(op_explicit<double>(m, S->U, S->E[0], fs, false, s, nullptr));
-  RUN(op_grad<double>(m, S->p_prev, nullptr, S->g, fs, s, nullptr));
+  RUN(step_explicit(S, S->U, S->E[0], s));
+  RUN(step_grad(S, S->p_prev, S->g, s));
   hm_kernel<<<gb, 256, 0, s>>>(S->h, S->U + Nn, Nn, dim, S->tmpv);
   count_launches(S->ctx, 1);
-  RUN(op_div<double>(m, S->tmpv, S->tmps, fs, s, nullptr));
+  RUN(step_div(S, S->tmpv, S->tmps, s));
   implicit_terms_kernel<<<gb, 256, 0, s>>>(S->U, mv.rhob, S->g, S->tmps, grav, Nn, dim, S->I[0]);
   count_launches(S->ctx, 1);
   RUN(check("stage 1"));
@@ -464,24 +474,24 @@ extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double 
       picard_prep_kernel<<<gb, 256, 0, s>>>(S->p, mv.pb, S->rho, S->mk, S->mhat, S->Ehat, Nn, dim, S->h, S->rhs,
                                             S->tmpv);
       count_launches(S->ctx, 1);
-      RUN(op_div<double>(m, S->tmpv, S->tmps, fs, s, nullptr));
+      RUN(step_div(S, S->tmpv, S->tmps, s));
       axpy_kernel<<<gb, 256, 0, s>>>(S->rhs, S->tmps, -dta, Nn);
       count_launches(S->ctx, 1);
       RUN(check("picard"));
       if (nsolve >= 64) return fail(DG_EINVAL, "too many Picard iterations per step (at most 32)");
       RUN(helmholtz_solve(S, &o, dta * dta, &st, S->solve_out + 4 * nsolve, s));
       ++nsolve;
-      RUN(op_grad<double>(m, S->p, nullptr, S->g, fs, s, nullptr));
+      RUN(step_grad(S, S->p, S->g, s));
       momentum_kernel<<<gb, 256, 0, s>>>(S->mhat, S->g, dta, (int64_t)dim * Nn, S->mk);
       count_launches(S->ctx, 1);
     }
     stage_state_kernel<<<gb, 256, 0, s>>>(S->rho, S->mk, S->p, mv.pb, Nn, dim, S->Ui);
     count_launches(S->ctx, 1);
-    RUN(op_explicit<double>(m, S->Ui, S->E[i], fs, false, s, nullptr));
+    RUN(step_explicit(S, S->Ui, S->E[i], s));
     if (i == 1) {
       hm_kernel<<<gb, 256, 0, s>>>(S->h, S->mk, Nn, dim, S->tmpv);
       count_launches(S->ctx, 1);
-      RUN(op_div<double>(m, S->tmpv, S->tmps, fs, s, nullptr));
+      RUN(step_div(S, S->tmpv, S->tmps, s));
       implicit_terms_kernel<<<gb, 256, 0, s>>>(S->Ui, mv.rhob, S->g, S->tmps, grav, Nn, dim, S->I[1]);
       count_launches(S->ctx, 1);
     }

@@ -218,13 +218,19 @@ def test_imex_steps_hill2d(dg, ctx):
     assert err < 1e-10, err
 
 
-def test_imex_fp32_refined_step(dg, ctx):
-    """FP32 inner GMRES inside FP64 refinement reaches the same FP64 tolerance."""
+@pytest.mark.parametrize("fused", [1, 0])
+def test_imex_fp32_refined_step(dg, ctx, fused):
+    """FP32 Krylov mat-vecs and basis inside FP64 iterative refinement.
+
+    The FP64 residual at every restart drives each Helmholtz solve to the FP64
+    tolerance, so after 10 steps the deviation from the background agrees
+    with the FP64 oracle to 1e-8 (the FP32-refined target).
+    """
     case = make_case("bubble2d", 0)
-    opts = dg.solver_opts(tol=1e-12, precision=dg.DG_FP32, inner_tol=1e-4)
+    opts = dg.solver_opts(tol=1e-12, precision=dg.DG_FP32, inner_tol=1e-4, fused=fused)
     U, Ur, ref = _run_steps(dg, ctx, case, 10, opts)
-    err = _per_var_rel(U - ref.Ubg, Ur - ref.Ubg)
-    assert err < 1e-8, err
+    assert _per_var_rel(U, Ur) < 1e-10
+    assert _per_var_rel(U - ref.Ubg, Ur - ref.Ubg) < 1e-8
 
 
 def test_rest_state_stays_at_rest(dg, ctx):

@@ -35,7 +35,11 @@ sys.path.insert(0, ROOT)
 P_VOL = {2: 25, 3: 45}
 P_FACE = {2: 70, 3: 90}
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz (nominal 1.25 TF)
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel as it
+# stands (profiles/gmres_persistent_hill2d.md); set to None whenever that kernel changes
+NCU_TRAFFIC_BYTES = {("hill2d", "gmres"): 5.8176e6 + 0.377088e6}
 
 
 def algorithmic(dim, degree, n_nodes, kind, s=8):
@@ -151,6 +155,67 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def apply_sweep(dg, torch, case_name, reps=10):
+    """Throughput of the operator applies on a mesh whose vectors exceed L2 (FP64 and FP32)."""
+    from workloads import make_case
+
+    case = make_case(case_name, 0)
+    ctx = dg.Context(torch.cuda.current_device())
+    mesh = dg.Mesh(ctx, case)
+    hbm, src = measured_peaks()
+    stream = torch.cuda.current_stream()
+    U = torch.empty(mesh.shape(), dtype=torch.float64, device="cuda")
+    dg.dg_init_state(ctx, mesh, "inflow", [10.0], U)
+    Ubg = torch.empty_like(U)
+    dg.dg_background(ctx, mesh, Ubg)
+    U += 1e-3 * torch.randn_like(U) * Ubg.abs().clamp(min=1.0)
+    Up32 = (U - Ubg).float()
+    shp = (mesh.n_cells, mesh.nodes_per_cell)
+    p64 = 100.0 * torch.randn(shp, dtype=torch.float64, device="cuda")
+    h64 = torch.full(shp, 3.5e5, dtype=torch.float64, device="cuda")
+    p32, h32 = p64.float(), h64.float()
+    out = {}
+
+    def timeit(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    n = mesh.n_nodes
+    for prec, name, s_b, peak in ((dg.DG_FP64, "fp64", 8, FP64_PEAK_TFLOPS), (dg.DG_FP32, "fp32", 4, FP32_PEAK_TFLOPS)):
+        Uin = U if prec == dg.DG_FP64 else Up32
+        R = torch.empty_like(Uin)
+        t = timeit(lambda: dg.dg_apply_explicit(ctx, mesh, Uin, R, prec, dg.DG_TERMS_FULL))
+        fl, by = algorithmic(case.dim, case.degree, n, "explicit", s_b)
+        out["explicit_" + name] = {"ms": t, "dof_per_s": mesh.n_dof / (t / 1e3), "alg_gbs": by / (t / 1e3) / 1e9,
+                                   "hbm_frac": by / (t / 1e3) / 1e9 / hbm, "tflops": fl / (t / 1e3) / 1e12,
+                                   "alu_frac": fl / (t / 1e3) / 1e12 / peak}
+        pp, hh = (p64, h64) if prec == dg.DG_FP64 else (p32, h32)
+        Ap = torch.empty_like(pp)
+        t = timeit(lambda: dg.dg_apply_implicit(ctx, mesh, hh, pp, Ap, 1.0, prec))
+        fl, by = algorithmic(case.dim, case.degree, n, "helmholtz", s_b)
+        out["helmholtz_" + name] = {"ms": t, "dof_per_s": n / (t / 1e3), "alg_gbs": by / (t / 1e3) / 1e9,
+                                    "hbm_frac": by / (t / 1e3) / 1e9 / hbm, "tflops": fl / (t / 1e3) / 1e12,
+                                    "alu_frac": fl / (t / 1e3) / 1e12 / peak}
+    out["workload"] = "%s: %d cells, degree %d, %d DoF (vectors larger than L2)" % (
+        case_name, mesh.n_cells, case.degree, mesh.n_dof)
+    out["hbm_peak_gbs"] = hbm
+    out["peaks"] = "HBM %s; FP64 %.3f and FP32 %.1f TFLOP/s derived from SM count and clock" % (
+        src, FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS)
+    mesh.close()
+    ctx.close()
+    return out
+
+
 METRIC = "DG apply DoF/s fp64 vs fp32, %HBM peak; ensemble steps/s, p50/p99 latency"
 CONFIG = {
     "hill2d": {
@@ -176,6 +241,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hill2d", choices=sorted(CONFIG))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the operator-apply sweep on the large 3D mesh")
+    ap.add_argument("--sweep-workload", default="hill3d_big")
+    ap.add_argument("--sweep-only", action="store_true", help="run only the operator-apply sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -190,6 +258,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.sweep_only:
+        print(json.dumps({"applies": apply_sweep(dg, torch, args.sweep_workload)}))
+        return
     if world > 1:
         import torch.distributed as dist
 
@@ -315,7 +386,8 @@ def main():
     roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "peak_source": "derived FP64 rate: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
-            "traffic": None, "avg_launch_us": avg_ms * 1e3, "launches": cats[dom]["count"],
+            "traffic": NCU_TRAFFIC_BYTES.get((args.workload, dom)), "traffic_unit": "bytes per launch",
+            "avg_launch_us": avg_ms * 1e3, "launches": cats[dom]["count"],
             "hbm_peak_gbs": hbm, "hbm_peak_source": peak_src}
 
     line = {
@@ -333,6 +405,8 @@ def main():
         "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(local),
     }
+    if rank == 0 and not args.no_sweep:
+        line["applies"] = apply_sweep(dg, torch, args.sweep_workload)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(args.workload, 12.0)
     if rank == 0:

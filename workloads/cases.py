@@ -325,7 +325,7 @@ def hill3d(seed: int = 0, degree: int = 3, base=(32, 32, 16), name="hill3d") -> 
     rng = np.random.default_rng(seed)
     extent = (40e3, 40e3, 20e3)
     jit = rng.uniform(-1e3, 1e3, size=2)
-    band = 1.5e3 * (16 / base[2]) if base[2] > 16 else 1.5e3
+    band = 1.5e3
 
     def rule(level, centre):
         return level == 0 and centre[2] < band

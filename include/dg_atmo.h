@@ -260,6 +260,22 @@ int dg_state_download(dg_state* state, double* host_U);
 int imex_rk2_step(dg_ctx* ctx, const dg_mesh* mesh, dg_state* state, double dt, const dg_solver_opts* opts,
                   dg_step_stats* stats, void* stream);
 
+/* Ensemble step (batching of many uneven members, one persistent kernel per
+ * stage): advance n independent members -- each with its own mesh and state,
+ * any mix of dimensions and degrees, the same solver options -- by one IMEX-RK2
+ * step each, member i with step dt[i].  Each phase of the step is enqueued for
+ * every member before the next phase; the Helmholtz solves of one Picard
+ * iteration of all members run in ONE cooperative launch per (dimension,
+ * degree, precision) group, each member on its own share of the CTAs (in
+ * proportion to its node count) with its own barrier, so members progress and
+ * converge independently inside the launch.  Each member's result equals the
+ * result of imex_rk2_step on that member alone (same kernels, same order).
+ * Two members may not share a mesh (DG_EINVAL).  stats[n] and statuses[n] may
+ * be NULL; returns the first non-OK member status, DG_ETIMEOUT if a barrier
+ * wait of the batched launch ran out (bounded at 2 s; never expected). */
+int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states, const double* dt,
+                  const dg_solver_opts* opts, dg_step_stats* stats, int* statuses, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,7 @@ from .api import (  # noqa: F401
     Mesh,
     State,
     dg_apply_div,
+    dg_batch_step,
     dg_apply_explicit,
     dg_apply_grad,
     dg_apply_implicit,

@@ -95,6 +95,7 @@ def _load():
         "dg_state_upload": (c_int, [P, P]),
         "dg_state_download": (c_int, [P, P]),
         "imex_rk2_step": (c_int, [P, P, P, c_double, ctypes.POINTER(SolverOpts), ctypes.POINTER(StepStats), P]),
+        "dg_batch_step": (c_int, [P, c_int, P, P, P, ctypes.POINTER(SolverOpts), P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -276,3 +276,25 @@ def imex_rk2_step(ctx, mesh, state, dt, opts=None, stream=None, raise_on_error=T
     if raise_on_error:
         check(rc, "imex_rk2_step")
     return {k: getattr(st, k) for k, _ in B.StepStats._fields_} | {"status": rc}
+
+
+def dg_batch_step(ctx, meshes, states, dts, opts=None, stream=None, raise_on_error=True):
+    """One IMEX-RK2 step of every member (mesh, state, dt); solves batched per (dim, degree, precision)."""
+    n = len(states)
+    if not (len(meshes) == n == len(dts)):
+        raise ValueError("meshes, states and dts must have the same length")
+    o = opts if opts is not None else solver_opts()
+    mh = (ctypes.c_void_p * n)(*[m.handle.value for m in meshes])
+    sh = (ctypes.c_void_p * n)(*[st.handle.value for st in states])
+    dt = (ctypes.c_double * n)(*[float(x) for x in dts])
+    stats = (B.StepStats * n)()
+    statuses = (ctypes.c_int * n)()
+    rc = lib.dg_batch_step(ctx.handle, n, mh, sh, dt, ctypes.byref(o), stats, statuses, _stream(stream))
+    if raise_on_error:
+        check(rc, "dg_batch_step")
+    out = []
+    for i in range(n):
+        d = {k: getattr(stats[i], k) for k, _ in B.StepStats._fields_}
+        d["status"] = statuses[i]
+        out.append(d)
+    return out

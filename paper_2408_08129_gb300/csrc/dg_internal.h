@@ -82,6 +82,8 @@ struct dg_ctx {
   long long prof_n[8] = {0};
   long long launches = 0;  // kernels launched through this context
   unsigned long long* d_phase = nullptr;  // [16] ns per fused-GMRES phase (profiling on)
+  void* d_batch = nullptr;  // workspace of batched solves (argument table, CTA map, barriers)
+  size_t batch_bytes = 0;
 };
 
 namespace dg {

@@ -48,7 +48,7 @@ struct GmresPArgs {
   double* w64;            // [n] FP64 residual mat-vec output (may alias w when TK = double)
   double* Gh;             // face scratch (dim*nf*NF doubles), reused as TK
   double* gv;             // [dim][n] gradient scratch (doubles), reused as TK
-  double* partial;        // >= gridDim.x doubles
+  double* partial;        // >= 2 x (CTAs of the solve) doubles
   double* out;            // [4]: iterations, relative residual, converged (0/1), ||b||
   unsigned long long* phase;  // optional [16] ns per phase accumulated by block 0 (NULL = off)
   double alpha;           // (a_ii dt)^2
@@ -65,7 +65,7 @@ enum GmresPhase {
 };
 
 struct PhaseClock {
-  unsigned long long* acc;
+  unsigned long long* acc;  // NULL = off; set only on the CTA that records
   unsigned long long last;
   __device__ __forceinline__ static unsigned long long now() {
     unsigned long long t;
@@ -73,12 +73,66 @@ struct PhaseClock {
     return t;
   }
   __device__ __forceinline__ void mark(int p) {
-    if (acc && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (acc && threadIdx.x == 0) {
       const unsigned long long t = now();
       acc[p] += t - last;
       last = t;
     }
   }
+};
+
+// Barrier over the CTAs working on one solve.  GridSync: the whole grid of a
+// cooperative launch (cooperative-groups barrier).  SubSync: the CTAs of one
+// member of a batched launch (a generation barrier on two global counters;
+// all CTAs of a cooperative launch are co-resident, so it cannot deadlock).
+// Its wait is bounded: after kBarrierTimeoutNs it raises the launch's error
+// flag and every barrier of the launch returns at once from then on, so a
+// fault can only end the kernel early, never hang it.
+struct GridSync {
+  cooperative_groups::grid_group grid;
+  int rank, size;
+  __device__ GridSync() : grid(cooperative_groups::this_grid()), rank(blockIdx.x), size(gridDim.x) {}
+  __device__ __forceinline__ void sync() { grid.sync(); }
+  __device__ __forceinline__ bool failed() const { return false; }
+};
+
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+
+struct SubSync {
+  int rank, size;
+  unsigned int* count;  // arrivals at the current barrier
+  unsigned int* gen;    // barrier generation
+  int* err;             // launch-wide error flag
+  int* sfail;           // shared-memory copy of err, read by every thread
+  __device__ __forceinline__ void sync() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (!*(volatile int*)err && size > 1) {
+        __threadfence();
+        const unsigned int g = *(volatile unsigned int*)gen;
+        const unsigned int arrived = atomicAdd(count, 1u) + 1u;
+        if (arrived == (unsigned int)size) {
+          atomicExch(count, 0u);
+          __threadfence();
+          atomicAdd(gen, 1u);
+        } else {
+          const unsigned long long t0 = PhaseClock::now();
+          while (*(volatile unsigned int*)gen == g) {
+            if (*(volatile int*)err) break;
+            if (PhaseClock::now() - t0 > kBarrierTimeoutNs) {
+              atomicExch(err, 1);
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+        __threadfence();
+      }
+      *sfail = *(volatile int*)err;
+    }
+    __syncthreads();
+  }
+  __device__ __forceinline__ bool failed() const { return *(volatile int*)sfail != 0; }
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sred) {
@@ -115,29 +169,27 @@ __device__ __forceinline__ double block_sum_k(TK v, double* sred) {
 }
 
 // out = scale * (ident p/(gamma-1) - alpha div(h grad p)) (four phases, four grid barriers)
-template <int DIM, int DEG, typename T>
+template <int DIM, int DEG, typename T, class Sync>
 __device__ __forceinline__ void pmatvec(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p, T scale,
-                                        T* out,
-                                        T* Gh, T* gv, cooperative_groups::grid_group& grid, T* scell, const T* sD,
-                                        const T* sDw, const T* sIt, PhaseClock& pc) {
+                                        T* out, T* Gh, T* gv, Sync& sg, T* scell, const T* sD, const T* sDw,
+                                        const T* sIt, PhaseClock& pc) {
   using S = Shape<DIM, DEG>;
   const int64_t nfi = (int64_t)(mv.nconf + mv.nsub) * S::NF;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)sg.size * blockDim.x;
+  const int64_t tid = (int64_t)sg.rank * blockDim.x + threadIdx.x;
   const int64_t nb = (mv.n_cells + S::CPB - 1) / S::CPB;
   for (int64_t t = tid; t < nfi; t += stride) grad_face_item<DIM, DEG, T>(mv, p, Gh, t);
-  grid.sync();
+  sg.sync();
   pc.mark(PH_GRAD_FACE);
-  for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x)
-    grad_cell_batch<DIM, DEG, T>(mv, p, h, Gh, gv, bt, scell, sD, sIt);
-  grid.sync();
+  for (int64_t bt = sg.rank; bt < nb; bt += sg.size) grad_cell_batch<DIM, DEG, T>(mv, p, h, Gh, gv, bt, scell, sD, sIt);
+  sg.sync();
   pc.mark(PH_GRAD_CELL);
   for (int64_t t = tid; t < nfi; t += stride) div_face_item<DIM, DEG, T>(mv, gv, Gh, t);
-  grid.sync();
+  sg.sync();
   pc.mark(PH_DIV_FACE);
-  for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x)
+  for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
     div_cell_batch<DIM, DEG, T, true>(mv, gv, Gh, p, alpha, scale, ident, out, bt, scell, sDw, sIt);
-  grid.sync();
+  sg.sync();
   pc.mark(PH_DIV_CELL);
 }
 
@@ -145,9 +197,9 @@ __device__ __forceinline__ void pmatvec(const MeshView<T>& mv, const T* h, T alp
 // j < nv-1 and v_{nv-1} = w itself (so the last entry is ||w||^2 by chunks)
 template <typename TK>
 __device__ __forceinline__ void pdots(const TK* Q, int64_t n, const TK* w, int nv, int C, double* partial,
-                                      double* sred) {
+                                      double* sred, int rank, int size) {
   const int64_t chunk = (n + C - 1) / C;
-  for (int it = blockIdx.x; it < nv * C; it += gridDim.x) {
+  for (int it = rank; it < nv * C; it += size) {
     const int j = it / C, c = it % C;
     const int64_t lo = (int64_t)c * chunk;
     const int64_t hi = lo + chunk < n ? lo + chunk : n;
@@ -188,13 +240,11 @@ __device__ __forceinline__ TK lincomb(const TK* __restrict__ Q, int64_t n, int64
   return acc;
 }
 
-template <int DIM, int DEG, typename TK>
-__global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a) {
-  namespace cg = cooperative_groups;
-  cg::grid_group grid = cg::this_grid();
+template <int DIM, int DEG, typename TK, class Sync>
+__device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw,
+                                           bool record) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = a.m;
   double* sigma = (double*)smem_raw;  // [m+1] scale of q_j (1/beta for j = 0, else 1)
   double* hh = sigma + (m + 1);       // [m+2] Gram-Schmidt coefficients (+ ||w||^2 in [k+1])
@@ -231,11 +281,11 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
     sItk[q] = a.mvk.tab[S::T_IT + q];
   }
   __syncthreads();
-  PhaseClock pc{a.phase, PhaseClock::now()};
+  PhaseClock pc{record ? a.phase : nullptr, PhaseClock::now()};
 
   const int64_t n = a.n;
-  const int G = gridDim.x;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int G = sg.size;
+  const int64_t tid = (int64_t)sg.rank * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)G * blockDim.x;
   const int64_t chunk1 = (n + G - 1) / G;
   const bool mixed = sizeof(TK) != sizeof(double);
@@ -244,14 +294,14 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
 
   // ||b||
   {
-    const int64_t lo = (int64_t)blockIdx.x * chunk1;
+    const int64_t lo = (int64_t)sg.rank * chunk1;
     const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
     double acc = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += a.b[i] * a.b[i];
     const double s = block_sum(acc, sred);
-    if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+    if (threadIdx.x == 0) a.partial[sg.rank] = s;
   }
-  grid.sync();
+  sg.sync();
   stage_partials(a.partial, G, spart);
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -262,7 +312,7 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
   const double bn = sc[0];
   if (bn == 0.0) {
     for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (sg.rank == 0 && threadIdx.x == 0) {
       a.out[0] = 0;
       a.out[1] = 0;
       a.out[2] = 1;
@@ -270,17 +320,17 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
     }
     return;
   }
-  grid.sync();  // partial reused below
+  sg.sync();  // partial reused below
 
   int total = 0;
   double rel = 1.0;
   bool converged = false;
   while (true) {
     // r = b - A x with the FP64 operator -> q_0 (unnormalised), beta
-    pmatvec<DIM, DEG, double>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.Gh, a.gv, grid, scell64, sD64,
-                              sDw64, sIt64, pc);
+    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.Gh, a.gv, sg, scell64, sD64,
+                                    sDw64, sIt64, pc);
     {
-      const int64_t lo = (int64_t)blockIdx.x * chunk1;
+      const int64_t lo = (int64_t)sg.rank * chunk1;
       const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
       double acc = 0.0;
       for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
@@ -289,9 +339,9 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
         acc += r * r;
       }
       const double s = block_sum(acc, sred);
-      if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+      if (threadIdx.x == 0) a.partial[sg.rank] = s;
     }
-    grid.sync();
+    sg.sync();
     pc.mark(PH_RESIDUAL);
     stage_partials(a.partial, G, spart);
     if (threadIdx.x == 0) {
@@ -308,6 +358,7 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
     }
     __syncthreads();
     rel = sc[2] / bn;
+    if (sg.failed()) break;
     if (sflag[1]) {
       converged = true;
       break;
@@ -319,14 +370,14 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
       const TK* qk = a.Q + (int64_t)k * n;
       // Arnoldi on B = A - I/(gamma-1): same Krylov space, Hessenberg of A = that of B
       // plus 1/(gamma-1) on the diagonal; w = B q_k has no large component along q_k
-      pmatvec<DIM, DEG, TK>(a.mvk, a.hk, (TK)a.alpha, TK(0), qk, (TK)sigma[k], a.w, Ghk, gvk, grid, scellk, sDk,
-                            sDwk, sItk, pc);
+      pmatvec<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(0), qk, (TK)sigma[k], a.w, Ghk, gvk, sg, scellk,
+                                  sDk, sDwk, sItk, pc);
       // h_j = q_j . w (j <= k) and ||w||^2, one pass
       const int nv = k + 2;
       int C = G / nv;
       if (C < 1) C = 1;
-      pdots<TK>(a.Q, n, a.w, nv, C, a.partial, sred);
-      grid.sync();
+      pdots<TK>(a.Q, n, a.w, nv, C, a.partial, sred, sg.rank, sg.size);
+      sg.sync();
       pc.mark(PH_DOTS);
       stage_partials(a.partial, nv * C, spart);
       if (threadIdx.x < nv) {
@@ -355,11 +406,11 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
         for (int64_t i = tid; i < n; i += gstride) qn[i] = (a.w[i] - lincomb(a.Q, n, i, coef, k + 1)) * invk;
       } else {
         // second Gram-Schmidt pass
-        if (a.phase && blockIdx.x == 0 && threadIdx.x == 0) a.phase[14] += 1;
+        if (pc.acc && threadIdx.x == 0) a.phase[14] += 1;
         for (int64_t i = tid; i < n; i += gstride) a.w[i] -= lincomb(a.Q, n, i, coef, k + 1);
-        grid.sync();
-        pdots<TK>(a.Q, n, a.w, nv, C, a.partial, sred);
-        grid.sync();
+        sg.sync();
+        pdots<TK>(a.Q, n, a.w, nv, C, a.partial, sred, sg.rank, sg.size);
+        sg.sync();
         pc.mark(PH_REORTH);
         stage_partials(a.partial, nv * C, spart);
         if (threadIdx.x < nv) {
@@ -410,12 +461,12 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
         sflag[1] = resid <= a.tol * bn ? 1 : 0;
         sflag[0] = (resid <= cycle_floor || hn == 0.0 || total + 1 >= a.max_iters) ? 1 : 0;
       }
-      grid.sync();
+      sg.sync();
       pc.mark(PH_UPDATE);
       ++total;
       kd = k + 1;
       rel = sc[1] / bn;
-      if (sflag[0]) break;
+      if (sflag[0] || sg.failed()) break;
     }
     // x += sum_j y_j q_j, y from the rotated Hessenberg system
     if (threadIdx.x == 0) {
@@ -428,7 +479,7 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
     }
     __syncthreads();
     for (int64_t i = tid; i < n; i += gstride) a.x[i] += (double)lincomb(a.Q, n, i, coef, kd);
-    grid.sync();
+    sg.sync();
     pc.mark(PH_SOLUTION);
     // plain FP64 GMRES trusts its residual estimate; the mixed form re-checks
     // with the FP64 residual at the next restart
@@ -436,15 +487,47 @@ __global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a)
       converged = true;
       break;
     }
-    if (total >= a.max_iters) break;
+    if (total >= a.max_iters || sg.failed()) break;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sg.rank == 0 && threadIdx.x == 0) {
     a.out[0] = total;
     a.out[1] = rel;
-    a.out[2] = converged ? 1.0 : 0.0;
+    a.out[2] = (converged && !sg.failed()) ? 1.0 : 0.0;
     a.out[3] = bn;
-    if (a.phase) a.phase[PH_ITERS] += (unsigned long long)total;
+    if (pc.acc) a.phase[PH_ITERS] += (unsigned long long)total;
   }
+}
+
+template <int DIM, int DEG, typename TK>
+__global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  GridSync sg;
+  gmres_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
+}
+
+// Many independent solves in one cooperative launch: CTA b works on member
+// cta_member[b] as its rank cta_rank[b] of member_ctas[member] CTAs, with the
+// member's own barrier; members progress and finish independently.
+struct BatchMap {
+  const int* cta_member;
+  const int* cta_rank;
+  const int* member_ctas;
+  unsigned int* bar_count;  // [members]
+  unsigned int* bar_gen;    // [members]
+  int* err;                 // [1]
+};
+
+template <int DIM, int DEG, typename TK>
+__global__ void __launch_bounds__(256) gmres_batched_kernel(const GmresPArgs<TK>* __restrict__ args, BatchMap map) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sfail;
+  const int mem = map.cta_member[blockIdx.x];
+  if (threadIdx.x == 0) sfail = 0;
+  __syncthreads();
+  SubSync sg{map.cta_rank[blockIdx.x], map.member_ctas[mem], map.bar_count + mem, map.bar_gen + mem, map.err,
+             &sfail};
+  const GmresPArgs<TK> a = args[mem];
+  gmres_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
 }
 
 template <int DIM, int DEG, typename TK>

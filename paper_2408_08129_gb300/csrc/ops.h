@@ -43,6 +43,40 @@ template <int DIM, typename TK>
 int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
                  double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64,
                  double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s);
+// One member of a batched solve (see launch_gmres_batched).
+template <typename TK>
+struct GmresItem {
+  const dg_mesh* m;
+  const double* h64;
+  const TK* hk;
+  const double* b;
+  double* x;
+  double alpha, tol, inner_tol;
+  int max_iters;
+  TK* Q;
+  TK* w;
+  double* w64;
+  double* partial;
+  int npartial;
+  double* out;
+};
+
+// Solve every item's Helmholtz system in ONE cooperative launch (more if the
+// items outnumber the co-resident CTAs).  All items share dimension, degree
+// and TK, and no two share a mesh (the mesh holds the mat-vec scratch).  The
+// CTAs are split among the items in proportion to their node counts; each
+// item's solve runs on its own CTAs with its own barrier.  *err (device int)
+// is set if a barrier wait ran out.
+template <int DIM, typename TK>
+int launch_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int restart, int* err,
+                         cudaStream_t s);
+template <typename TK>
+inline int op_gmres_batched(dg_ctx* ctx, int dim, const GmresItem<TK>* items, int n_items, int restart, int* err,
+                            cudaStream_t s) {
+  return dim == 2 ? launch_gmres_batched<2, TK>(ctx, items, n_items, restart, err, s)
+                  : launch_gmres_batched<3, TK>(ctx, items, n_items, restart, err, s);
+}
+
 template <typename TK>
 inline int op_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
                     double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64,

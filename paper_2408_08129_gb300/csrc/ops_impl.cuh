@@ -1,7 +1,10 @@
 // Launcher bodies; included once per (dimension, precision) translation unit.
 #pragma once
 
+#include <algorithm>
+#include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "k_explicit.cuh"
 #include "k_gmres.cuh"
@@ -107,6 +110,112 @@ int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b
   return DG_OK;
 }
 
+template <int DIM, int DEG, typename TK>
+int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int restart, int* err,
+                      cudaStream_t s) {
+  auto kern = gmres_batched_kernel<DIM, DEG, TK>;
+  const size_t smem = gmres_smem_bytes<DIM, DEG, TK>(restart);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "batched gmres smem attribute");
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "batched gmres occupancy");
+  if (per_sm < 1) return fail(DG_ECUDA, "batched GMRES kernel does not fit on an SM");
+  const int gtot = ctx->sm_count * (per_sm < 2 ? per_sm : 2);
+  for (int first = 0; first < n_items; first += gtot) {
+    const int B = std::min(gtot, n_items - first);
+    const GmresItem<TK>* it = items + first;
+    // CTAs in proportion to node counts, at least one each
+    std::vector<int> ctas(B, 1);
+    double wsum = 0.0;
+    for (int i = 0; i < B; ++i) wsum += (double)it[i].m->Nn;
+    int used = 0;
+    for (int i = 0; i < B; ++i) {
+      const int cap = std::max(1, std::min(512, it[i].npartial / 2));
+      ctas[i] = std::min(cap, std::max(1, (int)((double)(gtot - B) * it[i].m->Nn / wsum) + 1));
+      used += ctas[i];
+    }
+    while (used > gtot) {  // rounding overshoot: take from the largest
+      int j = (int)(std::max_element(ctas.begin(), ctas.end()) - ctas.begin());
+      if (ctas[j] <= 1) break;
+      --ctas[j];
+      --used;
+    }
+    std::vector<GmresPArgs<TK>> args(B);
+    std::vector<int> cta_member, cta_rank;
+    for (int i = 0; i < B; ++i) {
+      GmresPArgs<TK>& a = args[i];
+      const dg_mesh* m = it[i].m;
+      a.mv64 = m->v64;
+      a.mvk = view<TK>(m);
+      a.h64 = it[i].h64;
+      a.hk = it[i].hk;
+      a.b = it[i].b;
+      a.x = it[i].x;
+      a.Q = it[i].Q;
+      a.w = it[i].w;
+      a.w64 = it[i].w64;
+      a.Gh = m->d_face_scratch64;
+      a.gv = m->d_vec_scratch64;
+      a.partial = it[i].partial;
+      a.out = it[i].out;
+      a.phase = nullptr;
+      a.alpha = it[i].alpha;
+      a.tol = it[i].tol;
+      a.inner_tol = it[i].inner_tol;
+      a.m = restart;
+      a.max_iters = it[i].max_iters;
+      a.n = m->Nn;
+      for (int r = 0; r < ctas[i]; ++r) {
+        cta_member.push_back(i);
+        cta_rank.push_back(r);
+      }
+    }
+    const int G = (int)cta_member.size();
+    const size_t b_args = ((sizeof(GmresPArgs<TK>) * B) + 255) & ~(size_t)255;
+    const size_t b_map = (((size_t)2 * G + B) * sizeof(int) + 255) & ~(size_t)255;
+    const size_t b_bar = ((size_t)2 * B) * sizeof(unsigned int);
+    const size_t need = b_args + b_map + b_bar + 256;
+    if (need > ctx->batch_bytes) {
+      if (ctx->d_batch) {
+        DG_CUDA(cudaStreamSynchronize(s));
+        cudaFree(ctx->d_batch);
+      }
+      ctx->d_batch = nullptr;
+      ctx->batch_bytes = 0;
+      DG_CUDA(cudaMalloc(&ctx->d_batch, need * 2));
+      ctx->batch_bytes = need * 2;
+    }
+    std::vector<unsigned char> host(b_args + b_map, 0);
+    std::memcpy(host.data(), args.data(), sizeof(GmresPArgs<TK>) * B);
+    int* hm = (int*)(host.data() + b_args);
+    std::memcpy(hm, cta_member.data(), G * sizeof(int));
+    std::memcpy(hm + G, cta_rank.data(), G * sizeof(int));
+    std::memcpy(hm + 2 * G, ctas.data(), B * sizeof(int));
+    unsigned char* dev = (unsigned char*)ctx->d_batch;
+    DG_CUDA(cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    DG_CUDA(cudaMemsetAsync(dev + b_args + b_map, 0, b_bar, s));
+    BatchMap map;
+    const int* dm = (const int*)(dev + b_args);
+    map.cta_member = dm;
+    map.cta_rank = dm + G;
+    map.member_ctas = dm + 2 * G;
+    map.bar_count = (unsigned int*)(dev + b_args + b_map);
+    map.bar_gen = map.bar_count + B;
+    map.err = err;
+    const GmresPArgs<TK>* dargs = (const GmresPArgs<TK>*)dev;
+    count_launches(ctx, 1);
+    void* kargs[] = {(void*)&dargs, (void*)&map};
+    e = cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(256), kargs, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched GMRES launch");
+    // the argument table is rewritten by the next chunk: keep launches ordered
+    if (first + B < n_items) DG_CUDA(cudaStreamSynchronize(s));
+  }
+  return DG_OK;
+}
+
 }  // namespace
 
 #define DG_DEGREE_SWITCH(deg, ...)                         \
@@ -153,6 +262,13 @@ int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double
                                                                s)))
 }
 
+template <int DIM, typename TK>
+int launch_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int restart, int* err,
+                         cudaStream_t s) {
+  if (n_items <= 0) return DG_OK;
+  DG_DEGREE_SWITCH(items[0].m->degree, return (run_gmres_batched<DIM, DEG, TK>(ctx, items, n_items, restart, err, s)))
+}
+
 #define DG_INSTANTIATE_OPS(DIM, T)                                                                              \
   template int launch_explicit<DIM, T>(const dg_mesh*, const T*, T*, T*, bool, cudaStream_t, const int*);      \
   template int launch_grad<DIM, T>(const dg_mesh*, const T*, const T*, T*, T*, cudaStream_t, const int*);      \
@@ -161,6 +277,7 @@ int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double
                                         const int*);                                                            \
   template int launch_gmres<DIM, T>(const dg_mesh*, const double*, const T*, const double*, double*, double,     \
                                     double, double, int, int, T*, T*, double*, double*, int, double*,            \
-                                    unsigned long long*, cudaStream_t);
+                                    unsigned long long*, cudaStream_t);                                         \
+  template int launch_gmres_batched<DIM, T>(dg_ctx*, const GmresItem<T>*, int, int, int*, cudaStream_t);
 
 }  // namespace dg

@@ -12,7 +12,9 @@
 //    the kinetic energy lagged:  p'/(g-1) - (dt a_ii)^2 div(h grad p') =
 //    Ehat - p_bar/(g-1) - rho k - dt a_ii div(h mhat), solved by GMRES from the
 //    previous iterate; m = mhat - dt a_ii grad p'; rho E = p/(g-1) + rho k.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "krylov.cuh"
 #include "ops.h"
@@ -235,9 +237,7 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
     if (o->precision == DG_FP64)
       return op_gmres<double>(m, S->h, S->h, S->rhs, S->p, alpha, o->tol, 0.0, restart, o->max_iters, S->gm64.Q,
                               S->gm64.w, S->gm64.w, S->gm64.d.partial, npart, out, phase, s);
-    float* h32 = S->f32;
-    to_f32_kernel<<<gridn(Nn), 256, 0, s>>>(S->h, h32, Nn);
-    count_launches(S->ctx, 1);
+    float* h32 = S->f32;  // converted by phase_picard_pre
     return op_gmres<float>(m, S->h, h32, S->rhs, S->p, alpha, o->tol, o->inner_tol, restart, o->max_iters,
                            S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, npart, out, phase, s);
   }
@@ -420,102 +420,305 @@ extern "C" int dg_state_download(dg_state* S, double* host_U) {
   return DG_OK;
 }
 
-extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double dt, const dg_solver_opts* opts,
-                             dg_step_stats* stats, void* stream) {
-  if (!ctx || !m || !S || S->mesh != m) return fail(DG_EINVAL, "bad arguments");
-  if (!(dt > 0.0)) return fail(DG_EINVAL, "dt must be positive");
-  dg_solver_opts o;
-  dg_solver_opts_default(&o);
-  if (opts) o = *opts;
-  if (o.precision != DG_FP64 && o.precision != DG_FP32) return fail(DG_EINVAL, "bad precision");
-  if (o.picard < 1) return fail(DG_EINVAL, "picard must be >= 1");
-  dg_step_stats st{};
-  cudaStream_t s = (cudaStream_t)stream;
-  const int64_t Nn = S->Nn;
-  const int V = S->V, dim = S->dim;
-  const unsigned gb = gridn(Nn);
-  const double grav = m->desc.gravity;
-  const MeshView<double>& mv = m->v64;
+namespace dg {
+namespace {
 
-  int rc = DG_OK;
-  int status = DG_OK;
-  ProfScope step_scope(ctx, DG_PROF_STEP, s);
+// One member of a step: the state, its step size and options, and what the
+// phases below accumulate.  imex_rk2_step runs the phases for one member;
+// dg_batch_step runs each phase for every member and solves all members'
+// Helmholtz systems of a Picard iteration in one batched launch.
+struct Member {
+  dg_state* S = nullptr;
+  const dg_mesh* m = nullptr;
+  double dt = 0.0;
+  dg_solver_opts o{};
+  dg_step_stats st{};
   int nsolve = 0;
-#define RUN(x)                     \
-  do {                             \
-    if ((rc = (x)) != DG_OK) return rc; \
-  } while (0)
-  // stage 1: U^(1) = U^n
+  int flag = 0;
+};
+
+inline double stage_dta(const Member& M, int i) { return M.dt * AIM[i][i]; }
+
+int phase_stage1(Member& M, cudaStream_t s) {
+  dg_state* S = M.S;
+  const int64_t Nn = S->Nn;
+  const int dim = S->dim;
+  const unsigned gb = gridn(Nn);
+  const MeshView<double>& mv = M.m->v64;
+  int rc;
   pressure_kernel<<<gb, 256, 0, s>>>(S->U, mv.pb, Nn, dim, S->p_prev, S->h);
   count_launches(S->ctx, 1);
-  RUN(step_explicit(S, S->U, S->E[0], s));
-  RUN(step_grad(S, S->p_prev, S->g, s));
+  if ((rc = step_explicit(S, S->U, S->E[0], s)) != DG_OK) return rc;
+  if ((rc = step_grad(S, S->p_prev, S->g, s)) != DG_OK) return rc;
   hm_kernel<<<gb, 256, 0, s>>>(S->h, S->U + Nn, Nn, dim, S->tmpv);
   count_launches(S->ctx, 1);
-  RUN(step_div(S, S->tmpv, S->tmps, s));
-  implicit_terms_kernel<<<gb, 256, 0, s>>>(S->U, mv.rhob, S->g, S->tmps, grav, Nn, dim, S->I[0]);
+  if ((rc = step_div(S, S->tmpv, S->tmps, s)) != DG_OK) return rc;
+  implicit_terms_kernel<<<gb, 256, 0, s>>>(S->U, mv.rhob, S->g, S->tmps, M.m->desc.gravity, Nn, dim, S->I[0]);
   count_launches(S->ctx, 1);
-  RUN(check("stage 1"));
-  for (int i = 1; i <= 2; ++i) {
-    const double aii = AIM[i][i];
-    const double dta = dt * aii;
-    StageCoef c{};
-    c.nprev = i;
-    for (int j = 0; j < i; ++j) {
-      c.ae[j] = AEX[i][j];
-      c.ai[j] = AIM[i][j];
-    }
-    stage_combine_kernel<<<gb, 256, 0, s>>>(S->U, S->E[0], S->E[1], S->I[0], S->I[1], c, dt, dta, mv.rhob, grav, Nn,
-                                            dim, S->rho, S->mhat, S->Ehat);
-    count_launches(S->ctx, 1);
-    DG_CUDA(cudaMemcpyAsync(S->p, S->p_prev, Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    DG_CUDA(cudaMemcpyAsync(S->mk, S->mhat, (size_t)dim * Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    for (int it = 0; it < o.picard; ++it) {
-      picard_prep_kernel<<<gb, 256, 0, s>>>(S->p, mv.pb, S->rho, S->mk, S->mhat, S->Ehat, Nn, dim, S->h, S->rhs,
-                                            S->tmpv);
-      count_launches(S->ctx, 1);
-      RUN(step_div(S, S->tmpv, S->tmps, s));
-      axpy_kernel<<<gb, 256, 0, s>>>(S->rhs, S->tmps, -dta, Nn);
-      count_launches(S->ctx, 1);
-      RUN(check("picard"));
-      if (nsolve >= 64) return fail(DG_EINVAL, "too many Picard iterations per step (at most 32)");
-      RUN(helmholtz_solve(S, &o, dta * dta, &st, S->solve_out + 4 * nsolve, s));
-      ++nsolve;
-      RUN(step_grad(S, S->p, S->g, s));
-      momentum_kernel<<<gb, 256, 0, s>>>(S->mhat, S->g, dta, (int64_t)dim * Nn, S->mk);
-      count_launches(S->ctx, 1);
-    }
-    stage_state_kernel<<<gb, 256, 0, s>>>(S->rho, S->mk, S->p, mv.pb, Nn, dim, S->Ui);
-    count_launches(S->ctx, 1);
-    RUN(step_explicit(S, S->Ui, S->E[i], s));
-    if (i == 1) {
-      hm_kernel<<<gb, 256, 0, s>>>(S->h, S->mk, Nn, dim, S->tmpv);
-      count_launches(S->ctx, 1);
-      RUN(step_div(S, S->tmpv, S->tmps, s));
-      implicit_terms_kernel<<<gb, 256, 0, s>>>(S->Ui, mv.rhob, S->g, S->tmps, grav, Nn, dim, S->I[1]);
-      count_launches(S->ctx, 1);
-    }
-    std::swap(S->p, S->p_prev);
+  return check("stage 1");
+}
+
+int phase_stage_begin(Member& M, int i, cudaStream_t s) {
+  dg_state* S = M.S;
+  const int64_t Nn = S->Nn;
+  const int dim = S->dim;
+  StageCoef c{};
+  c.nprev = i;
+  for (int j = 0; j < i; ++j) {
+    c.ae[j] = AEX[i][j];
+    c.ai[j] = AIM[i][j];
   }
-  DG_CUDA(cudaMemsetAsync(S->flag, 0, sizeof(int), s));
-  final_kernel<<<gb, 256, 0, s>>>(S->Ui, S->E[0], S->E[1], S->E[2], dt * (BW[0] - AEX[2][0]),
-                                  dt * (BW[1] - AEX[2][1]), dt * (BW[2] - AEX[2][2]), (int64_t)V * Nn, S->U,
-                                  S->flag);
+  stage_combine_kernel<<<gridn(Nn), 256, 0, s>>>(S->U, S->E[0], S->E[1], S->I[0], S->I[1], c, M.dt,
+                                                 stage_dta(M, i), M.m->v64.rhob, M.m->desc.gravity, Nn, dim, S->rho,
+                                                 S->mhat, S->Ehat);
   count_launches(S->ctx, 1);
-  RUN(check("final combination"));
+  DG_CUDA(cudaMemcpyAsync(S->p, S->p_prev, Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaMemcpyAsync(S->mk, S->mhat, (size_t)dim * Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return check("stage begin");
+}
+
+// right-hand side of the Helmholtz problem for the current Picard iterate
+int phase_picard_pre(Member& M, int i, cudaStream_t s) {
+  dg_state* S = M.S;
+  const int64_t Nn = S->Nn;
+  const unsigned gb = gridn(Nn);
+  int rc;
+  if (M.nsolve >= 64) return fail(DG_EINVAL, "too many Picard iterations per step (at most 32)");
+  picard_prep_kernel<<<gb, 256, 0, s>>>(S->p, M.m->v64.pb, S->rho, S->mk, S->mhat, S->Ehat, Nn, S->dim, S->h,
+                                        S->rhs, S->tmpv);
+  count_launches(S->ctx, 1);
+  if ((rc = step_div(S, S->tmpv, S->tmps, s)) != DG_OK) return rc;
+  axpy_kernel<<<gb, 256, 0, s>>>(S->rhs, S->tmps, -stage_dta(M, i), Nn);
+  count_launches(S->ctx, 1);
+  if (M.o.precision == DG_FP32 && M.o.fused) {
+    to_f32_kernel<<<gb, 256, 0, s>>>(S->h, S->f32, Nn);  // h for the FP32 Arnoldi mat-vecs
+    count_launches(S->ctx, 1);
+  }
+  return check("picard");
+}
+
+int phase_solve_single(Member& M, int i, cudaStream_t s) {
+  const double dta = stage_dta(M, i);
+  int rc = helmholtz_solve(M.S, &M.o, dta * dta, &M.st, M.S->solve_out + 4 * M.nsolve, s);
+  ++M.nsolve;
+  return rc;
+}
+
+int phase_picard_post(Member& M, int i, cudaStream_t s) {
+  dg_state* S = M.S;
+  int rc;
+  if ((rc = step_grad(S, S->p, S->g, s)) != DG_OK) return rc;
+  momentum_kernel<<<gridn(S->Nn), 256, 0, s>>>(S->mhat, S->g, stage_dta(M, i), (int64_t)S->dim * S->Nn, S->mk);
+  count_launches(S->ctx, 1);
+  return check("momentum update");
+}
+
+int phase_stage_end(Member& M, int i, cudaStream_t s) {
+  dg_state* S = M.S;
+  const int64_t Nn = S->Nn;
+  const int dim = S->dim;
+  const unsigned gb = gridn(Nn);
+  int rc;
+  stage_state_kernel<<<gb, 256, 0, s>>>(S->rho, S->mk, S->p, M.m->v64.pb, Nn, dim, S->Ui);
+  count_launches(S->ctx, 1);
+  if ((rc = step_explicit(S, S->Ui, S->E[i], s)) != DG_OK) return rc;
+  if (i == 1) {
+    hm_kernel<<<gb, 256, 0, s>>>(S->h, S->mk, Nn, dim, S->tmpv);
+    count_launches(S->ctx, 1);
+    if ((rc = step_div(S, S->tmpv, S->tmps, s)) != DG_OK) return rc;
+    implicit_terms_kernel<<<gb, 256, 0, s>>>(S->Ui, M.m->v64.rhob, S->g, S->tmps, M.m->desc.gravity, Nn, dim,
+                                             S->I[1]);
+    count_launches(S->ctx, 1);
+  }
+  std::swap(S->p, S->p_prev);
+  return check("stage end");
+}
+
+int phase_final(Member& M, cudaStream_t s) {
+  dg_state* S = M.S;
+  const double dt = M.dt;
+  DG_CUDA(cudaMemsetAsync(S->flag, 0, sizeof(int), s));
+  final_kernel<<<gridn(S->Nn), 256, 0, s>>>(S->Ui, S->E[0], S->E[1], S->E[2], dt * (BW[0] - AEX[2][0]),
+                                            dt * (BW[1] - AEX[2][1]), dt * (BW[2] - AEX[2][2]),
+                                            (int64_t)S->V * S->Nn, S->U, S->flag);
+  count_launches(S->ctx, 1);
+  return check("final combination");
+}
+
+// after the stream has been synchronised: solve results and the non-finite flag
+int member_finish(Member& M, const double* sol, int flag) {
+  int status = DG_OK;
+  for (int k = 0; k < M.nsolve; ++k) {
+    M.st.gmres_iters += (int)sol[4 * k];
+    M.st.max_rel_residual = std::max(M.st.max_rel_residual, sol[4 * k + 1]);
+    if (sol[4 * k + 2] == 0.0) status = fail(DG_ENOTCONV, "a Helmholtz solve missed its tolerance");
+  }
+  M.st.solves = M.nsolve;
+  if (flag) status = fail(DG_ENONFINITE, "non-finite value in the new state");
+  return status;
+}
+
+int prepare_member(Member& M, dg_ctx* ctx, const dg_mesh* m, dg_state* S, double dt, const dg_solver_opts* opts) {
+  if (!ctx || !m || !S || S->mesh != m) return fail(DG_EINVAL, "bad arguments");
+  if (!(dt > 0.0)) return fail(DG_EINVAL, "dt must be positive");
+  dg_solver_opts_default(&M.o);
+  if (opts) M.o = *opts;
+  if (M.o.precision != DG_FP64 && M.o.precision != DG_FP32) return fail(DG_EINVAL, "bad precision");
+  if (M.o.picard < 1 || M.o.picard > 32) return fail(DG_EINVAL, "picard must be in 1..32");
+  M.S = S;
+  M.m = m;
+  M.dt = dt;
+  return DG_OK;
+}
+
+}  // namespace
+}  // namespace dg
+
+extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double dt, const dg_solver_opts* opts,
+                             dg_step_stats* stats, void* stream) {
+  Member M;
+  int rc = prepare_member(M, ctx, m, S, dt, opts);
+  if (rc != DG_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope step_scope(ctx, DG_PROF_STEP, s);
+#define RUN(x)                          \
+  do {                                  \
+    if ((rc = (x)) != DG_OK) return rc; \
+  } while (0)
+  RUN(phase_stage1(M, s));
+  for (int i = 1; i <= 2; ++i) {
+    RUN(phase_stage_begin(M, i, s));
+    for (int it = 0; it < M.o.picard; ++it) {
+      RUN(phase_picard_pre(M, i, s));
+      RUN(phase_solve_single(M, i, s));
+      RUN(phase_picard_post(M, i, s));
+    }
+    RUN(phase_stage_end(M, i, s));
+  }
+  RUN(phase_final(M, s));
+#undef RUN
   int flag = 0;
   double sol[256];
   DG_CUDA(cudaMemcpyAsync(&flag, S->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DG_CUDA(cudaMemcpyAsync(sol, S->solve_out, 4 * nsolve * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaMemcpyAsync(sol, S->solve_out, 4 * M.nsolve * sizeof(double), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
-#undef RUN
-  for (int k = 0; k < nsolve; ++k) {
-    st.gmres_iters += (int)sol[4 * k];
-    st.max_rel_residual = std::max(st.max_rel_residual, sol[4 * k + 1]);
-    if (sol[4 * k + 2] == 0.0) status = fail(DG_ENOTCONV, "a Helmholtz solve missed its tolerance");
-  }
-  st.solves = nsolve;
-  if (stats) *stats = st;
-  if (flag) return fail(DG_ENONFINITE, "non-finite value in the new state");
+  const int status = member_finish(M, sol, flag);
+  if (stats) *stats = M.st;
   return status;
+}
+
+extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states,
+                             const double* dt, const dg_solver_opts* opts, dg_step_stats* stats, int* statuses,
+                             void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!meshes || !states || !dt))) return fail(DG_EINVAL, "null argument");
+  if (n == 0) return DG_OK;
+  std::vector<Member> M(n);
+  int rc;
+  for (int i = 0; i < n; ++i) {
+    if ((rc = prepare_member(M[i], ctx, meshes[i], states[i], dt[i], opts)) != DG_OK) return rc;
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i]) return fail(DG_EINVAL, "members of a batch must not share a mesh");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope step_scope(ctx, DG_PROF_STEP, s);
+  const dg_solver_opts& o = M[0].o;
+  const int restart = std::min(o.restart, kMaxRestart);
+  for (int i = 0; i < n; ++i)
+    if (M[i].S->restart < restart) return fail(DG_EINVAL, "a state was created with a shorter restart length");
+  int* err = nullptr;
+  DG_CUDA(cudaMalloc(&err, sizeof(int)));
+  DG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  struct Free {
+    int* p;
+    ~Free() { cudaFree(p); }
+  } free_err{err};
+#define RUN(x)                          \
+  do {                                  \
+    if ((rc = (x)) != DG_OK) return rc; \
+  } while (0)
+  // batched solve of one Picard iteration: fused solves grouped by (dim, degree, precision)
+  auto solve_all = [&](int stage) -> int {
+    std::vector<int> rest;
+    std::vector<std::vector<int>> groups;
+    std::vector<std::pair<std::pair<int, int>, int>> keys;
+    for (int i = 0; i < n; ++i) {
+      if (!M[i].o.fused) {
+        rest.push_back(i);
+        continue;
+      }
+      const std::pair<int, int> key{M[i].m->dim * 16 + M[i].m->degree, M[i].o.precision};
+      size_t g = 0;
+      for (; g < keys.size(); ++g)
+        if (keys[g].first == key) break;
+      if (g == keys.size()) {
+        keys.push_back({key, (int)g});
+        groups.emplace_back();
+      }
+      groups[g].push_back(i);
+    }
+    for (size_t g = 0; g < groups.size(); ++g) {
+      ProfScope ps(ctx, DG_PROF_GMRES, s);
+      const int dim = M[groups[g][0]].m->dim;
+      const bool f32 = keys[g].first.second == DG_FP32;
+      if (!f32) {
+        std::vector<GmresItem<double>> items;
+        for (int i : groups[g]) {
+          dg_state* S = M[i].S;
+          const double dta = stage_dta(M[i], stage);
+          items.push_back({M[i].m, S->h, S->h, S->rhs, S->p, dta * dta, o.tol, 0.0, o.max_iters, S->gm64.Q,
+                           S->gm64.w, S->gm64.w, S->gm64.d.partial, (restart + 1) * kDotBlocks,
+                           S->solve_out + 4 * M[i].nsolve});
+        }
+        if ((rc = op_gmres_batched<double>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)
+          return rc;
+      } else {
+        std::vector<GmresItem<float>> items;
+        for (int i : groups[g]) {
+          dg_state* S = M[i].S;
+          const double dta = stage_dta(M[i], stage);
+          items.push_back({M[i].m, S->h, S->f32, S->rhs, S->p, dta * dta, o.tol, o.inner_tol, o.max_iters,
+                           S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, (restart + 1) * kDotBlocks,
+                           S->solve_out + 4 * M[i].nsolve});
+        }
+        if ((rc = op_gmres_batched<float>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)
+          return rc;
+      }
+      for (int i : groups[g]) ++M[i].nsolve;
+    }
+    for (int i : rest)
+      if ((rc = phase_solve_single(M[i], stage, s)) != DG_OK) return rc;
+    return DG_OK;
+  };
+  for (auto& mm : M) RUN(phase_stage1(mm, s));
+  for (int i = 1; i <= 2; ++i) {
+    for (auto& mm : M) RUN(phase_stage_begin(mm, i, s));
+    for (int it = 0; it < o.picard; ++it) {
+      for (auto& mm : M) RUN(phase_picard_pre(mm, i, s));
+      RUN(solve_all(i));
+      for (auto& mm : M) RUN(phase_picard_post(mm, i, s));
+    }
+    for (auto& mm : M) RUN(phase_stage_end(mm, i, s));
+  }
+  for (auto& mm : M) RUN(phase_final(mm, s));
+#undef RUN
+  // read every member's flag and solve results with one synchronisation
+  std::vector<int> flags(n, 0);
+  std::vector<double> sol((size_t)n * 256, 0.0);
+  int herr = 0;
+  for (int i = 0; i < n; ++i) {
+    DG_CUDA(cudaMemcpyAsync(&flags[i], M[i].S->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaMemcpyAsync(&sol[(size_t)i * 256], M[i].S->solve_out, 4 * M[i].nsolve * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+  }
+  DG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  int worst = DG_OK;
+  for (int i = 0; i < n; ++i) {
+    int st = member_finish(M[i], &sol[(size_t)i * 256], flags[i]);
+    if (herr) st = fail(DG_ETIMEOUT, "a barrier of the batched GMRES launch ran out of time");
+    if (stats) stats[i] = M[i].st;
+    if (statuses) statuses[i] = st;
+    if (st != DG_OK && worst == DG_OK) worst = st;
+  }
+  return worst;
 }

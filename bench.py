@@ -216,6 +216,86 @@ def apply_sweep(dg, torch, case_name, reps=10):
     return out
 
 
+def ensemble_bench(dg, torch, n_members=64, steps=10):
+    """Config-4 shape: 64 uneven 2D members (16x8..128x64 base, 0-2 levels, degree 2-5), FP32-refined,
+    one dg_batch_step per ensemble step."""
+    from workloads.cases import member2d
+
+    ctx = dg.Context(torch.cuda.current_device())
+    cases = [member2d(1000 + i) for i in range(n_members)]
+    opts = dg.solver_opts(tol=1e-12, precision=dg.DG_FP32, inner_tol=1e-4)
+    meshes = [dg.Mesh(ctx, c) for c in cases]
+    states = [dg.State(ctx, m, opts) for m in meshes]
+    for c, m, st in zip(cases, meshes, states):
+        kind, params = dg.api.init_params(c)
+        dg.dg_init_state(ctx, m, kind, params, st.U)
+    dts = [c.dt for c in cases]
+    dg.dg_batch_step(ctx, meshes, states, dts, opts)  # warm-up
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = 0
+    for _ in range(steps):
+        res = dg.dg_batch_step(ctx, meshes, states, dts, opts)
+        iters += sum(r["gmres_iters"] for r in res)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    dof = sum(m.n_dof for m in meshes)
+    out = {"workload": "%d 2D members (base 16x8..128x64, 0-2 levels, degree 2-5), %d DoF in all, "
+                       "FP32 Krylov + FP64 residual, dg_batch_step" % (n_members, dof),
+           "member_steps_per_s": n_members * steps / (ms / 1e3), "dof_steps_per_s": dof * steps / (ms / 1e3),
+           "ms_per_ensemble_step": ms / steps, "gmres_iters_per_member_step": iters / (n_members * steps)}
+    for st in states:
+        st.close()
+    for m in meshes:
+        m.close()
+    ctx.close()
+    return out
+
+
+def serving_bench(dg, torch, n_requests=40, rate=20.0, dof_hi=3e5, steps_hi=40, budget=160e9):
+    """Config-5 shape, bounded sample: Poisson arrivals, 2D/3D, degree 2-5, FP64 or FP32-refined."""
+    from workloads.cases import serving_trace
+
+    trace = serving_trace(7, n_requests, rate, 1e4, dof_hi, 5, steps_hi)
+    ctx = dg.Context(torch.cuda.current_device())
+    sv = dg.Server(ctx, int(budget))
+    t0 = time.perf_counter()
+    ids = []
+    for (t_arr, case, steps, prec) in trace:
+        now = time.perf_counter() - t0
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        o = dg.solver_opts(tol=1e-10, precision=dg.DG_FP64 if prec == "fp64" else dg.DG_FP32, inner_tol=1e-4)
+        ids.append((sv.submit(case, steps, opts=o), case, steps))
+    for rid, _, _ in ids:
+        sv.wait(rid, 900)
+    infos = [sv.poll(rid) for rid, _, _ in ids]
+    ok = [i for i in infos if i["state"] == "done"]
+    lat = sorted(i["t_finish"] - i["t_submit"] for i in ok)
+    t_first = min(i["t_submit"] for i in infos)
+    t_last = max(i["t_finish"] for i in infos)
+    span = t_last - t_first
+    steps_total = sum(s for _, _, s in ids)
+    dof_steps = sum(c.n_dof * s for _, c, s in ids)
+    stats = sv.stats()
+    sv.close()
+    ctx.close()
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] if lat else None
+
+    return {"workload": "%d requests, Poisson %.0f/s, 2D/3D, degree 2-5, DoF 1e4-%.0e, %d-%d steps, "
+                        "FP64 or FP32-refined 50/50, %.0f GB budget (bounded sample of the serving stream)"
+                        % (n_requests, rate, dof_hi, 5, steps_hi, budget / 1e9),
+            "completed": len(ok), "p50_s": pct(0.5), "p99_s": pct(0.99), "makespan_s": span,
+            "member_steps_per_s": steps_total / span, "dof_steps_per_s": dof_steps / span,
+            "ticks": stats["ticks"]}
+
+
 METRIC = "DG apply DoF/s fp64 vs fp32, %HBM peak; ensemble steps/s, p50/p99 latency"
 CONFIG = {
     "hill2d": {
@@ -244,6 +324,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the operator-apply sweep on the large 3D mesh")
     ap.add_argument("--sweep-workload", default="hill3d_big")
     ap.add_argument("--sweep-only", action="store_true", help="run only the operator-apply sweep")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble and serving measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -407,6 +488,9 @@ def main():
     }
     if rank == 0 and not args.no_sweep:
         line["applies"] = apply_sweep(dg, torch, args.sweep_workload)
+    if rank == 0 and not args.no_ensemble:
+        line["ensemble"] = ensemble_bench(dg, torch)
+        line["serving"] = serving_bench(dg, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(args.workload, 12.0)
     if rank == 0:

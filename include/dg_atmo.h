@@ -276,6 +276,70 @@ int imex_rk2_step(dg_ctx* ctx, const dg_mesh* mesh, dg_state* state, double dt, 
 int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states, const double* dt,
                   const dg_solver_opts* opts, dg_step_stats* stats, int* statuses, void* stream);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop for simulation requests of different mesh sizes, degrees,
+ * orographies and precisions.  Requests are queued on submit; a worker thread
+ * (its own context and stream, on the device of the creating context) admits
+ * them first come first served while their device-memory footprint fits the
+ * budget and a slot is free, keeps every admitted member's state resident,
+ * and advances all resident members one IMEX-RK2 step per tick with
+ * dg_batch_step (continuous batching: members join and leave between ticks,
+ * their work overlaps in the batched launches).  A member's result equals the
+ * result of stepping it alone to the Krylov tolerance.  The paper has no
+ * serving layer; this is the deployment form of the same path. */
+typedef struct dg_server dg_server;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* admission budget for resident members (bytes)      */
+  int max_members;         /* resident slots; 0 = limited by the budget only     */
+} dg_serve_opts;
+
+typedef struct {
+  dg_mesh_desc mesh;       /* copied on submit (level and ijk arrays too)        */
+  int init_kind;           /* dg_init_kind                                       */
+  double init_params[8];   /* see dg_init_state                                  */
+  int n_init_params;
+  double dt;               /* step size (s)                                      */
+  int steps;               /* IMEX-RK2 steps to run                              */
+  dg_solver_opts solver;   /* precision and Krylov settings                      */
+} dg_request;
+
+typedef enum { DG_REQ_QUEUED = 0, DG_REQ_RUNNING = 1, DG_REQ_DONE = 2, DG_REQ_FAILED = 3 } dg_request_state;
+
+typedef struct {
+  int state;               /* dg_request_state                                   */
+  int status;              /* DG_OK, or why the request failed                   */
+  int steps_done;
+  long long gmres_iters;   /* inner GMRES iterations so far                      */
+  double t_submit, t_admit, t_finish; /* seconds since the server was created    */
+  size_t footprint_bytes;  /* device bytes reserved while resident (estimate)    */
+  int64_t n_dof;
+} dg_request_info;
+
+typedef struct {
+  int queued, running;
+  size_t used_bytes;
+  long long ticks;
+  double elapsed_s;
+} dg_serve_info;
+
+int dg_serve_create(dg_ctx* ctx, const dg_serve_opts* opts, dg_server** out);
+/* Queue a request; *id identifies it.  DG_EINVAL for a malformed request,
+ * DG_EBUDGET if its footprint exceeds the whole budget (it could never be
+ * admitted); neither disturbs resident members. */
+int dg_serve_submit(dg_server* server, const dg_request* req, uint64_t* id);
+/* Non-blocking status; host_U (may be NULL) receives the final state
+ * ([n_vars][cells][nodes] doubles) once the request is done. */
+int dg_serve_poll(dg_server* server, uint64_t id, dg_request_info* info, double* host_U);
+/* Wait until the request is done or failed, at most timeout_s seconds
+ * (DG_ETIMEOUT otherwise). */
+int dg_serve_wait(dg_server* server, uint64_t id, double timeout_s);
+/* Forget a finished request and free its stored result. */
+int dg_serve_release(dg_server* server, uint64_t id);
+int dg_serve_stats(dg_server* server, dg_serve_info* info);
+/* Stop the worker: resident members are freed, queued ones fail. */
+int dg_serve_destroy(dg_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@ from .api import (  # noqa: F401
     Context,
     DGError,
     Mesh,
+    Server,
     State,
     dg_apply_div,
     dg_batch_step,

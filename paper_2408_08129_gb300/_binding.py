@@ -57,6 +57,30 @@ class StepStats(ctypes.Structure):
     _fields_ = [("gmres_iters", c_int), ("solves", c_int), ("refine_steps", c_int), ("max_rel_residual", c_double)]
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_members", c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("mesh", MeshDesc), ("init_kind", c_int), ("init_params", c_double * 8), ("n_init_params", c_int),
+        ("dt", c_double), ("steps", c_int), ("solver", SolverOpts),
+    ]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [
+        ("state", c_int), ("status", c_int), ("steps_done", c_int), ("gmres_iters", ctypes.c_longlong),
+        ("t_submit", c_double), ("t_admit", c_double), ("t_finish", c_double),
+        ("footprint_bytes", ctypes.c_size_t), ("n_dof", c_int64),
+    ]
+
+
+class ServeInfo(ctypes.Structure):
+    _fields_ = [("queued", c_int), ("running", c_int), ("used_bytes", ctypes.c_size_t),
+                ("ticks", ctypes.c_longlong), ("elapsed_s", c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -96,6 +120,13 @@ def _load():
         "dg_state_download": (c_int, [P, P]),
         "imex_rk2_step": (c_int, [P, P, P, c_double, ctypes.POINTER(SolverOpts), ctypes.POINTER(StepStats), P]),
         "dg_batch_step": (c_int, [P, c_int, P, P, P, ctypes.POINTER(SolverOpts), P, P, P]),
+        "dg_serve_create": (c_int, [P, ctypes.POINTER(ServeOpts), ctypes.POINTER(P)]),
+        "dg_serve_submit": (c_int, [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+        "dg_serve_poll": (c_int, [P, ctypes.c_uint64, ctypes.POINTER(RequestInfo), P]),
+        "dg_serve_wait": (c_int, [P, ctypes.c_uint64, c_double]),
+        "dg_serve_release": (c_int, [P, ctypes.c_uint64]),
+        "dg_serve_stats": (c_int, [P, ctypes.POINTER(ServeInfo)]),
+        "dg_serve_destroy": (c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -59,34 +59,53 @@ class Context:
             pass
 
 
+def mesh_desc(case, gravity=None):
+    """dg_mesh_desc of a workload description; returns (desc, arrays to keep alive)."""
+    d = B.MeshDesc()
+    d.dim = case.dim
+    d.degree = case.degree
+    d.n_cells = case.n_cells
+    level = np.ascontiguousarray(case.levels, dtype=np.uint8)
+    ijk = np.ascontiguousarray(case.ijk, dtype=np.int32)
+    d.level = level.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    d.ijk = ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    for a in range(case.dim):
+        d.base[a] = case.base[a]
+        d.extent[a] = case.extent[a]
+        d.periodic[a] = 1 if case.periodic[a] else 0
+    hill = case.hill
+    d.hill_kind = DG_HILL[hill["kind"]]
+    d.hill_hc = hill.get("hc", 0.0)
+    d.hill_half_width = hill.get("half_width", 1.0)
+    d.hill_xc = hill.get("xc", 0.0)
+    d.hill_yc = hill.get("yc", 0.0)
+    atm = case.atmosphere
+    d.atm_kind = DG_ATM[atm["kind"]]
+    d.atm_T = atm.get("T0", atm.get("T_ref", 0.0))
+    d.atm_N = atm.get("N", 0.0)
+    d.atm_p_ref = atm.get("p_ref", 0.0)
+    d.gravity = case.gravity if gravity is None else gravity
+    return d, (level, ijk)
+
+
+def init_params(case):
+    """(dg_init_kind, parameter list) of a workload's initial state."""
+    init = case.init
+    if init["kind"] == "bubble":
+        p = [init["amp"], init["radius"], init["xc"], init["zc"]]
+        if case.dim == 3:
+            p.append(init.get("yc", 0.5 * case.extent[1]))
+        return DG_INIT["bubble"], p
+    if init["kind"] == "inflow":
+        return DG_INIT["inflow"], [init.get("u0", 10.0)]
+    return DG_INIT["rest"], []
+
+
 class Mesh:
     """dg_mesh built from a workload description (see workloads.Case)."""
 
     def __init__(self, ctx, case, gravity=None):
-        d = B.MeshDesc()
-        d.dim = case.dim
-        d.degree = case.degree
-        d.n_cells = case.n_cells
-        self._level = np.ascontiguousarray(case.levels, dtype=np.uint8)
-        self._ijk = np.ascontiguousarray(case.ijk, dtype=np.int32)
-        d.level = self._level.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
-        d.ijk = self._ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        for a in range(case.dim):
-            d.base[a] = case.base[a]
-            d.extent[a] = case.extent[a]
-            d.periodic[a] = 1 if case.periodic[a] else 0
-        hill = case.hill
-        d.hill_kind = DG_HILL[hill["kind"]]
-        d.hill_hc = hill.get("hc", 0.0)
-        d.hill_half_width = hill.get("half_width", 1.0)
-        d.hill_xc = hill.get("xc", 0.0)
-        d.hill_yc = hill.get("yc", 0.0)
-        atm = case.atmosphere
-        d.atm_kind = DG_ATM[atm["kind"]]
-        d.atm_T = atm.get("T0", atm.get("T_ref", 0.0))
-        d.atm_N = atm.get("N", 0.0)
-        d.atm_p_ref = atm.get("p_ref", 0.0)
-        d.gravity = case.gravity if gravity is None else gravity
+        d, self._keep = mesh_desc(case, gravity)
         h = ctypes.c_void_p()
         check(lib.dg_mesh_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "dg_mesh_create")
         self.handle = h
@@ -298,3 +317,68 @@ def dg_batch_step(ctx, meshes, states, dts, opts=None, stream=None, raise_on_err
         d["status"] = statuses[i]
         out.append(d)
     return out
+
+
+REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+
+class Server:
+    """dg_server: request loop with memory-budget admission and continuous batching."""
+
+    def __init__(self, ctx, hbm_budget_bytes, max_members=0):
+        o = B.ServeOpts(hbm_budget_bytes=int(hbm_budget_bytes), max_members=int(max_members))
+        h = ctypes.c_void_p()
+        check(lib.dg_serve_create(ctx.handle, ctypes.byref(o), ctypes.byref(h)), "dg_serve_create")
+        self.handle = h
+        self._shapes = {}
+
+    def submit(self, case, steps, dt=None, opts=None):
+        r = B.Request()
+        desc, keep = mesh_desc(case)
+        r.mesh = desc
+        kind, params = init_params(case)
+        r.init_kind = kind
+        for i, v in enumerate(params):
+            r.init_params[i] = v
+        r.n_init_params = len(params)
+        r.dt = case.dt if dt is None else dt
+        r.steps = int(steps)
+        r.solver = opts if opts is not None else solver_opts()
+        rid = ctypes.c_uint64()
+        check(lib.dg_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)), "dg_serve_submit")
+        self._shapes[rid.value] = (case.dim + 2, case.n_cells, (case.degree + 1) ** case.dim)
+        return rid.value
+
+    def poll(self, rid, with_result=False):
+        info = B.RequestInfo()
+        U = np.zeros(self._shapes[rid]) if with_result else None
+        check(lib.dg_serve_poll(self.handle, rid, ctypes.byref(info), U.ctypes.data if U is not None else None),
+              "dg_serve_poll")
+        d = {k: getattr(info, k) for k, _ in B.RequestInfo._fields_}
+        d["state"] = REQ_STATES[d["state"]]
+        if with_result:
+            d["U"] = U
+        return d
+
+    def wait(self, rid, timeout_s=600.0):
+        check(lib.dg_serve_wait(self.handle, rid, float(timeout_s)), "dg_serve_wait")
+
+    def release(self, rid):
+        check(lib.dg_serve_release(self.handle, rid), "dg_serve_release")
+        self._shapes.pop(rid, None)
+
+    def stats(self):
+        i = B.ServeInfo()
+        check(lib.dg_serve_stats(self.handle, ctypes.byref(i)), "dg_serve_stats")
+        return {k: getattr(i, k) for k, _ in B.ServeInfo._fields_}
+
+    def close(self):
+        if self.handle:
+            lib.dg_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

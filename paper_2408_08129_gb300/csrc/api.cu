@@ -152,6 +152,8 @@ extern "C" int dg_ctx_destroy(dg_ctx* c) {
   if (!c) return DG_OK;
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->d_phase) cudaFree(c->d_phase);
+  if (c->d_batch) cudaFree(c->d_batch);
+  if (c->d_batch_err) cudaFree(c->d_batch_err);
   delete c;
   return DG_OK;
 }

@@ -84,6 +84,7 @@ struct dg_ctx {
   unsigned long long* d_phase = nullptr;  // [16] ns per fused-GMRES phase (profiling on)
   void* d_batch = nullptr;  // workspace of batched solves (argument table, CTA map, barriers)
   size_t batch_bytes = 0;
+  int* d_batch_err = nullptr;  // barrier-timeout flag of batched launches
 };
 
 namespace dg {

@@ -625,13 +625,9 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, d
   const int restart = std::min(o.restart, kMaxRestart);
   for (int i = 0; i < n; ++i)
     if (M[i].S->restart < restart) return fail(DG_EINVAL, "a state was created with a shorter restart length");
-  int* err = nullptr;
-  DG_CUDA(cudaMalloc(&err, sizeof(int)));
+  if (!ctx->d_batch_err) DG_CUDA(cudaMalloc(&ctx->d_batch_err, sizeof(int)));
+  int* err = ctx->d_batch_err;
   DG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-  struct Free {
-    int* p;
-    ~Free() { cudaFree(p); }
-  } free_err{err};
 #define RUN(x)                          \
   do {                                  \
     if ((rc = (x)) != DG_OK) return rc; \

@@ -408,6 +408,58 @@ def tiny_case(
     )
 
 
+def request_case(seed: int, dof_lo: float = 1e4, dof_hi: float = 5e6) -> Case:
+    """One serving request: 2D or 3D (50/50), degree 2-5, DoF log-uniform in [dof_lo, dof_hi].
+
+    The base grid is sized to the drawn DoF (x by y by z/2 cells), with a
+    seeded hill of up to 1 km and a bubble or an inflow, 0 or 1 refinement
+    level near the ground.
+    """
+    rng = np.random.default_rng(seed)
+    dim = int(rng.choice([2, 3]))
+    degree = int(rng.integers(2, 6))
+    dof = float(np.exp(rng.uniform(np.log(dof_lo), np.log(dof_hi))))
+    V = dim + 2
+    cells = dof / (V * (degree + 1) ** dim)
+    if dim == 2:
+        nx = max(4, 2 * int(round(math.sqrt(2.0 * cells) / 2)))
+        base, extent, periodic = (nx, nx // 2), (40e3, 20e3), (True, False)
+    else:
+        nx = max(4, 2 * int(round((2.0 * cells) ** (1.0 / 3.0) / 2)))
+        base, extent, periodic = (nx, nx, nx // 2), (40e3, 40e3, 20e3), (True, True, False)
+    refine = bool(rng.uniform() < 0.5)
+    dz = extent[-1] / base[-1]
+
+    def rule(level, centre):
+        return level == 0 and centre[-1] < 1.1 * dz
+
+    leaves = build_tree(dim, base, extent, periodic, rule if refine else None, 1 if refine else 0)
+    hill = dict(kind="gauss", hc=float(rng.uniform(0.0, 1e3)), half_width=2e3, xc=20e3, yc=20e3)
+    if rng.uniform() < 0.5:
+        init = dict(kind="bubble", amp=2.0, radius=2e3, xc=float(rng.uniform(10e3, 30e3)), zc=3e3, yc=20e3)
+    else:
+        init = dict(kind="inflow", u0=10.0)
+    return _finish(
+        "request", dim, degree, base, extent, periodic, leaves, hill,
+        dict(kind="stratified", N=0.01, T_ref=293.15, p_ref=1e5), init, 1.0, 10, seed,
+    )
+
+
+def serving_trace(seed: int, n: int, rate: float = 20.0, dof_lo: float = 1e4, dof_hi: float = 5e6,
+                  steps_lo: int = 10, steps_hi: int = 500):
+    """Poisson arrivals (mean `rate` per second) of n requests: (arrival s, case, steps, 'fp64'|'fp32')."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        case = request_case(seed * 100003 + i, dof_lo, dof_hi)
+        steps = int(rng.integers(steps_lo, steps_hi + 1))
+        prec = "fp64" if rng.uniform() < 0.5 else "fp32"
+        out.append((t, case, steps, prec))
+    return out
+
+
 CONFIGS = {
     "bubble2d": bubble2d,
     "hill2d": hill2d,

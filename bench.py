@@ -482,6 +482,7 @@ def main():
                                          if k not in ("iterations", "second_passes")},
         "gmres_second_pass_fraction": phases["second_passes"] / max(1, phases["iterations"]),
         "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in stats),
+        "autotuned_solver": mesh.autotuned(),
         "fp32_refined": fp32,
         "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(local),

@@ -142,6 +142,10 @@ typedef struct {
   int max_level;
   double min_edge;                      /* smallest computational cell edge   */
   size_t device_bytes;                  /* device memory held by the mesh     */
+  int solver_form[2];                   /* autotuned Helmholtz solver for FP64 */
+                                        /* [0] and FP32 [1]: 1 persistent, 0   */
+                                        /* multi-kernel, -1 not tuned yet      */
+  float solver_ms[2][2];                /* the timed solves: [precision][form] */
 } dg_mesh_info;
 
 /* Build connectivity (conforming faces, 2:1 subfaces, walls), check the 2:1
@@ -227,7 +231,9 @@ typedef struct {
   double inner_tol;    /* DG_FP32: relative tolerance of each inner solve (1e-4) */
   int max_refine;      /* DG_FP32: outer refinement steps cap (20)              */
   int fused;           /* 1: each GMRES solve is one persistent cooperative     */
-                       /*    kernel (default); 0: one launch per Krylov kernel  */
+                       /*    kernel; 0: one launch per Krylov kernel; -1       */
+                       /*    (default): autotuned per mesh and precision by     */
+                       /*    timing both forms on the first solve               */
 } dg_solver_opts;
 
 typedef struct {

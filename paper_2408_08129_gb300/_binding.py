@@ -43,6 +43,7 @@ class MeshInfo(ctypes.Structure):
         ("n_cells", c_int64), ("n_nodes", c_int64), ("n_dof", c_int64),
         ("n_conforming", c_int64), ("n_subfaces", c_int64), ("n_walls", c_int64),
         ("max_level", c_int), ("min_edge", c_double), ("device_bytes", ctypes.c_size_t),
+        ("solver_form", c_int * 2), ("solver_ms", (ctypes.c_float * 2) * 2),
     ]
 
 

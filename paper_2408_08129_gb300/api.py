@@ -113,13 +113,21 @@ class Mesh:
         self.case = case
         info = B.MeshInfo()
         check(lib.dg_mesh_get_info(h, ctypes.byref(info)), "dg_mesh_get_info")
-        self.info = {k: getattr(info, k) for k, _ in B.MeshInfo._fields_}
+        self.info = {k: getattr(info, k) for k, _ in B.MeshInfo._fields_ if k not in ("solver_form", "solver_ms")}
         self.dim = case.dim
         self.n_vars = info.n_vars
         self.n_cells = info.n_cells
         self.nodes_per_cell = info.nodes_per_cell
         self.n_nodes = info.n_nodes
         self.n_dof = info.n_dof
+
+    def autotuned(self):
+        """Autotuner outcome: per precision, the chosen Helmholtz solver form and the timed solves (ms)."""
+        info = B.MeshInfo()
+        check(lib.dg_mesh_get_info(self.handle, ctypes.byref(info)), "dg_mesh_get_info")
+        forms = {1: "persistent", 0: "multi-kernel", -1: None}
+        return {p: {"form": forms[info.solver_form[i]], "ms_multi_kernel": info.solver_ms[i][0],
+                    "ms_persistent": info.solver_ms[i][1]} for i, p in enumerate(("fp64", "fp32"))}
 
     def faces(self):
         i = self.info

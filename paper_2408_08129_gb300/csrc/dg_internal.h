@@ -134,4 +134,8 @@ struct dg_mesh {
   double* d_face_scratch64 = nullptr;
   double* d_vec_scratch64 = nullptr;  // [dim][Nn]
   double* d_red_scratch = nullptr;    // [2*512] block partials of the conservation sums
+  // autotuned Helmholtz solver per precision (-1 = not tuned yet, 0 = one launch
+  // per Krylov kernel, 1 = persistent single-launch solve), chosen by timing
+  mutable int tuned_fused[2] = {-1, -1};
+  mutable float tuned_ms[2][2] = {{0, 0}, {0, 0}};
 };

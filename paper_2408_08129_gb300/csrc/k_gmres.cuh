@@ -499,7 +499,7 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
 }
 
 template <int DIM, int DEG, typename TK>
-__global__ void __launch_bounds__(256) gmres_persistent_kernel(GmresPArgs<TK> a) {
+__global__ void __launch_bounds__(256, 2) gmres_persistent_kernel(GmresPArgs<TK> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GridSync sg;
   gmres_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
@@ -518,7 +518,7 @@ struct BatchMap {
 };
 
 template <int DIM, int DEG, typename TK>
-__global__ void __launch_bounds__(256) gmres_batched_kernel(const GmresPArgs<TK>* __restrict__ args, BatchMap map) {
+__global__ void __launch_bounds__(256, 3) gmres_batched_kernel(const GmresPArgs<TK>* __restrict__ args, BatchMap map) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sfail;
   const int mem = map.cta_member[blockIdx.x];

@@ -42,6 +42,7 @@ struct dg_state {
   double* g = nullptr;    // [dim][Nn]
   double* r64 = nullptr;  // FP64 outer residual
   double* solve_out = nullptr;  // [64][4] per-solve results of one step
+  double* p_save = nullptr;     // initial guess kept while the autotuner tries both solver forms
   float* f32 = nullptr;   // FP32 Krylov: h, rhs, delta [3 Nn]
   int* flag = nullptr;    // non-finite flag
   dg::Gmres<double> gm64;
@@ -325,7 +326,7 @@ extern "C" void dg_solver_opts_default(dg_solver_opts* o) {
   o->precision = DG_FP64;
   o->inner_tol = 1e-4;
   o->max_refine = 20;
-  o->fused = 1;
+  o->fused = -1;
 }
 
 extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_opts* opts, dg_state** out) {
@@ -346,7 +347,7 @@ extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_op
   const int V = S->V, dim = S->dim;
   // every buffer is rounded up to 32 doubles (256 bytes); 20 buffers in all
   auto rup = [](size_t n) { return (n + 31) & ~(size_t)31; };
-  const size_t nd = 7 * rup((size_t)V * Nn) + 4 * rup((size_t)dim * Nn) + 8 * rup((size_t)Nn) + rup(8) + rup(256);
+  const size_t nd = 7 * rup((size_t)V * Nn) + 4 * rup((size_t)dim * Nn) + 9 * rup((size_t)Nn) + rup(8) + rup(256);
   cudaError_t e = cudaSetDevice(ctx->device);
   const size_t nf32 = (size_t)Nn * 3 + 256;
   if (e == cudaSuccess) e = cudaMalloc(&S->block, nd * sizeof(double) + nf32 * sizeof(float) + 1024);
@@ -378,6 +379,7 @@ extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_op
   S->r64 = take(Nn);
   S->flag = (int*)take(8);
   S->solve_out = take(256);
+  S->p_save = take(Nn);
   S->f32 = (float*)p;
   int rc = S->gm64.init(Nn, o.restart);
   if (rc == DG_OK) rc = S->gm32.init(Nn, o.restart);
@@ -490,18 +492,51 @@ int phase_picard_pre(Member& M, int i, cudaStream_t s) {
   if ((rc = step_div(S, S->tmpv, S->tmps, s)) != DG_OK) return rc;
   axpy_kernel<<<gb, 256, 0, s>>>(S->rhs, S->tmps, -stage_dta(M, i), Nn);
   count_launches(S->ctx, 1);
-  if (M.o.precision == DG_FP32 && M.o.fused) {
+  if (M.o.precision == DG_FP32) {
     to_f32_kernel<<<gb, 256, 0, s>>>(S->h, S->f32, Nn);  // h for the FP32 Arnoldi mat-vecs
     count_launches(S->ctx, 1);
   }
   return check("picard");
 }
 
+// Autotuner: with fused = -1 the first solve of a (mesh, precision) is run
+// both as the persistent single-launch kernel and as one launch per Krylov
+// kernel, from the same initial guess, and the faster form is kept for every
+// later solve on that mesh (the persistent form wins on small meshes, where
+// launch latency dominates; the multi-kernel form on large FP64 meshes, where
+// full occupancy hides the FP64 pipe's latency).
 int phase_solve_single(Member& M, int i, cudaStream_t s) {
   const double dta = stage_dta(M, i);
-  int rc = helmholtz_solve(M.S, &M.o, dta * dta, &M.st, M.S->solve_out + 4 * M.nsolve, s);
+  double* out = M.S->solve_out + 4 * M.nsolve;
   ++M.nsolve;
-  return rc;
+  if (M.o.fused >= 0) return helmholtz_solve(M.S, &M.o, dta * dta, &M.st, out, s);
+  const int pi = M.o.precision == DG_FP32 ? 1 : 0;
+  dg_solver_opts o = M.o;
+  if (M.m->tuned_fused[pi] >= 0) {
+    o.fused = M.m->tuned_fused[pi];
+    return helmholtz_solve(M.S, &o, dta * dta, &M.st, out, s);
+  }
+  dg_state* S = M.S;
+  DG_CUDA(cudaMemcpyAsync(S->p_save, S->p, S->Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  cudaEvent_t e[3];
+  for (auto& ev : e) DG_CUDA(cudaEventCreate(&ev));
+  int rc;
+  float ms[2] = {0, 0};
+  for (int f = 1; f >= 0; --f) {
+    if (f == 0) DG_CUDA(cudaMemcpyAsync(S->p, S->p_save, S->Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    o.fused = f;
+    DG_CUDA(cudaEventRecord(e[f == 1 ? 0 : 1], s));
+    if ((rc = helmholtz_solve(S, &o, dta * dta, &M.st, out, s)) != DG_OK) return rc;
+  }
+  DG_CUDA(cudaEventRecord(e[2], s));
+  DG_CUDA(cudaEventSynchronize(e[2]));
+  cudaEventElapsedTime(&ms[1], e[0], e[1]);
+  cudaEventElapsedTime(&ms[0], e[1], e[2]);
+  for (auto& ev : e) cudaEventDestroy(ev);
+  M.m->tuned_ms[pi][0] = ms[0];
+  M.m->tuned_ms[pi][1] = ms[1];
+  M.m->tuned_fused[pi] = ms[1] <= ms[0] ? 1 : 0;
+  return DG_OK;
 }
 
 int phase_picard_post(Member& M, int i, cudaStream_t s) {
@@ -638,7 +673,8 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, d
     std::vector<std::vector<int>> groups;
     std::vector<std::pair<std::pair<int, int>, int>> keys;
     for (int i = 0; i < n; ++i) {
-      if (!M[i].o.fused) {
+      // members of a batch use the batched persistent solve unless told otherwise
+      if (M[i].o.fused == 0) {
         rest.push_back(i);
         continue;
       }

@@ -243,3 +243,19 @@ def test_rest_state_stays_at_rest(dg, ctx):
     U = st.download()
     assert np.abs(U[1:4]).max() < 1e-9
     assert _rel(U[0], ref.Ubg[0]) < 1e-14 and _rel(U[4], ref.Ubg[4]) < 1e-14
+
+
+def test_autotuner_times_both_solver_forms(dg, ctx):
+    """fused = -1 times the persistent and the multi-kernel solve once and keeps the faster."""
+    case = make_case("bubble2d", 0)
+    ref = DG(case)
+    mesh = dg.Mesh(ctx, case)
+    st = dg.State(ctx, mesh)
+    st.upload(ref.state())
+    assert mesh.autotuned()["fp64"]["form"] is None
+    dg.imex_rk2_step(ctx, mesh, st, case.dt, dg.solver_opts(tol=1e-12, fused=-1))
+    t = mesh.autotuned()["fp64"]
+    assert t["form"] in ("persistent", "multi-kernel")
+    assert t["ms_persistent"] > 0 and t["ms_multi_kernel"] > 0
+    faster = "persistent" if t["ms_persistent"] <= t["ms_multi_kernel"] else "multi-kernel"
+    assert t["form"] == faster

@@ -424,6 +424,30 @@ def main():
             "speedup_vs_fp64": sum(times) / sum(times32),
             "rel_err_vs_fp64_full_state": rel_full,
             "rel_err_vs_fp64_deviation": rel_dev}
+    # conjugate gradients (the Helmholtz operator is self-adjoint in the w J inner product),
+    # FP64 and FP32-refined, from the same start
+    cg = {}
+    for name, prec in (("fp64", dg.DG_FP64), ("fp32_refined", dg.DG_FP32)):
+        o = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=prec, inner_tol=1e-4,
+                           krylov=dg.DG_KRYLOV_CG)
+        state.upload(U_start)
+        tms, its = [], 0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            its += dg.imex_rk2_step(ctx, mesh, state, case.dt, o)["gmres_iters"]
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            tms.append(ev0.elapsed_time(ev1))
+        Uc = state.download()
+        cg[name] = {"ms_per_step": sum(tms) / args.steps, "value": world * dof * args.steps / (sum(tms) / 1e3),
+                    "speedup_vs_gmres_fp64": sum(times) / sum(tms), "iters_per_step": its / args.steps,
+                    "rel_err_vs_gmres_fp64_deviation": max(
+                        np.linalg.norm(Uc[v] - U64[v]) / max(np.linalg.norm(U64[v] - Ubg[v]), 1e-300)
+                        for v in range(mesh.n_vars))}
     state.upload(U64)
 
     # end to end through the C ABI with host buffers: upload, step, download per step
@@ -484,6 +508,7 @@ def main():
         "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in stats),
         "autotuned_solver": mesh.autotuned(),
         "fp32_refined": fp32,
+        "conjugate_gradients": cg,
         "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(local),
     }

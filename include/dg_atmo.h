@@ -62,6 +62,7 @@ typedef enum {
 } dg_status;
 
 typedef enum { DG_FP64 = 0, DG_FP32 = 1 } dg_precision;
+typedef enum { DG_KRYLOV_GMRES = 0, DG_KRYLOV_CG = 1 } dg_krylov;
 typedef enum { DG_TERMS_FULL = 0, DG_TERMS_IMEX_EXPLICIT = 1 } dg_terms;
 typedef enum { DG_HILL_NONE = 0, DG_HILL_GAUSS = 1, DG_HILL_BELL = 2, DG_HILL_PARABOLA = 3 } dg_hill_kind;
 typedef enum { DG_ATM_NONE = 0, DG_ATM_ISOTHERMAL = 1, DG_ATM_STRATIFIED = 2 } dg_atm_kind;
@@ -234,6 +235,10 @@ typedef struct {
                        /*    kernel; 0: one launch per Krylov kernel; -1       */
                        /*    (default): autotuned per mesh and precision by     */
                        /*    timing both forms on the first solve               */
+  int krylov;          /* DG_KRYLOV_GMRES (Sec. 3.2, default) or DG_KRYLOV_CG:  */
+                       /*    conjugate gradients in the w J inner product, in   */
+                       /*    which the Helmholtz operator is self-adjoint and   */
+                       /*    positive (persistent form only)                    */
 } dg_solver_opts;
 
 typedef struct {

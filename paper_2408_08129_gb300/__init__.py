@@ -8,6 +8,8 @@ without the built library raises ImportError: there is no CPU fallback.
 from .api import (  # noqa: F401
     DG_FP32,
     DG_FP64,
+    DG_KRYLOV_CG,
+    DG_KRYLOV_GMRES,
     DG_TERMS_FULL,
     DG_TERMS_IMEX_EXPLICIT,
     Context,

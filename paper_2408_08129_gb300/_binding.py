@@ -17,6 +17,7 @@ DG_STATUS = {
     -5: "DG_ENONFINITE", -6: "DG_EUNBALANCED", -7: "DG_EBUDGET", -8: "DG_ETIMEOUT",
 }
 DG_FP64, DG_FP32 = 0, 1
+DG_KRYLOV_GMRES, DG_KRYLOV_CG = 0, 1
 DG_TERMS_FULL, DG_TERMS_IMEX_EXPLICIT = 0, 1
 DG_HILL = {"none": 0, "gauss": 1, "bell": 2, "parabola": 3}
 DG_ATM = {"none": 0, "isothermal": 1, "stratified": 2}
@@ -51,6 +52,7 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [
         ("picard", c_int), ("restart", c_int), ("max_iters", c_int), ("tol", c_double),
         ("precision", c_int), ("inner_tol", c_double), ("max_refine", c_int), ("fused", c_int),
+        ("krylov", c_int),
     ]
 
 

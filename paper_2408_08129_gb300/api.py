@@ -12,7 +12,8 @@ import torch
 
 from . import _binding as B
 from ._binding import (  # noqa: F401
-    DG_ATM, DG_FP32, DG_FP64, DG_HILL, DG_INIT, DG_TERMS_FULL, DG_TERMS_IMEX_EXPLICIT, DGError, check, lib,
+    DG_ATM, DG_FP32, DG_FP64, DG_HILL, DG_INIT, DG_KRYLOV_CG, DG_KRYLOV_GMRES, DG_TERMS_FULL,
+    DG_TERMS_IMEX_EXPLICIT, DGError, check, lib,
 )
 
 

@@ -57,6 +57,7 @@ struct GmresPArgs {
   int m;
   int max_iters;
   int64_t n;
+  int method;  // 0: GMRES(m); 1: conjugate gradients in the M inner product (needs m >= 2)
 };
 
 enum GmresPhase {
@@ -498,11 +499,207 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
   }
 }
 
+// Conjugate gradients on the same Helmholtz system.  With the strong gradient
+// and weak divergence, M A is symmetric positive definite (M = diag(w J)), so
+// A is self-adjoint in the inner product <x, y>_M = sum w J x y and CG in that
+// inner product applies.  Chronopoulos-Gear form: one mat-vec and ONE fused
+// reduction (<r, r>_M, <A r, r>_M, ||r||^2) per iteration, then one vector
+// update pass -- six barriers per iteration against GMRES's eight, and no
+// orthogonalisation against a growing basis.  The stopping test is on the
+// Euclidean residual ||b - A x|| / ||b||, checked at the end with the FP64
+// operator (restarting the recurrence if the recursive residual drifted);
+// TK = float runs the recurrence in FP32 and restarts from the FP64 residual
+// whenever the residual has dropped by inner_tol (iterative refinement).
+template <int DIM, int DEG, typename TK, class Sync>
+__device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw, bool record) {
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N;
+  double* sred = (double*)smem_raw;  // [32]
+  double* sc = sred + 32;            // [16]
+  double* spart = sc + 16;           // [3*512]
+  double* sD64 = spart + 3 * 512;
+  double* sDw64 = sD64 + N * N;
+  double* sIt64 = sDw64 + N * N;
+  double* scell64 = sIt64 + 2 * N * N;
+  TK* sDk = (TK*)(scell64 + S::CPB * S::NC);
+  TK* sDwk = sDk + N * N;
+  TK* sItk = sDwk + N * N;
+  TK* scellk = (TK*)scell64;
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
+    sD64[q] = a.mv64.tab[S::T_D + q];
+    sDw64[q] = a.mv64.tab[S::T_DW + q];
+    sDk[q] = a.mvk.tab[S::T_D + q];
+    sDwk[q] = a.mvk.tab[S::T_DW + q];
+  }
+  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) {
+    sIt64[q] = a.mv64.tab[S::T_IT + q];
+    sItk[q] = a.mvk.tab[S::T_IT + q];
+  }
+  __syncthreads();
+  PhaseClock pc{record ? a.phase : nullptr, PhaseClock::now()};
+  const int64_t n = a.n;
+  const int G = sg.size;
+  const int64_t tid = (int64_t)sg.rank * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)G * blockDim.x;
+  const int64_t chunk1 = (n + G - 1) / G;
+  const int64_t lo = (int64_t)sg.rank * chunk1;
+  const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
+  const bool mixed = sizeof(TK) != sizeof(double);
+  TK* r = a.Q;
+  TK* p = a.Q + n;
+  TK* s = a.Q + 2 * n;
+  TK* w = a.w;
+  const TK* wJ = a.mvk.wJ;
+  TK* Ghk = (TK*)a.Gh;
+  TK* gvk = (TK*)a.gv;
+
+  {
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += a.b[i] * a.b[i];
+    const double t = block_sum(acc, sred);
+    if (threadIdx.x == 0) a.partial[sg.rank] = t;
+  }
+  sg.sync();
+  stage_partials(a.partial, G, spart);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < G; ++i) t += spart[i];
+    sc[0] = sqrt(t);
+  }
+  __syncthreads();
+  const double bn = sc[0];
+  if (bn == 0.0) {
+    for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
+    if (sg.rank == 0 && threadIdx.x == 0) {
+      a.out[0] = 0;
+      a.out[1] = 0;
+      a.out[2] = 1;
+      a.out[3] = 0;
+    }
+    return;
+  }
+  sg.sync();
+  int total = 0;
+  double rel = 1.0;
+  bool converged = false;
+  while (true) {
+    // true residual with the FP64 operator
+    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.Gh, a.gv, sg, scell64, sD64,
+                                    sDw64, sIt64, pc);
+    {
+      double acc = 0.0;
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double ri = a.b[i] - a.w64[i];
+        r[i] = (TK)ri;
+        acc += ri * ri;
+      }
+      const double t = block_sum(acc, sred);
+      if (threadIdx.x == 0) a.partial[sg.rank] = t;
+    }
+    sg.sync();
+    pc.mark(PH_RESIDUAL);
+    stage_partials(a.partial, G, spart);
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < G; ++i) t += spart[i];
+      sc[1] = sqrt(t);
+    }
+    __syncthreads();
+    const double beta0 = sc[1];
+    rel = beta0 / bn;
+    if (sg.failed()) break;
+    if (beta0 <= a.tol * bn) {
+      converged = true;
+      break;
+    }
+    if (total >= a.max_iters) break;
+    const double floor = fmax(a.tol * bn, (mixed ? a.inner_tol : 0.0) * beta0);
+    double alpha = 1.0, gamma = 1.0;
+    bool first = true;
+    for (;;) {
+      pmatvec<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(1), r, TK(1), w, Ghk, gvk, sg, scellk, sDk, sDwk,
+                                  sItk, pc);
+      {
+        TK g0 = TK(0), d0 = TK(0), e0 = TK(0);
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+          const TK ri = r[i], mi = wJ[i] * ri;
+          g0 += mi * ri;
+          d0 += mi * w[i];
+          e0 += ri * ri;
+        }
+        const double tg = block_sum_k<TK>(g0, sred);
+        const double td = block_sum_k<TK>(d0, sred);
+        const double te = block_sum_k<TK>(e0, sred);
+        if (threadIdx.x == 0) {
+          a.partial[3 * sg.rank] = tg;
+          a.partial[3 * sg.rank + 1] = td;
+          a.partial[3 * sg.rank + 2] = te;
+        }
+      }
+      sg.sync();
+      pc.mark(PH_DOTS);
+      stage_partials(a.partial, 3 * G, spart);
+      if (threadIdx.x == 0) {
+        double tg = 0.0, td = 0.0, te = 0.0;
+        for (int i = 0; i < G; ++i) {
+          tg += spart[3 * i];
+          td += spart[3 * i + 1];
+          te += spart[3 * i + 2];
+        }
+        sc[2] = tg;
+        sc[3] = td;
+        sc[4] = sqrt(te);
+      }
+      __syncthreads();
+      const double gnew = sc[2], delta = sc[3], rn = sc[4];
+      ++total;
+      rel = rn / bn;
+      if (sg.failed() || rn <= floor || total >= a.max_iters || !(delta > 0.0) || !(gnew > 0.0)) break;
+      double beta;
+      if (first) {
+        beta = 0.0;
+        alpha = gnew / delta;
+        first = false;
+      } else {
+        beta = gnew / gamma;
+        alpha = gnew / (delta - beta * gnew / alpha);
+      }
+      gamma = gnew;
+      const TK bk = (TK)beta, ak = (TK)alpha;
+      for (int64_t i = tid; i < n; i += gstride) {
+        const TK pi = r[i] + bk * p[i];
+        const TK si = w[i] + bk * s[i];
+        p[i] = pi;
+        s[i] = si;
+        a.x[i] += alpha * (double)pi;
+        r[i] -= ak * si;
+      }
+      sg.sync();
+      pc.mark(PH_UPDATE);
+    }
+    sg.sync();  // x complete before the residual mat-vec reads it
+    if (total >= a.max_iters || sg.failed()) {
+      // report the last residual estimate
+      break;
+    }
+  }
+  if (sg.rank == 0 && threadIdx.x == 0) {
+    a.out[0] = total;
+    a.out[1] = rel;
+    a.out[2] = (converged && !sg.failed()) ? 1.0 : 0.0;
+    a.out[3] = bn;
+    if (pc.acc) a.phase[PH_ITERS] += (unsigned long long)total;
+  }
+}
+
 template <int DIM, int DEG, typename TK>
 __global__ void __launch_bounds__(256, 2) gmres_persistent_kernel(GmresPArgs<TK> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GridSync sg;
-  gmres_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
+  if (a.method == 1)
+    cg_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
+  else
+    gmres_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
 }
 
 // Many independent solves in one cooperative launch: CTA b works on member
@@ -527,7 +724,10 @@ __global__ void __launch_bounds__(256, 3) gmres_batched_kernel(const GmresPArgs<
   SubSync sg{map.cta_rank[blockIdx.x], map.member_ctas[mem], map.bar_count + mem, map.bar_gen + mem, map.err,
              &sfail};
   const GmresPArgs<TK> a = args[mem];
-  gmres_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
+  if (a.method == 1)
+    cg_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
+  else
+    gmres_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
 }
 
 template <int DIM, int DEG, typename TK>
@@ -536,8 +736,10 @@ inline size_t gmres_smem_bytes(int m) {
   using S = Shape<DIM, DEG>;
   const size_t dbl = (size_t)(m + 1) + 2 * (size_t)(m + 2) + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m +
                      (m + 1) + 32 + 8 + 512;
-  return dbl * sizeof(double) + 4 * sizeof(int) + (size_t)(4 * N * N + S::CPB * S::NC) * sizeof(double) +
-         (size_t)(4 * N * N) * sizeof(TK) + 64;
+  const size_t tabs = (size_t)(4 * N * N + S::CPB * S::NC) * sizeof(double) + (size_t)(4 * N * N) * sizeof(TK);
+  const size_t gm = dbl * sizeof(double) + 4 * sizeof(int) + tabs + 64;
+  const size_t cg = (size_t)(32 + 16 + 3 * 512) * sizeof(double) + tabs + 64;
+  return gm > cg ? gm : cg;
 }
 
 }  // namespace dg

@@ -41,7 +41,7 @@ int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T
 // per-phase ns accumulators (16, or NULL).
 template <int DIM, typename TK>
 int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
-                 double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64,
+                 double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
                  double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s);
 // One member of a batched solve (see launch_gmres_batched).
 template <typename TK>
@@ -53,6 +53,7 @@ struct GmresItem {
   double* x;
   double alpha, tol, inner_tol;
   int max_iters;
+  int method;  // 0 GMRES, 1 CG
   TK* Q;
   TK* w;
   double* w64;
@@ -79,12 +80,12 @@ inline int op_gmres_batched(dg_ctx* ctx, int dim, const GmresItem<TK>* items, in
 
 template <typename TK>
 inline int op_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
-                    double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64,
+                    double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
                     double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
-  return m->dim == 2 ? launch_gmres<2, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart, max_iters, Q, w, w64,
-                                           partial, npartial, out, phase, s)
-                     : launch_gmres<3, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart, max_iters, Q, w, w64,
-                                           partial, npartial, out, phase, s);
+  return m->dim == 2 ? launch_gmres<2, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart, max_iters, method, Q,
+                                           w, w64, partial, npartial, out, phase, s)
+                     : launch_gmres<3, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart, max_iters, method, Q,
+                                           w, w64, partial, npartial, out, phase, s);
 }
 
 // dimension dispatch (with optional event timing per operator category)

@@ -66,8 +66,8 @@ int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, T* Dh, cu
 
 template <int DIM, int DEG, typename TK>
 int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
-              double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64, double* partial,
-              int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
+              double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
+              double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
   GmresPArgs<TK> a;
   a.mv64 = m->v64;
   a.mvk = view<TK>(m);
@@ -89,6 +89,8 @@ int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b
   a.m = restart;
   a.max_iters = max_iters;
   a.n = m->Nn;
+  a.method = method;
+  if (method == 1 && restart < 2) return fail(DG_EINVAL, "CG needs restart >= 2 (three work vectors)");
   auto kern = gmres_persistent_kernel<DIM, DEG, TK>;
   const size_t smem = gmres_smem_bytes<DIM, DEG, TK>(restart);
   if (smem > 48 * 1024) {
@@ -100,7 +102,7 @@ int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b
   if (e != cudaSuccess) return cuda_fail(e, "gmres occupancy");
   if (per_sm < 1) return fail(DG_ECUDA, "persistent GMRES kernel does not fit on an SM");
   int G = m->ctx->sm_count * (per_sm < 2 ? per_sm : 2);
-  if (G > npartial) G = npartial;
+  if (G > npartial / 3) G = npartial / 3;  // CG stores three partial sums per CTA
   if (G > 512) G = 512;  // staged partial sums in shared memory
   if (G < 1) return fail(DG_EINVAL, "GMRES partial buffer too small");
   count_launches(m->ctx, 1);
@@ -133,7 +135,7 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
     for (int i = 0; i < B; ++i) wsum += (double)it[i].m->Nn;
     int used = 0;
     for (int i = 0; i < B; ++i) {
-      const int cap = std::max(1, std::min(512, it[i].npartial / 2));
+      const int cap = std::max(1, std::min(512, it[i].npartial / 3));
       ctas[i] = std::min(cap, std::max(1, (int)((double)(gtot - B) * it[i].m->Nn / wsum) + 1));
       used += ctas[i];
     }
@@ -168,6 +170,7 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
       a.m = restart;
       a.max_iters = it[i].max_iters;
       a.n = m->Nn;
+      a.method = it[i].method;
       for (int r = 0; r < ctas[i]; ++r) {
         cta_member.push_back(i);
         cta_rank.push_back(r);
@@ -255,11 +258,11 @@ int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T
 
 template <int DIM, typename TK>
 int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
-                 double tol, double inner_tol, int restart, int max_iters, TK* Q, TK* w, double* w64,
+                 double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
                  double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
   DG_DEGREE_SWITCH(m->degree, return (run_gmres<DIM, DEG, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart,
-                                                               max_iters, Q, w, w64, partial, npartial, out, phase,
-                                                               s)))
+                                                               max_iters, method, Q, w, w64, partial, npartial, out,
+                                                               phase, s)))
 }
 
 template <int DIM, typename TK>
@@ -276,7 +279,7 @@ int launch_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, i
   template int launch_helmholtz<DIM, T>(const dg_mesh*, const T*, const T*, T*, T, T*, T*, cudaStream_t,       \
                                         const int*);                                                            \
   template int launch_gmres<DIM, T>(const dg_mesh*, const double*, const T*, const double*, double*, double,     \
-                                    double, double, int, int, T*, T*, double*, double*, int, double*,            \
+                                    double, double, int, int, int, T*, T*, double*, double*, int, double*,       \
                                     unsigned long long*, cudaStream_t);                                         \
   template int launch_gmres_batched<DIM, T>(dg_ctx*, const GmresItem<T>*, int, int, int*, cudaStream_t);
 

@@ -233,14 +233,14 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
   int rc;
   unsigned long long* phase = S->ctx->prof ? S->ctx->d_phase : nullptr;
   const int npart = (restart + 1) * kDotBlocks;
-  if (o->fused) {
+  if (o->fused || o->krylov == DG_KRYLOV_CG) {  // CG exists only in the persistent form
     ProfScope ps(S->ctx, DG_PROF_GMRES, s);
     if (o->precision == DG_FP64)
-      return op_gmres<double>(m, S->h, S->h, S->rhs, S->p, alpha, o->tol, 0.0, restart, o->max_iters, S->gm64.Q,
-                              S->gm64.w, S->gm64.w, S->gm64.d.partial, npart, out, phase, s);
+      return op_gmres<double>(m, S->h, S->h, S->rhs, S->p, alpha, o->tol, 0.0, restart, o->max_iters, o->krylov,
+                              S->gm64.Q, S->gm64.w, S->gm64.w, S->gm64.d.partial, npart, out, phase, s);
     float* h32 = S->f32;  // converted by phase_picard_pre
     return op_gmres<float>(m, S->h, h32, S->rhs, S->p, alpha, o->tol, o->inner_tol, restart, o->max_iters,
-                           S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, npart, out, phase, s);
+                           o->krylov, S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, npart, out, phase, s);
   }
   if (o->precision == DG_FP64) {
     rc = S->gm64.solve(S->ctx, A64, S->rhs, S->p, o->tol, o->max_iters, s, &res);
@@ -327,6 +327,7 @@ extern "C" void dg_solver_opts_default(dg_solver_opts* o) {
   o->inner_tol = 1e-4;
   o->max_refine = 20;
   o->fused = -1;
+  o->krylov = DG_KRYLOV_GMRES;
 }
 
 extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_opts* opts, dg_state** out) {
@@ -509,7 +510,7 @@ int phase_solve_single(Member& M, int i, cudaStream_t s) {
   const double dta = stage_dta(M, i);
   double* out = M.S->solve_out + 4 * M.nsolve;
   ++M.nsolve;
-  if (M.o.fused >= 0) return helmholtz_solve(M.S, &M.o, dta * dta, &M.st, out, s);
+  if (M.o.fused >= 0 || M.o.krylov == DG_KRYLOV_CG) return helmholtz_solve(M.S, &M.o, dta * dta, &M.st, out, s);
   const int pi = M.o.precision == DG_FP32 ? 1 : 0;
   dg_solver_opts o = M.o;
   if (M.m->tuned_fused[pi] >= 0) {
@@ -600,6 +601,7 @@ int prepare_member(Member& M, dg_ctx* ctx, const dg_mesh* m, dg_state* S, double
   if (opts) M.o = *opts;
   if (M.o.precision != DG_FP64 && M.o.precision != DG_FP32) return fail(DG_EINVAL, "bad precision");
   if (M.o.picard < 1 || M.o.picard > 32) return fail(DG_EINVAL, "picard must be in 1..32");
+  if (M.o.krylov != DG_KRYLOV_GMRES && M.o.krylov != DG_KRYLOV_CG) return fail(DG_EINVAL, "bad Krylov method");
   M.S = S;
   M.m = m;
   M.dt = dt;
@@ -674,7 +676,7 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, d
     std::vector<std::pair<std::pair<int, int>, int>> keys;
     for (int i = 0; i < n; ++i) {
       // members of a batch use the batched persistent solve unless told otherwise
-      if (M[i].o.fused == 0) {
+      if (M[i].o.fused == 0 && M[i].o.krylov != DG_KRYLOV_CG) {
         rest.push_back(i);
         continue;
       }
@@ -697,7 +699,7 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, d
         for (int i : groups[g]) {
           dg_state* S = M[i].S;
           const double dta = stage_dta(M[i], stage);
-          items.push_back({M[i].m, S->h, S->h, S->rhs, S->p, dta * dta, o.tol, 0.0, o.max_iters, S->gm64.Q,
+          items.push_back({M[i].m, S->h, S->h, S->rhs, S->p, dta * dta, o.tol, 0.0, o.max_iters, o.krylov, S->gm64.Q,
                            S->gm64.w, S->gm64.w, S->gm64.d.partial, (restart + 1) * kDotBlocks,
                            S->solve_out + 4 * M[i].nsolve});
         }
@@ -709,7 +711,7 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, d
           dg_state* S = M[i].S;
           const double dta = stage_dta(M[i], stage);
           items.push_back({M[i].m, S->h, S->f32, S->rhs, S->p, dta * dta, o.tol, o.inner_tol, o.max_iters,
-                           S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, (restart + 1) * kDotBlocks,
+                           o.krylov, S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, (restart + 1) * kDotBlocks,
                            S->solve_out + 4 * M[i].nsolve});
         }
         if ((rc = op_gmres_batched<float>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)

@@ -39,10 +39,10 @@ def _rel_dev(a, b, bg):
     return max(np.linalg.norm(a[v] - b[v]) / max(np.linalg.norm(b[v] - bg[v]), 1e-300) for v in range(a.shape[0]))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_batch_equals_alone(dg, ctx, precision):
+@pytest.mark.parametrize("precision,krylov", [("fp64", 0), ("fp32", 0), ("fp64", 1), ("fp32", 1)])
+def test_batch_equals_alone(dg, ctx, precision, krylov):
     prec = dg.DG_FP64 if precision == "fp64" else dg.DG_FP32
-    opts = dg.solver_opts(tol=1e-12, precision=prec, inner_tol=1e-4)
+    opts = dg.solver_opts(tol=1e-12, precision=prec, inner_tol=1e-4, krylov=krylov, fused=1)
     seeds = [1000, 1003, 1004, 1005, 1007, 1008, 1011, 1006]  # degrees 2..5, 16x8 .. 64x32, 0-2 levels
     cases = [member2d(s) for s in seeds]
     alone, meshes, states = [], [], []

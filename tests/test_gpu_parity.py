@@ -259,3 +259,16 @@ def test_autotuner_times_both_solver_forms(dg, ctx):
     assert t["ms_persistent"] > 0 and t["ms_multi_kernel"] > 0
     faster = "persistent" if t["ms_persistent"] <= t["ms_multi_kernel"] else "multi-kernel"
     assert t["form"] == faster
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_imex_steps_conjugate_gradients(dg, ctx, precision):
+    """CG in the w J inner product reaches the same step as the oracle's GMRES (M A is SPD)."""
+    prec = dg.DG_FP64 if precision == "fp64" else dg.DG_FP32
+    opts = dg.solver_opts(tol=1e-12, krylov=dg.DG_KRYLOV_CG, precision=prec, inner_tol=1e-4)
+    case = make_case("bubble2d", 0)
+    U, Ur, ref = _run_steps(dg, ctx, case, 10, opts)
+    assert _per_var_rel(U - ref.Ubg, Ur - ref.Ubg) < 1e-9
+    case = make_case("hill2d", 0)
+    U, Ur, ref = _run_steps(dg, ctx, case, 2, opts)
+    assert _per_var_rel(U - ref.Ubg, Ur - ref.Ubg) < 1e-9

@@ -39,7 +39,7 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 x
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel as it
 # stands (profiles/gmres_persistent_hill2d.md); set to None whenever that kernel changes
-NCU_TRAFFIC_BYTES = {("hill2d", "gmres"): 5.8176e6 + 0.377088e6}
+NCU_TRAFFIC_BYTES = {}  # (workload, kernel) -> dram read+write bytes per launch from one ncu capture
 
 
 def algorithmic(dim, degree, n_nodes, kind, s=8):
@@ -217,8 +217,8 @@ def apply_sweep(dg, torch, case_name, reps=10):
 
 
 def ensemble_bench(dg, torch, n_members=64, steps=10):
-    """Config-4 shape: 64 uneven 2D members (16x8..128x64 base, 0-2 levels, degree 2-5), FP32-refined,
-    one dg_batch_step per ensemble step."""
+    """64 uneven 2D members (16x8..128x64 base, 0-2 levels, degree 2-5), FP32-refined: one
+    dg_batch_step per ensemble step, then the same step as a captured batch plan (CUDA graph)."""
     from workloads.cases import member2d
 
     ctx = dg.Context(torch.cuda.current_device())
@@ -243,11 +243,34 @@ def ensemble_bench(dg, torch, n_members=64, steps=10):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    # the same step captured once as a CUDA graph (members on parallel branches), then replayed
+    t0 = time.perf_counter()
+    plan = dg.BatchPlan(ctx, meshes, states, dts, opts)
+    capture_ms = (time.perf_counter() - t0) * 1e3
+    plan.step()  # warm-up
+    torch.cuda.synchronize()
+    n0 = dg.dg_launch_count(ctx)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    giters = 0
+    for _ in range(steps):
+        res = plan.step()
+        giters += sum(r["gmres_iters"] for r in res)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gms = g0.elapsed_time(g1)
+    kernels_per_step = (dg.dg_launch_count(ctx) - n0) / steps
+    plan.close()
     dof = sum(m.n_dof for m in meshes)
     out = {"workload": "%d 2D members (base 16x8..128x64, 0-2 levels, degree 2-5), %d DoF in all, "
-                       "FP32 Krylov + FP64 residual, dg_batch_step" % (n_members, dof),
-           "member_steps_per_s": n_members * steps / (ms / 1e3), "dof_steps_per_s": dof * steps / (ms / 1e3),
-           "ms_per_ensemble_step": ms / steps, "gmres_iters_per_member_step": iters / (n_members * steps)}
+                       "FP32 Krylov + FP64 residual, one CUDA-graph replay per ensemble step" % (n_members, dof),
+           "member_steps_per_s": n_members * steps / (gms / 1e3), "dof_steps_per_s": dof * steps / (gms / 1e3),
+           "ms_per_ensemble_step": gms / steps, "gmres_iters_per_member_step": giters / (n_members * steps),
+           "graph_capture_ms": capture_ms, "kernels_per_ensemble_step": kernels_per_step,
+           "without_graph": {"ms_per_ensemble_step": ms / steps,
+                             "member_steps_per_s": n_members * steps / (ms / 1e3),
+                             "gmres_iters_per_member_step": iters / (n_members * steps)}}
     for st in states:
         st.close()
     for m in meshes:
@@ -401,14 +424,17 @@ def main():
     # the FP32-refined form from the same start: FP32 applies + FP32 inner GMRES, FP64 outer residual
     opts32 = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=dg.DG_FP32, inner_tol=1e-4)
     state.upload(U_start)
-    times32 = []
+    for _ in range(args.warmup):  # untimed: lazy loading and the autotuner's first FP32 solve
+        dg.imex_rk2_step(ctx, mesh, state, case.dt, opts32)
+    state.upload(U_start)
+    times32, its32 = [], 0
     for _ in range(args.steps):
         flush.zero_()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         ev0.record(stream)
-        dg.imex_rk2_step(ctx, mesh, state, case.dt, opts32)
+        its32 += dg.imex_rk2_step(ctx, mesh, state, case.dt, opts32)["gmres_iters"]
         ev1.record(stream)
         torch.cuda.synchronize()
         times32.append(ev0.elapsed_time(ev1))
@@ -422,6 +448,7 @@ def main():
     fp32 = {"ms_per_step": sum(times32) / args.steps,
             "value": world * dof * args.steps / (sum(times32) / 1e3),
             "speedup_vs_fp64": sum(times) / sum(times32),
+            "inner_iters_per_step": its32 / args.steps,
             "rel_err_vs_fp64_full_state": rel_full,
             "rel_err_vs_fp64_deviation": rel_dev}
     # conjugate gradients (the Helmholtz operator is self-adjoint in the w J inner product),
@@ -430,6 +457,9 @@ def main():
     for name, prec in (("fp64", dg.DG_FP64), ("fp32_refined", dg.DG_FP32)):
         o = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=prec, inner_tol=1e-4,
                            krylov=dg.DG_KRYLOV_CG)
+        state.upload(U_start)
+        for _ in range(args.warmup):
+            dg.imex_rk2_step(ctx, mesh, state, case.dt, o)
         state.upload(U_start)
         tms, its = [], 0
         for _ in range(args.steps):

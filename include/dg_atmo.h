@@ -287,6 +287,28 @@ int imex_rk2_step(dg_ctx* ctx, const dg_mesh* mesh, dg_state* state, double dt, 
 int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states, const double* dt,
                   const dg_solver_opts* opts, dg_step_stats* stats, int* statuses, void* stream);
 
+/* Batch plan: the ensemble step of dg_batch_step captured once as a CUDA graph
+ * and replayed for every later step (the paper's ensemble has no counterpart;
+ * this is the batching form of the step, Sec. 2 scheme per member).  In the
+ * graph, each member's per-phase kernels sit on one of up to 16 parallel
+ * branches, joined before each batched Helmholtz launch (one cooperative node
+ * per (dimension, degree, precision) group and Picard iteration), and the
+ * solve results and flags are copied to pinned host memory at the end.
+ * dg_batch_plan_create captures (runs nothing on the device); the members'
+ * meshes and states, and dt[i], are fixed for the plan's lifetime: meshes and
+ * states must outlive the plan and may not be used by another call while a
+ * plan step runs.  Needs the persistent solve (opts->fused != 0, or CG);
+ * DG_EINVAL otherwise or if two members share a mesh.  Each replay computes
+ * exactly what dg_batch_step computes on the same members (same kernels,
+ * same launch shapes, same per-member order).
+ * dg_batch_plan_step launches the graph on `stream`, waits for it, and fills
+ * stats[n] / statuses[n] (either may be NULL) like dg_batch_step. */
+typedef struct dg_batch_plan dg_batch_plan;
+int dg_batch_plan_create(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states,
+                         const double* dt, const dg_solver_opts* opts, dg_batch_plan** out);
+int dg_batch_plan_step(dg_batch_plan* plan, dg_step_stats* stats, int* statuses, void* stream);
+int dg_batch_plan_destroy(dg_batch_plan* plan);
+
 /* ---------------------------------------------------------------- serving
  * A request loop for simulation requests of different mesh sizes, degrees,
  * orographies and precisions.  Requests are queued on submit; a worker thread

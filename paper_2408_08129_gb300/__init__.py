@@ -12,6 +12,7 @@ from .api import (  # noqa: F401
     DG_KRYLOV_GMRES,
     DG_TERMS_FULL,
     DG_TERMS_IMEX_EXPLICIT,
+    BatchPlan,
     Context,
     DGError,
     Mesh,

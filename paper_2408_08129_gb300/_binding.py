@@ -123,6 +123,9 @@ def _load():
         "dg_state_download": (c_int, [P, P]),
         "imex_rk2_step": (c_int, [P, P, P, c_double, ctypes.POINTER(SolverOpts), ctypes.POINTER(StepStats), P]),
         "dg_batch_step": (c_int, [P, c_int, P, P, P, ctypes.POINTER(SolverOpts), P, P, P]),
+        "dg_batch_plan_create": (c_int, [P, c_int, P, P, P, ctypes.POINTER(SolverOpts), ctypes.POINTER(P)]),
+        "dg_batch_plan_step": (c_int, [P, P, P, P]),
+        "dg_batch_plan_destroy": (c_int, [P]),
         "dg_serve_create": (c_int, [P, ctypes.POINTER(ServeOpts), ctypes.POINTER(P)]),
         "dg_serve_submit": (c_int, [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
         "dg_serve_poll": (c_int, [P, ctypes.c_uint64, ctypes.POINTER(RequestInfo), P]),

@@ -328,6 +328,51 @@ def dg_batch_step(ctx, meshes, states, dts, opts=None, stream=None, raise_on_err
     return out
 
 
+class BatchPlan:
+    """dg_batch_plan: the ensemble step of dg_batch_step captured once as a CUDA graph, then replayed.
+
+    Keeps references to the meshes and states, which the plan uses on every step.
+    """
+
+    def __init__(self, ctx, meshes, states, dts, opts=None):
+        n = len(states)
+        if not (len(meshes) == n == len(dts)):
+            raise ValueError("meshes, states and dts must have the same length")
+        self.ctx, self.meshes, self.states, self.n = ctx, list(meshes), list(states), n
+        o = opts if opts is not None else solver_opts()
+        mh = (ctypes.c_void_p * n)(*[m.handle.value for m in meshes])
+        sh = (ctypes.c_void_p * n)(*[st.handle.value for st in states])
+        dt = (ctypes.c_double * n)(*[float(x) for x in dts])
+        h = ctypes.c_void_p()
+        check(lib.dg_batch_plan_create(ctx.handle, n, mh, sh, dt, ctypes.byref(o), ctypes.byref(h)),
+              "dg_batch_plan_create")
+        self.handle = h
+
+    def step(self, stream=None, raise_on_error=True):
+        stats = (B.StepStats * self.n)()
+        statuses = (ctypes.c_int * self.n)()
+        rc = lib.dg_batch_plan_step(self.handle, stats, statuses, _stream(stream))
+        if raise_on_error:
+            check(rc, "dg_batch_plan_step")
+        out = []
+        for i in range(self.n):
+            d = {k: getattr(stats[i], k) for k, _ in B.StepStats._fields_}
+            d["status"] = statuses[i]
+            out.append(d)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib.dg_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 

@@ -69,6 +69,25 @@ struct MeshView {
 
 }  // namespace dg
 
+namespace dg {
+// Argument tables of batched launches recorded into a CUDA graph: the tables
+// are written into `host` while the graph is captured and copied to `dev` once
+// the capture has ended (before the graph's first launch), so the captured
+// launches read tables that stay in place for every replay.
+struct BatchArena {
+  unsigned char* dev = nullptr;
+  std::vector<unsigned char> host;
+  size_t used = 0;
+  // 256-byte aligned region of `bytes`, or SIZE_MAX if the arena is full
+  size_t take(size_t bytes) {
+    const size_t off = (used + 255) & ~(size_t)255;
+    if (off + bytes > host.size()) return SIZE_MAX;
+    used = off + bytes;
+    return off;
+  }
+};
+}  // namespace dg
+
 struct dg_ctx {
   int device = 0;
   int sm_count = 0;
@@ -85,6 +104,7 @@ struct dg_ctx {
   void* d_batch = nullptr;  // workspace of batched solves (argument table, CTA map, barriers)
   size_t batch_bytes = 0;
   int* d_batch_err = nullptr;  // barrier-timeout flag of batched launches
+  dg::BatchArena* arena = nullptr;  // set while a batch plan is being captured
 };
 
 namespace dg {

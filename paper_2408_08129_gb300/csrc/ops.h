@@ -62,6 +62,9 @@ struct GmresItem {
   double* out;
 };
 
+// upper bound of one member's entry in a batched launch's argument table
+constexpr size_t kBatchArgBytes = 1024;
+
 // Solve every item's Helmholtz system in ONE cooperative launch (more if the
 // items outnumber the co-resident CTAs).  All items share dimension, degree
 // and TK, and no two share a mesh (the mesh holds the mat-vec scratch).  The

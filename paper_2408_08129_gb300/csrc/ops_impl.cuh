@@ -115,6 +115,7 @@ int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b
 template <int DIM, int DEG, typename TK>
 int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int restart, int* err,
                       cudaStream_t s) {
+  static_assert(sizeof(GmresPArgs<TK>) <= kBatchArgBytes, "argument table entry larger than planned");
   auto kern = gmres_batched_kernel<DIM, DEG, TK>;
   const size_t smem = gmres_smem_bytes<DIM, DEG, TK>(restart);
   if (smem > 48 * 1024) {
@@ -181,24 +182,35 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
     const size_t b_map = (((size_t)2 * G + B) * sizeof(int) + 255) & ~(size_t)255;
     const size_t b_bar = ((size_t)2 * B) * sizeof(unsigned int);
     const size_t need = b_args + b_map + b_bar + 256;
-    if (need > ctx->batch_bytes) {
-      if (ctx->d_batch) {
-        DG_CUDA(cudaStreamSynchronize(s));
-        cudaFree(ctx->d_batch);
+    unsigned char* dev;
+    unsigned char* host;
+    std::vector<unsigned char> staging;
+    if (ctx->arena) {  // graph capture: tables go to the plan's arena, uploaded after the capture
+      const size_t off = ctx->arena->take(need);
+      if (off == SIZE_MAX) return fail(DG_EINVAL, "batch plan argument arena is full");
+      dev = ctx->arena->dev + off;
+      host = ctx->arena->host.data() + off;
+    } else {
+      if (need > ctx->batch_bytes) {
+        if (ctx->d_batch) {
+          DG_CUDA(cudaStreamSynchronize(s));
+          cudaFree(ctx->d_batch);
+        }
+        ctx->d_batch = nullptr;
+        ctx->batch_bytes = 0;
+        DG_CUDA(cudaMalloc(&ctx->d_batch, need * 2));
+        ctx->batch_bytes = need * 2;
       }
-      ctx->d_batch = nullptr;
-      ctx->batch_bytes = 0;
-      DG_CUDA(cudaMalloc(&ctx->d_batch, need * 2));
-      ctx->batch_bytes = need * 2;
+      dev = (unsigned char*)ctx->d_batch;
+      staging.assign(b_args + b_map, 0);
+      host = staging.data();
     }
-    std::vector<unsigned char> host(b_args + b_map, 0);
-    std::memcpy(host.data(), args.data(), sizeof(GmresPArgs<TK>) * B);
-    int* hm = (int*)(host.data() + b_args);
+    std::memcpy(host, args.data(), sizeof(GmresPArgs<TK>) * B);
+    int* hm = (int*)(host + b_args);
     std::memcpy(hm, cta_member.data(), G * sizeof(int));
     std::memcpy(hm + G, cta_rank.data(), G * sizeof(int));
     std::memcpy(hm + 2 * G, ctas.data(), B * sizeof(int));
-    unsigned char* dev = (unsigned char*)ctx->d_batch;
-    DG_CUDA(cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    if (!ctx->arena) DG_CUDA(cudaMemcpyAsync(dev, host, b_args + b_map, cudaMemcpyHostToDevice, s));
     DG_CUDA(cudaMemsetAsync(dev + b_args + b_map, 0, b_bar, s));
     BatchMap map;
     const int* dm = (const int*)(dev + b_args);
@@ -213,8 +225,8 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
     void* kargs[] = {(void*)&dargs, (void*)&map};
     e = cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(256), kargs, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "batched GMRES launch");
-    // the argument table is rewritten by the next chunk: keep launches ordered
-    if (first + B < n_items) DG_CUDA(cudaStreamSynchronize(s));
+    // the shared argument table is rewritten by the next chunk: keep launches ordered
+    if (!ctx->arena && first + B < n_items) DG_CUDA(cudaStreamSynchronize(s));
   }
   return DG_OK;
 }

@@ -502,8 +502,8 @@ int phase_picard_pre(Member& M, int i, cudaStream_t s) {
 
 // Autotuner: with fused = -1 the first solve of a (mesh, precision) is run
 // both as the persistent single-launch kernel and as one launch per Krylov
-// kernel, from the same initial guess, and the faster form is kept for every
-// later solve on that mesh (the persistent form wins on small meshes, where
+// kernel, from the same initial guess (two rounds, the second one timed), and
+// the faster form is kept for every later solve on that mesh (the persistent form wins on small meshes, where
 // launch latency dominates; the multi-kernel form on large FP64 meshes, where
 // full occupancy hides the FP64 pipe's latency).
 int phase_solve_single(Member& M, int i, cudaStream_t s) {
@@ -523,11 +523,23 @@ int phase_solve_single(Member& M, int i, cudaStream_t s) {
   for (auto& ev : e) DG_CUDA(cudaEventCreate(&ev));
   int rc;
   float ms[2] = {0, 0};
-  for (int f = 1; f >= 0; --f) {
-    if (f == 0) DG_CUDA(cudaMemcpyAsync(S->p, S->p_save, S->Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    o.fused = f;
-    DG_CUDA(cudaEventRecord(e[f == 1 ? 0 : 1], s));
-    if ((rc = helmholtz_solve(S, &o, dta * dta, &M.st, out, s)) != DG_OK) return rc;
+  // Two rounds, each form from the same initial guess: the first round pays
+  // the one-off costs (lazy module loading, occupancy queries, first-touch of
+  // the Krylov workspace) and is not timed; the second is.
+  bool first = true;
+  const dg_step_stats st0 = M.st;  // only the last (kept) solve counts in the step's statistics
+  for (int round = 0; round < 2; ++round) {
+    for (int f = 1; f >= 0; --f) {
+      M.st = st0;
+      if (!first) DG_CUDA(cudaMemcpyAsync(S->p, S->p_save, S->Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      first = false;
+      o.fused = f;
+      if (round == 1) DG_CUDA(cudaEventRecord(e[f == 1 ? 0 : 1], s));
+      if ((rc = helmholtz_solve(S, &o, dta * dta, &M.st, out, s)) != DG_OK) {
+        for (auto& ev : e) cudaEventDestroy(ev);
+        return rc;
+      }
+    }
   }
   DG_CUDA(cudaEventRecord(e[2], s));
   DG_CUDA(cudaEventSynchronize(e[2]));
@@ -644,97 +656,180 @@ extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double 
   return status;
 }
 
-extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states,
-                             const double* dt, const dg_solver_opts* opts, dg_step_stats* stats, int* statuses,
-                             void* stream) {
+namespace dg {
+namespace {
+
+// Parallel branches for the per-member phases of a captured batch step: each
+// segment of member work forks from the main stream, member i runs on branch
+// i mod K, and the branches join before the next batched solve.
+struct Branches {
+  std::vector<cudaStream_t> st;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+};
+
+// Batched Helmholtz solves of one Picard iteration: the persistent solves
+// grouped by (dim, degree, precision), one batched launch per group; members
+// that asked for the one-launch-per-kernel form are solved alone.
+int solve_all(dg_ctx* ctx, std::vector<Member>& M, const dg_solver_opts& o, int stage, int* err,
+              cudaStream_t s) {
+  const int n = (int)M.size();
+  const int restart = std::min(o.restart, kMaxRestart);
+  int rc;
+  std::vector<int> rest;
+  std::vector<std::vector<int>> groups;
+  std::vector<std::pair<std::pair<int, int>, int>> keys;
+  for (int i = 0; i < n; ++i) {
+    // members of a batch use the batched persistent solve unless told otherwise
+    if (M[i].o.fused == 0 && M[i].o.krylov != DG_KRYLOV_CG) {
+      rest.push_back(i);
+      continue;
+    }
+    const std::pair<int, int> key{M[i].m->dim * 16 + M[i].m->degree, M[i].o.precision};
+    size_t g = 0;
+    for (; g < keys.size(); ++g)
+      if (keys[g].first == key) break;
+    if (g == keys.size()) {
+      keys.push_back({key, (int)g});
+      groups.emplace_back();
+    }
+    groups[g].push_back(i);
+  }
+  for (size_t g = 0; g < groups.size(); ++g) {
+    ProfScope ps(ctx, DG_PROF_GMRES, s);
+    const int dim = M[groups[g][0]].m->dim;
+    const bool f32 = keys[g].first.second == DG_FP32;
+    if (!f32) {
+      std::vector<GmresItem<double>> items;
+      for (int i : groups[g]) {
+        dg_state* S = M[i].S;
+        const double dta = stage_dta(M[i], stage);
+        items.push_back({M[i].m, S->h, S->h, S->rhs, S->p, dta * dta, o.tol, 0.0, o.max_iters, o.krylov, S->gm64.Q,
+                         S->gm64.w, S->gm64.w, S->gm64.d.partial, (restart + 1) * kDotBlocks,
+                         S->solve_out + 4 * M[i].nsolve});
+      }
+      if ((rc = op_gmres_batched<double>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)
+        return rc;
+    } else {
+      std::vector<GmresItem<float>> items;
+      for (int i : groups[g]) {
+        dg_state* S = M[i].S;
+        const double dta = stage_dta(M[i], stage);
+        items.push_back({M[i].m, S->h, S->f32, S->rhs, S->p, dta * dta, o.tol, o.inner_tol, o.max_iters, o.krylov,
+                         S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, (restart + 1) * kDotBlocks,
+                         S->solve_out + 4 * M[i].nsolve});
+      }
+      if ((rc = op_gmres_batched<float>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)
+        return rc;
+    }
+    for (int i : groups[g]) ++M[i].nsolve;
+  }
+  for (int i : rest)
+    if ((rc = phase_solve_single(M[i], stage, s)) != DG_OK) return rc;
+  return DG_OK;
+}
+
+// One IMEX-RK2 step of every member: the per-member phases (on branches if
+// given) between the batched solves of each Picard iteration.
+int batch_phases(dg_ctx* ctx, std::vector<Member>& M, const dg_solver_opts& o, int* err, cudaStream_t s,
+                 const Branches* br) {
+  int rc;
+  // run body(member, stream) for every member, forked over the branches
+  auto segment = [&](auto&& body) -> int {
+    const int K = br ? (int)br->st.size() : 0;
+    if (K == 0) {
+      for (auto& mm : M)
+        if ((rc = body(mm, s)) != DG_OK) return rc;
+      return DG_OK;
+    }
+    DG_CUDA(cudaEventRecord(br->fork, s));
+    for (int k = 0; k < K; ++k) DG_CUDA(cudaStreamWaitEvent(br->st[k], br->fork, 0));
+    for (size_t i = 0; i < M.size(); ++i)
+      if ((rc = body(M[i], br->st[i % K])) != DG_OK) return rc;
+    for (int k = 0; k < K; ++k) {
+      DG_CUDA(cudaEventRecord(br->join[k], br->st[k]));
+      DG_CUDA(cudaStreamWaitEvent(s, br->join[k], 0));
+    }
+    return DG_OK;
+  };
+#define RUN(x)                          \
+  do {                                  \
+    if ((rc = (x)) != DG_OK) return rc; \
+  } while (0)
+  RUN(segment([&](Member& mm, cudaStream_t t) {
+    int r;
+    if ((r = phase_stage1(mm, t)) != DG_OK) return r;
+    if ((r = phase_stage_begin(mm, 1, t)) != DG_OK) return r;
+    return phase_picard_pre(mm, 1, t);
+  }));
+  for (int i = 1; i <= 2; ++i) {
+    for (int it = 0; it < o.picard; ++it) {
+      RUN(solve_all(ctx, M, o, i, err, s));
+      const bool last = it == o.picard - 1;
+      RUN(segment([&](Member& mm, cudaStream_t t) {
+        int r;
+        if ((r = phase_picard_post(mm, i, t)) != DG_OK) return r;
+        if (!last) return phase_picard_pre(mm, i, t);
+        if ((r = phase_stage_end(mm, i, t)) != DG_OK) return r;
+        if (i == 1) {
+          if ((r = phase_stage_begin(mm, 2, t)) != DG_OK) return r;
+          return phase_picard_pre(mm, 2, t);
+        }
+        return phase_final(mm, t);
+      }));
+    }
+  }
+#undef RUN
+  return DG_OK;
+}
+
+int prepare_batch(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states, const double* dt,
+                  const dg_solver_opts* opts, std::vector<Member>& M) {
   if (!ctx || n < 0 || (n > 0 && (!meshes || !states || !dt))) return fail(DG_EINVAL, "null argument");
-  if (n == 0) return DG_OK;
-  std::vector<Member> M(n);
+  M.assign(n, Member{});
   int rc;
   for (int i = 0; i < n; ++i) {
     if ((rc = prepare_member(M[i], ctx, meshes[i], states[i], dt[i], opts)) != DG_OK) return rc;
     for (int j = 0; j < i; ++j)
       if (meshes[j] == meshes[i]) return fail(DG_EINVAL, "members of a batch must not share a mesh");
   }
+  if (n > 0) {
+    const int restart = std::min(M[0].o.restart, kMaxRestart);
+    for (int i = 0; i < n; ++i)
+      if (M[i].S->restart < restart) return fail(DG_EINVAL, "a state was created with a shorter restart length");
+  }
+  if (!ctx->d_batch_err) DG_CUDA(cudaMalloc(&ctx->d_batch_err, sizeof(int)));
+  return DG_OK;
+}
+
+// statuses and statistics of every member from the flags and solve results read back after the step
+int finish_batch(std::vector<Member>& M, const int* flags, const double* sol, int herr, dg_step_stats* stats,
+                 int* statuses) {
+  int worst = DG_OK;
+  for (size_t i = 0; i < M.size(); ++i) {
+    int st = member_finish(M[i], &sol[i * 256], flags[i]);
+    if (herr) st = fail(DG_ETIMEOUT, "a barrier of the batched GMRES launch ran out of time");
+    if (stats) stats[i] = M[i].st;
+    if (statuses) statuses[i] = st;
+    if (st != DG_OK && worst == DG_OK) worst = st;
+  }
+  return worst;
+}
+
+}  // namespace
+}  // namespace dg
+
+extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states,
+                             const double* dt, const dg_solver_opts* opts, dg_step_stats* stats, int* statuses,
+                             void* stream) {
+  std::vector<Member> M;
+  int rc = prepare_batch(ctx, n, meshes, states, dt, opts, M);
+  if (rc != DG_OK || n == 0) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   ProfScope step_scope(ctx, DG_PROF_STEP, s);
-  const dg_solver_opts& o = M[0].o;
-  const int restart = std::min(o.restart, kMaxRestart);
-  for (int i = 0; i < n; ++i)
-    if (M[i].S->restart < restart) return fail(DG_EINVAL, "a state was created with a shorter restart length");
-  if (!ctx->d_batch_err) DG_CUDA(cudaMalloc(&ctx->d_batch_err, sizeof(int)));
   int* err = ctx->d_batch_err;
   DG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-#define RUN(x)                          \
-  do {                                  \
-    if ((rc = (x)) != DG_OK) return rc; \
-  } while (0)
-  // batched solve of one Picard iteration: fused solves grouped by (dim, degree, precision)
-  auto solve_all = [&](int stage) -> int {
-    std::vector<int> rest;
-    std::vector<std::vector<int>> groups;
-    std::vector<std::pair<std::pair<int, int>, int>> keys;
-    for (int i = 0; i < n; ++i) {
-      // members of a batch use the batched persistent solve unless told otherwise
-      if (M[i].o.fused == 0 && M[i].o.krylov != DG_KRYLOV_CG) {
-        rest.push_back(i);
-        continue;
-      }
-      const std::pair<int, int> key{M[i].m->dim * 16 + M[i].m->degree, M[i].o.precision};
-      size_t g = 0;
-      for (; g < keys.size(); ++g)
-        if (keys[g].first == key) break;
-      if (g == keys.size()) {
-        keys.push_back({key, (int)g});
-        groups.emplace_back();
-      }
-      groups[g].push_back(i);
-    }
-    for (size_t g = 0; g < groups.size(); ++g) {
-      ProfScope ps(ctx, DG_PROF_GMRES, s);
-      const int dim = M[groups[g][0]].m->dim;
-      const bool f32 = keys[g].first.second == DG_FP32;
-      if (!f32) {
-        std::vector<GmresItem<double>> items;
-        for (int i : groups[g]) {
-          dg_state* S = M[i].S;
-          const double dta = stage_dta(M[i], stage);
-          items.push_back({M[i].m, S->h, S->h, S->rhs, S->p, dta * dta, o.tol, 0.0, o.max_iters, o.krylov, S->gm64.Q,
-                           S->gm64.w, S->gm64.w, S->gm64.d.partial, (restart + 1) * kDotBlocks,
-                           S->solve_out + 4 * M[i].nsolve});
-        }
-        if ((rc = op_gmres_batched<double>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)
-          return rc;
-      } else {
-        std::vector<GmresItem<float>> items;
-        for (int i : groups[g]) {
-          dg_state* S = M[i].S;
-          const double dta = stage_dta(M[i], stage);
-          items.push_back({M[i].m, S->h, S->f32, S->rhs, S->p, dta * dta, o.tol, o.inner_tol, o.max_iters,
-                           o.krylov, S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, (restart + 1) * kDotBlocks,
-                           S->solve_out + 4 * M[i].nsolve});
-        }
-        if ((rc = op_gmres_batched<float>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)
-          return rc;
-      }
-      for (int i : groups[g]) ++M[i].nsolve;
-    }
-    for (int i : rest)
-      if ((rc = phase_solve_single(M[i], stage, s)) != DG_OK) return rc;
-    return DG_OK;
-  };
-  for (auto& mm : M) RUN(phase_stage1(mm, s));
-  for (int i = 1; i <= 2; ++i) {
-    for (auto& mm : M) RUN(phase_stage_begin(mm, i, s));
-    for (int it = 0; it < o.picard; ++it) {
-      for (auto& mm : M) RUN(phase_picard_pre(mm, i, s));
-      RUN(solve_all(i));
-      for (auto& mm : M) RUN(phase_picard_post(mm, i, s));
-    }
-    for (auto& mm : M) RUN(phase_stage_end(mm, i, s));
-  }
-  for (auto& mm : M) RUN(phase_final(mm, s));
-#undef RUN
+  if ((rc = batch_phases(ctx, M, M[0].o, err, s, nullptr)) != DG_OK) return rc;
   // read every member's flag and solve results with one synchronisation
   std::vector<int> flags(n, 0);
   std::vector<double> sol((size_t)n * 256, 0.0);
@@ -746,13 +841,138 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, d
   }
   DG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
-  int worst = DG_OK;
-  for (int i = 0; i < n; ++i) {
-    int st = member_finish(M[i], &sol[(size_t)i * 256], flags[i]);
-    if (herr) st = fail(DG_ETIMEOUT, "a barrier of the batched GMRES launch ran out of time");
-    if (stats) stats[i] = M[i].st;
-    if (statuses) statuses[i] = st;
-    if (st != DG_OK && worst == DG_OK) worst = st;
+  return finish_batch(M, flags.data(), sol.data(), herr, stats, statuses);
+}
+
+// ---- batch plans: one captured CUDA graph per ensemble step ----
+
+struct dg_batch_plan {
+  dg_ctx* ctx = nullptr;
+  std::vector<dg::Member> M;
+  int n = 0;
+  cudaStream_t cs = nullptr;  // capture stream
+  dg::Branches br;
+  dg::BatchArena arena;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;       // kernels in one replay
+  int* h_flags = nullptr;      // pinned: [n] flags, then the timeout flag
+  double* h_sol = nullptr;     // pinned: [n*256] solve results
+};
+
+extern "C" int dg_batch_plan_destroy(dg_batch_plan* P) {
+  if (!P) return DG_OK;
+  cudaSetDevice(P->ctx->device);
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  for (auto st : P->br.st) cudaStreamDestroy(st);
+  for (auto ev : P->br.join) cudaEventDestroy(ev);
+  if (P->br.fork) cudaEventDestroy(P->br.fork);
+  if (P->cs) cudaStreamDestroy(P->cs);
+  if (P->arena.dev) cudaFree(P->arena.dev);
+  if (P->h_flags) cudaFreeHost(P->h_flags);
+  if (P->h_sol) cudaFreeHost(P->h_sol);
+  delete P;
+  return DG_OK;
+}
+
+extern "C" int dg_batch_plan_create(dg_ctx* ctx, int n, const dg_mesh* const* meshes, dg_state* const* states,
+                                    const double* dt, const dg_solver_opts* opts, dg_batch_plan** out) {
+  if (!out) return fail(DG_EINVAL, "null argument");
+  *out = nullptr;
+  if (n < 1) return fail(DG_EINVAL, "a batch plan needs at least one member");
+  dg_batch_plan* P = new (std::nothrow) dg_batch_plan();
+  if (!P) return fail(DG_ENOMEM, "host allocation failed");
+  P->ctx = ctx;
+  P->n = n;
+  int rc = prepare_batch(ctx, n, meshes, states, dt, opts, P->M);
+  if (rc != DG_OK) {
+    delete P;
+    return rc;
   }
-  return worst;
+  for (auto& mm : P->M)
+    if (mm.o.fused == 0 && mm.o.krylov != DG_KRYLOV_CG) {
+      delete P;
+      return fail(DG_EINVAL, "a batch plan needs the persistent solve (fused != 0)");
+    }
+  const dg_solver_opts& o = P->M[0].o;
+  auto bail = [&](int r) {
+    dg_batch_plan_destroy(P);
+    return r;
+  };
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking);
+  const int K = std::min(n, 16);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) P->br.st.push_back(st);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) P->br.join.push_back(ev);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->br.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMallocHost(&P->h_flags, (n + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&P->h_sol, (size_t)n * 256 * sizeof(double));
+  // argument tables of the batched launches: per launch at most one table of
+  // n members and a CTA map of 2 x (2 CTAs per SM) entries; one launch per
+  // group (at most n) in each of the 2 x picard Picard iterations
+  const size_t per_member = kBatchArgBytes;
+  const size_t per_launch = (size_t)(2 * 2 * ctx->sm_count) * sizeof(int) + 4 * 256;
+  const size_t arena_bytes = (size_t)2 * o.picard * ((per_member + 3 * sizeof(int) + 16) * n + per_launch * n);
+  if (e == cudaSuccess) e = cudaMalloc(&P->arena.dev, arena_bytes);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "batch plan resources"));
+  P->arena.host.assign(arena_bytes, 0);
+
+  // capture one step; nothing runs while the capture is open
+  const bool prof = ctx->prof;
+  const long long launches0 = ctx->launches;
+  ctx->prof = false;
+  ctx->arena = &P->arena;
+  int* err = ctx->d_batch_err;
+  e = cudaStreamBeginCapture(P->cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = DG_OK;
+    e = cudaMemsetAsync(err, 0, sizeof(int), P->cs);
+    if (e != cudaSuccess) rc = cuda_fail(e, "batch plan capture");
+    if (rc == DG_OK) rc = batch_phases(ctx, P->M, o, err, P->cs, &P->br);
+    for (int i = 0; i < n && rc == DG_OK; ++i) {
+      e = cudaMemcpyAsync(&P->h_flags[i], P->M[i].S->flag, sizeof(int), cudaMemcpyDeviceToHost, P->cs);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&P->h_sol[(size_t)i * 256], P->M[i].S->solve_out, 4 * P->M[i].nsolve * sizeof(double),
+                            cudaMemcpyDeviceToHost, P->cs);
+      if (e != cudaSuccess) rc = cuda_fail(e, "batch plan capture");
+    }
+    if (rc == DG_OK) {
+      e = cudaMemcpyAsync(&P->h_flags[n], err, sizeof(int), cudaMemcpyDeviceToHost, P->cs);
+      if (e != cudaSuccess) rc = cuda_fail(e, "batch plan capture");
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(P->cs, &g);  // ends the capture whether or not the phases succeeded
+    P->graph = g;
+    if (rc == DG_OK && e != cudaSuccess) rc = cuda_fail(e, "batch plan capture");
+  } else {
+    rc = cuda_fail(e, "batch plan capture");
+  }
+  ctx->arena = nullptr;
+  ctx->prof = prof;
+  P->kernels = ctx->launches - launches0;
+  ctx->launches = launches0;
+  if (rc != DG_OK) return bail(rc);
+  e = cudaMemcpy(P->arena.dev, P->arena.host.data(), P->arena.used, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "batch plan instantiation"));
+  *out = P;
+  return DG_OK;
+}
+
+extern "C" int dg_batch_plan_step(dg_batch_plan* P, dg_step_stats* stats, int* statuses, void* stream) {
+  if (!P) return fail(DG_EINVAL, "null plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope step_scope(P->ctx, DG_PROF_STEP, s);
+  DG_CUDA(cudaGraphLaunch(P->exec, s));
+  count_launches(P->ctx, (int)P->kernels);
+  DG_CUDA(cudaStreamSynchronize(s));
+  for (auto& mm : P->M) mm.st = dg_step_stats{};
+  return finish_batch(P->M, P->h_flags, P->h_sol, P->h_flags[P->n], stats, statuses);
 }

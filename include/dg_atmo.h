@@ -62,7 +62,7 @@ typedef enum {
 } dg_status;
 
 typedef enum { DG_FP64 = 0, DG_FP32 = 1 } dg_precision;
-typedef enum { DG_KRYLOV_GMRES = 0, DG_KRYLOV_CG = 1 } dg_krylov;
+typedef enum { DG_KRYLOV_GMRES = 0, DG_KRYLOV_CG = 1, DG_KRYLOV_GMRES_CGS2 = 2 } dg_krylov;
 typedef enum { DG_TERMS_FULL = 0, DG_TERMS_IMEX_EXPLICIT = 1 } dg_terms;
 typedef enum { DG_HILL_NONE = 0, DG_HILL_GAUSS = 1, DG_HILL_BELL = 2, DG_HILL_PARABOLA = 3 } dg_hill_kind;
 typedef enum { DG_ATM_NONE = 0, DG_ATM_ISOTHERMAL = 1, DG_ATM_STRATIFIED = 2 } dg_atm_kind;
@@ -99,11 +99,14 @@ int dg_profile_enable(dg_ctx* ctx, int on);
 int dg_profile_read(dg_ctx* ctx, double* ms, long long* counts);
 int dg_profile_reset(dg_ctx* ctx);
 /* Nanoseconds spent in each phase of the fused GMRES solves while profiling
- * was on, as seen by block 0 between grid barriers (so each phase includes the
- * wait for the slowest block), into ns[16]: 0 gradient faces, 1 gradient
- * cells, 2 divergence faces, 3 divergence cells, 4 Gram-Schmidt dots,
- * 5 basis update + Givens, 6 second Gram-Schmidt pass, 7 FP64 residual,
- * 8 solution update; ns[15] = GMRES iterations.  Synchronises the device. */
+ * was on, as seen by block 0 (a phase that ends at a grid barrier includes the
+ * wait for the slowest block), into ns[16]: 1 gradient (one cell pass with its
+ * face terms), 3 divergence (the same), 4 wait at the barrier after the
+ * Gram-Schmidt dots, 5 wait at the barrier after the basis update, 6 second
+ * Gram-Schmidt pass (classical form), 7 FP64 residual, 8 solution update,
+ * 9 Gram-Schmidt dots (work), 10 sums of the block partials, 11 Hessenberg
+ * column and Givens rotation, 12 update coefficients, 13 basis update (work);
+ * ns[14] = second passes, ns[15] = GMRES iterations.  Synchronises the device. */
 int dg_profile_read_gmres_phases(dg_ctx* ctx, double* ns);
 /* Number of CUDA kernels the library has launched through this context so far. */
 int dg_launch_count(const dg_ctx* ctx, long long* out);
@@ -235,10 +238,16 @@ typedef struct {
                        /*    kernel; 0: one launch per Krylov kernel; -1       */
                        /*    (default): autotuned per mesh and precision by     */
                        /*    timing both forms on the first solve               */
-  int krylov;          /* DG_KRYLOV_GMRES (Sec. 3.2, default) or DG_KRYLOV_CG:  */
-                       /*    conjugate gradients in the w J inner product, in   */
-                       /*    which the Helmholtz operator is self-adjoint and   */
-                       /*    positive (persistent form only)                    */
+  int krylov;          /* DG_KRYLOV_GMRES (Sec. 3.2, default): persistent form  */
+                       /*    with one reduction per Arnoldi step (second        */
+                       /*    Gram-Schmidt pass delayed into the next step);     */
+                       /*    DG_KRYLOV_GMRES_CGS2: classical Gram-Schmidt twice */
+                       /*    per step (two or three reductions);               */
+                       /*    DG_KRYLOV_CG: conjugate gradients in the w J inner */
+                       /*    product, in which the Helmholtz operator is        */
+                       /*    self-adjoint and positive (persistent form only).  */
+                       /*    The one-launch-per-kernel form (fused = 0) runs    */
+                       /*    GMRES with classical Gram-Schmidt twice.           */
 } dg_solver_opts;
 
 typedef struct {

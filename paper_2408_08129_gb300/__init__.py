@@ -10,6 +10,7 @@ from .api import (  # noqa: F401
     DG_FP64,
     DG_KRYLOV_CG,
     DG_KRYLOV_GMRES,
+    DG_KRYLOV_GMRES_CGS2,
     DG_TERMS_FULL,
     DG_TERMS_IMEX_EXPLICIT,
     BatchPlan,

@@ -17,7 +17,7 @@ DG_STATUS = {
     -5: "DG_ENONFINITE", -6: "DG_EUNBALANCED", -7: "DG_EBUDGET", -8: "DG_ETIMEOUT",
 }
 DG_FP64, DG_FP32 = 0, 1
-DG_KRYLOV_GMRES, DG_KRYLOV_CG = 0, 1
+DG_KRYLOV_GMRES, DG_KRYLOV_CG, DG_KRYLOV_GMRES_CGS2 = 0, 1, 2
 DG_TERMS_FULL, DG_TERMS_IMEX_EXPLICIT = 0, 1
 DG_HILL = {"none": 0, "gauss": 1, "bell": 2, "parabola": 3}
 DG_ATM = {"none": 0, "isothermal": 1, "stratified": 2}

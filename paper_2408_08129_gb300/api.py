@@ -12,7 +12,7 @@ import torch
 
 from . import _binding as B
 from ._binding import (  # noqa: F401
-    DG_ATM, DG_FP32, DG_FP64, DG_HILL, DG_INIT, DG_KRYLOV_CG, DG_KRYLOV_GMRES, DG_TERMS_FULL,
+    DG_ATM, DG_FP32, DG_FP64, DG_HILL, DG_INIT, DG_KRYLOV_CG, DG_KRYLOV_GMRES, DG_KRYLOV_GMRES_CGS2, DG_TERMS_FULL,
     DG_TERMS_IMEX_EXPLICIT, DGError, check, lib,
 )
 
@@ -177,14 +177,15 @@ def dg_profile_read(ctx):
     return {name: {"ms": float(ms[i]), "count": int(n[i])} for i, name in PROF_CATEGORIES.items()}
 
 
-GMRES_PHASES = ["grad_faces", "grad_cells", "div_faces", "div_cells", "gs_dots", "basis_update_givens",
-                "gs_second_pass", "fp64_residual", "solution_update"]
+GMRES_PHASES = {1: "gradient", 3: "divergence", 4: "gs_dots_barrier", 5: "basis_update_barrier",
+                6: "gs_second_pass", 7: "fp64_residual", 8: "solution_update", 9: "gs_dots_work",
+                10: "partial_sums", 11: "givens", 12: "coefficients", 13: "basis_update_work"}
 
 
 def dg_profile_read_gmres_phases(ctx):
     ns = np.zeros(16)
     check(lib.dg_profile_read_gmres_phases(ctx.handle, ns.ctypes.data), "dg_profile_read_gmres_phases")
-    out = {name: ns[i] / 1e6 for i, name in enumerate(GMRES_PHASES)}  # ms
+    out = {name: ns[i] / 1e6 for i, name in GMRES_PHASES.items()}  # ms
     out["iterations"] = int(ns[15])
     out["second_passes"] = int(ns[14])
     return out

@@ -31,6 +31,8 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "k_implicit.cuh"
 
 namespace dg {
@@ -46,7 +48,6 @@ struct GmresPArgs {
   TK* Q;                  // [(m+1)][n] Krylov basis (q_0 unnormalised, scale sigma_0)
   TK* w;                  // [n] Arnoldi mat-vec output
   double* w64;            // [n] FP64 residual mat-vec output (may alias w when TK = double)
-  double* Gh;             // face scratch (dim*nf*NF doubles), reused as TK
   double* gv;             // [dim][n] gradient scratch (doubles), reused as TK
   double* partial;        // >= 2 x (CTAs of the solve) doubles
   double* out;            // [4]: iterations, relative residual, converged (0/1), ||b||
@@ -57,12 +58,13 @@ struct GmresPArgs {
   int m;
   int max_iters;
   int64_t n;
-  int method;  // 0: GMRES(m); 1: conjugate gradients in the M inner product (needs m >= 2)
+  int method;  // 0: GMRES(m), one reduction per step; 1: conjugate gradients in the M inner
+              // product (needs m >= 2); 2: GMRES(m) with classical Gram-Schmidt twice per step
 };
 
 enum GmresPhase {
-  PH_GRAD_FACE = 0, PH_GRAD_CELL, PH_DIV_FACE, PH_DIV_CELL, PH_DOTS, PH_UPDATE, PH_REORTH, PH_RESIDUAL,
-  PH_SOLUTION, PH_ITERS = 15
+  PH_GRAD_CELL = 1, PH_DIV_CELL = 3, PH_DOTS, PH_UPDATE, PH_REORTH, PH_RESIDUAL,
+  PH_SOLUTION, PH_DOTS_WORK = 9, PH_SUMS, PH_GIVENS, PH_COEFS, PH_LINCOMB, PH_ITERS = 15
 };
 
 struct PhaseClock {
@@ -148,7 +150,8 @@ __device__ __forceinline__ double block_sum(double v, double* sred) {
   return r;
 }
 
-// copy cnt (<= 512) global partial sums into shared memory with all threads
+// copy cnt global partial sums (no more than the staging area holds) into
+// shared memory with all threads
 // (one parallel round trip instead of a serial chain of loads)
 __device__ __forceinline__ void stage_partials(const double* partial, int cnt, double* spart) {
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) spart[i] = partial[i];
@@ -169,27 +172,20 @@ __device__ __forceinline__ double block_sum_k(TK v, double* sred) {
   return r;
 }
 
-// out = scale * (ident p/(gamma-1) - alpha div(h grad p)) (four phases, four grid barriers)
+// out = scale * (ident p/(gamma-1) - alpha div(h grad p)) (two phases, two grid barriers;
+// the face terms are computed inside the cell passes)
 template <int DIM, int DEG, typename T, class Sync>
 __device__ __forceinline__ void pmatvec(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p, T scale,
-                                        T* out, T* Gh, T* gv, Sync& sg, T* scell, const T* sD, const T* sDw,
-                                        const T* sIt, PhaseClock& pc) {
+                                        T* out, T* gv, Sync& sg, T* scell, T* sJ, const T* sD, const T* sDw,
+                                        const T* sII, PhaseClock& pc) {
   using S = Shape<DIM, DEG>;
-  const int64_t nfi = (int64_t)(mv.nconf + mv.nsub) * S::NF;
-  const int64_t stride = (int64_t)sg.size * blockDim.x;
-  const int64_t tid = (int64_t)sg.rank * blockDim.x + threadIdx.x;
   const int64_t nb = (mv.n_cells + S::CPB - 1) / S::CPB;
-  for (int64_t t = tid; t < nfi; t += stride) grad_face_item<DIM, DEG, T>(mv, p, Gh, t);
-  sg.sync();
-  pc.mark(PH_GRAD_FACE);
-  for (int64_t bt = sg.rank; bt < nb; bt += sg.size) grad_cell_batch<DIM, DEG, T>(mv, p, h, Gh, gv, bt, scell, sD, sIt);
+  for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
+    grad_cell_batch<DIM, DEG, T>(mv, p, h, gv, bt, scell, sJ, sD, sII);
   sg.sync();
   pc.mark(PH_GRAD_CELL);
-  for (int64_t t = tid; t < nfi; t += stride) div_face_item<DIM, DEG, T>(mv, gv, Gh, t);
-  sg.sync();
-  pc.mark(PH_DIV_FACE);
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-    div_cell_batch<DIM, DEG, T, true>(mv, gv, Gh, p, alpha, scale, ident, out, bt, scell, sDw, sIt);
+    div_cell_batch<DIM, DEG, T, true>(mv, gv, p, alpha, scale, ident, out, bt, scell, sJ, sDw, sII);
   sg.sync();
   pc.mark(PH_DIV_CELL);
 }
@@ -241,9 +237,388 @@ __device__ __forceinline__ TK lincomb(const TK* __restrict__ Q, int64_t n, int64
   return acc;
 }
 
+// partial[2 (j C + c) + {0, 1}] = sum over chunk c of V_j . u and V_j . w for
+// j < nv, where V_j = Q_j and u = Q_{nv-1} (so the last pair is u.u, u.w)
+template <typename TK>
+__device__ __forceinline__ void pdots2(const TK* Q, int64_t n, const TK* w, int nv, int C, double* partial,
+                                       double* sred, int rank, int size) {
+  const TK* u = Q + (int64_t)(nv - 1) * n;
+  const int64_t chunk = (n + C - 1) / C;
+  for (int it = rank; it < nv * C; it += size) {
+    const int j = it / C, c = it % C;
+    const int64_t lo = (int64_t)c * chunk;
+    const int64_t hi = lo + chunk < n ? lo + chunk : n;
+    const TK* q = Q + (int64_t)j * n;
+    // four nodes per thread per round: twelve loads in flight
+    TK su[4] = {TK(0), TK(0), TK(0), TK(0)}, sw[4] = {TK(0), TK(0), TK(0), TK(0)};
+    const int64_t bd = blockDim.x;
+    int64_t i = lo + threadIdx.x;
+    for (; i + 3 * bd < hi; i += 4 * bd) {
+      TK qv[4], uv[4], wv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        qv[r] = q[i + r * bd];
+        uv[r] = u[i + r * bd];
+        wv[r] = w[i + r * bd];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        su[r] += qv[r] * uv[r];
+        sw[r] += qv[r] * wv[r];
+      }
+    }
+    for (; i < hi; i += bd) {
+      const TK qv = q[i];
+      su[0] += qv * u[i];
+      sw[0] += qv * w[i];
+    }
+    const double du = block_sum_k<TK>((su[0] + su[1]) + (su[2] + su[3]), sred);
+    const double dw = block_sum_k<TK>((sw[0] + sw[1]) + (sw[2] + sw[3]), sred);
+    if (threadIdx.x == 0) {
+      partial[2 * it] = du;
+      partial[2 * it + 1] = dw;
+    }
+  }
+}
+
+// o1 = sum_{j<cnt} c1[j] Q_j[i], o2 = sum_{j<cnt} c2[j] Q_j[i] in TK, reading
+// each basis vector once with eight loads in flight
+template <typename TK>
+__device__ __forceinline__ void lincomb2(const TK* __restrict__ Q, int64_t n, int64_t i,
+                                         const double* __restrict__ c1, const double* __restrict__ c2, int cnt,
+                                         TK& o1, TK& o2) {
+  TK a1 = TK(0), a2 = TK(0);
+  int j = 0;
+  for (; j + 8 <= cnt; j += 8) {
+    TK q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) q[u] = Q[(int64_t)(j + u) * n + i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a1 += (TK)c1[j + u] * q[u];
+      a2 += (TK)c2[j + u] * q[u];
+    }
+  }
+  for (; j < cnt; ++j) {
+    const TK q = Q[(int64_t)j * n + i];
+    a1 += (TK)c1[j] * q;
+    a2 += (TK)c2[j] * q;
+  }
+  o1 = a1;
+  o2 = a2;
+}
+
+// 1D tables of the mesh's degree into shared memory, FP64 and TK copies:
+// D, Dw, then I (2 N^2) followed by It (2 N^2)
+template <int DIM, int DEG, typename TK>
+__device__ __forceinline__ void load_tables(const GmresPArgs<TK>& a, double* sD64, double* sDw64, double* sII64,
+                                            TK* sDk, TK* sDwk, TK* sIIk) {
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N;
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
+    sD64[q] = a.mv64.tab[S::T_D + q];
+    sDw64[q] = a.mv64.tab[S::T_DW + q];
+    sDk[q] = a.mvk.tab[S::T_D + q];
+    sDwk[q] = a.mvk.tab[S::T_DW + q];
+  }
+  for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) {
+    sII64[q] = a.mv64.tab[S::T_I + q];
+    sIIk[q] = a.mvk.tab[S::T_I + q];
+  }
+  __syncthreads();
+}
+
+// Restarted GMRES(m) with one global reduction per Arnoldi step: classical
+// Gram-Schmidt with the second (re-orthogonalisation) pass of each vector
+// delayed into the next step, in the manner of the low-synchronisation DCGS2
+// Arnoldi of Swirydowicz et al. (2020) and Bielich et al. (2022); the
+// derivation below is our own.  Step k has u_k = B q_{k-1} - Q_k hf (one
+// Gram-Schmidt pass, not normalised; u_0 = r) in basis slot k and
+//   1. v = B u_k                                   (mat-vec, two phases)
+//   2. a = Q_k^T u_k, b = Q_k^T v, u_k.u_k, u_k.v   (ONE reduction)
+//   3. rho^2 = u_k.u_k - |a|^2, q_k = (u_k - Q_k a)/rho;  column k-1 of H is
+//      hf + a with subdiagonal rho (Givens update, residual estimate);
+//      B q_k = (v - Q_{k+1} z)/rho with z = H a (Arnoldi relation), so the
+//      first pass of column k is hf'_i = (b_i - z_i)/rho (i < k),
+//      hf'_k = ((u_k.v - a.b)/rho - z_k)/rho, and
+//      u_{k+1} = v/rho - c u_k - Q_k d,  c = (z_k/rho + hf'_k)/rho,
+//      d = z/rho + hf' - c a                          (no further reduction)
+//   4. one pass writes q_k and u_{k+1}.
+// Four grid barriers per step (two in the mat-vec), two passes over the basis.
+// Arnoldi runs on B = A - I/(gamma-1) (same Krylov space; the Hessenberg of A
+// adds 1/(gamma-1) on the diagonal).  Each cycle ends one mat-vec after its
+// last column (the step that completes it).  TK = float: FP32 basis and
+// mat-vecs, FP64 residual recomputed at every restart (iterative refinement).
 template <int DIM, int DEG, typename TK, class Sync>
 __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw,
                                            bool record) {
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N;
+  const int m = a.m;
+  double* Hb = (double*)smem_raw;    // [(m+1)*m] Hessenberg of B, column j at Hb[j*(m+1)]
+  double* R = Hb + (m + 1) * m;      // [(m+1)*m] rotated Hessenberg of A
+  double* cs = R + (m + 1) * m;      // [m]
+  double* sn = cs + m;               // [m]
+  double* gg = sn + m;               // [m+1]
+  double* y = gg + (m + 1);          // [m]
+  double* av = y + m;                // [m+1] a (second pass), then u.u in [k]; solution weights at the end
+  double* bv = av + (m + 1);         // [m+1] b, then u.v in [k]
+  double* hf = bv + (m + 1);         // [m+1] first-pass coefficients of the newest column
+  double* zc = hf + (m + 1);         // [m+1] z = H a
+  double* dv = zc + (m + 1);         // [m+1] d
+  double* sred = dv + (m + 1);       // [32]
+  double* sc = sred + 32;            // [8]: 0 ||b||, 1 resid, 2 beta, 3 rho, 4 c
+  double* spart = sc + 8;            // [1024] staged block partials
+  int* sflag = (int*)(spart + 1024);  // [4]: 0 stop cycle, 1 converged
+  double* t64 = (double*)(sflag + 4);  // FP64 tables D, Dw, I|It
+  double* sD64 = t64;
+  double* sDw64 = sD64 + N * N;
+  double* sII64 = sDw64 + N * N;
+  double* scell64 = sII64 + 4 * N * N;      // cell tile, CPB*NC doubles (reused as TK)
+  double* sJ64 = scell64 + S::CPB * S::NC;  // coarse-pass buffer (reused as TK)
+  TK* tk = (TK*)(sJ64 + coarse_buffer<DIM, DEG, DIM>());
+  TK* sDk = tk;
+  TK* sDwk = sDk + N * N;
+  TK* sIIk = sDwk + N * N;
+  TK* scellk = (TK*)scell64;
+  TK* sJk = (TK*)sJ64;
+  load_tables<DIM, DEG, TK>(a, sD64, sDw64, sII64, sDk, sDwk, sIIk);
+  PhaseClock pc{record ? a.phase : nullptr, PhaseClock::now()};
+
+  const int64_t n = a.n;
+  const int G = sg.size;
+  const int64_t tid = (int64_t)sg.rank * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)G * blockDim.x;
+  const int64_t chunk1 = (n + G - 1) / G;
+  const bool mixed = sizeof(TK) != sizeof(double);
+  const double shift = 1.0 / (kGamma - 1.0);
+  TK* gvk = (TK*)a.gv;
+
+  // ||b||
+  {
+    const int64_t lo = (int64_t)sg.rank * chunk1;
+    const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += a.b[i] * a.b[i];
+    const double s = block_sum(acc, sred);
+    if (threadIdx.x == 0) a.partial[sg.rank] = s;
+  }
+  sg.sync();
+  stage_partials(a.partial, G, spart);
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < G; ++i) s += spart[i];
+    sc[0] = sqrt(s);
+  }
+  __syncthreads();
+  const double bn = sc[0];
+  if (bn == 0.0) {
+    for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
+    if (sg.rank == 0 && threadIdx.x == 0) {
+      a.out[0] = 0;
+      a.out[1] = 0;
+      a.out[2] = 1;
+      a.out[3] = 0;
+    }
+    return;
+  }
+  sg.sync();  // partial reused below
+
+  int total = 0;
+  double rel = 1.0;
+  bool converged = false;
+  while (true) {
+    // r = b - A x with the FP64 operator -> u_0 in slot 0, beta
+    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.gv, sg, scell64, sJ64, sD64,
+                                    sDw64, sII64, pc);
+    {
+      const int64_t lo = (int64_t)sg.rank * chunk1;
+      const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
+      double acc = 0.0;
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double r = a.b[i] - a.w64[i];
+        a.Q[i] = (TK)r;
+        acc += r * r;
+      }
+      const double s = block_sum(acc, sred);
+      if (threadIdx.x == 0) a.partial[sg.rank] = s;
+    }
+    sg.sync();
+    pc.mark(PH_RESIDUAL);
+    stage_partials(a.partial, G, spart);
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < G; ++i) s += spart[i];
+      const double beta = sqrt(s);
+      sc[2] = beta;
+      sflag[1] = (beta <= a.tol * bn) ? 1 : 0;
+      sflag[0] = 0;
+    }
+    __syncthreads();
+    rel = sc[2] / bn;
+    if (sg.failed()) break;
+    if (sflag[1]) {
+      converged = true;
+      break;
+    }
+    if (total >= a.max_iters) break;
+    const double cycle_floor = fmax(a.tol * bn, (mixed ? a.inner_tol : 0.0) * sc[2]);
+    int kd = 0;
+    for (int k = 0; k <= m; ++k) {
+      TK* uk = a.Q + (int64_t)k * n;
+      // 1. v = B u_k
+      pmatvec<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(0), uk, TK(1), a.w, gvk, sg, scellk, sJk, sDk, sDwk,
+                                  sIIk, pc);
+      // 2. a = Q_k^T u_k, b = Q_k^T v, u.u, u.v: one reduction
+      const int nv = k + 1;
+      int C = G / nv;
+      if (C < 1) C = 1;
+      pdots2<TK>(a.Q, n, a.w, nv, C, a.partial, sred, sg.rank, sg.size);
+      pc.mark(PH_DOTS_WORK);
+      sg.sync();
+      pc.mark(PH_DOTS);
+      if (sg.failed()) break;
+      stage_partials(a.partial, 2 * nv * C, spart);
+      if (threadIdx.x < nv) {
+        double su = 0.0, sw = 0.0;
+        for (int c = 0; c < C; ++c) {
+          su += spart[2 * (threadIdx.x * C + c)];
+          sw += spart[2 * (threadIdx.x * C + c) + 1];
+        }
+        av[threadIdx.x] = su;
+        bv[threadIdx.x] = sw;
+      }
+      __syncthreads();
+      pc.mark(PH_SUMS);
+      // 3. rho, column k-1 with its Givens rotation, stop test
+      if (threadIdx.x == 0) {
+        double ss = 0.0;
+        for (int j = 0; j < k; ++j) ss += av[j] * av[j];
+        const double uu = av[k];
+        const double rho2 = uu - ss;
+        // breakdown (u_k in the span of Q_k to working precision) ends the cycle
+        const double rho = (rho2 > 1e-24 * uu && rho2 > 0.0) ? sqrt(rho2) : 0.0;
+        sc[3] = rho;
+        int stop = 0;
+        if (k == 0) {
+          gg[0] = rho;
+          for (int j = 1; j <= m; ++j) gg[j] = 0.0;
+          if (rho == 0.0) stop = 1;
+        } else {
+          double* hb = Hb + (int64_t)(k - 1) * (m + 1);
+          double* col = R + (int64_t)(k - 1) * (m + 1);
+          for (int j = 0; j < k; ++j) {
+            hb[j] = hf[j] + av[j];
+            col[j] = hb[j];
+          }
+          hb[k] = rho;
+          col[k - 1] += shift;
+          col[k] = rho;
+          for (int j = 0; j < k - 1; ++j) {
+            const double t = cs[j] * col[j] + sn[j] * col[j + 1];
+            col[j + 1] = -sn[j] * col[j] + cs[j] * col[j + 1];
+            col[j] = t;
+          }
+          const double den = hypot(col[k - 1], col[k]);
+          const double c = den > 0.0 ? col[k - 1] / den : 1.0;
+          const double sgn = den > 0.0 ? col[k] / den : 0.0;
+          cs[k - 1] = c;
+          sn[k - 1] = sgn;
+          col[k - 1] = den;
+          col[k] = 0.0;
+          gg[k] = -sgn * gg[k - 1];
+          gg[k - 1] = c * gg[k - 1];
+          const double resid = fabs(gg[k]);
+          sc[1] = resid;
+          sflag[1] = resid <= a.tol * bn ? 1 : 0;
+          stop = (resid <= cycle_floor || rho == 0.0 || total + 1 >= a.max_iters || k == m) ? 1 : 0;
+        }
+        sflag[0] = stop;
+      }
+      __syncthreads();
+      pc.mark(PH_GIVENS);
+      if (k > 0) {
+        ++total;
+        rel = sc[1] / bn;
+      }
+      kd = k;
+      if (sflag[0]) break;
+      const double rho = sc[3];
+      // z = H a over the completed columns 0..k-1 (z_k = rho a_{k-1})
+      if (threadIdx.x <= k) {
+        const int i = threadIdx.x;
+        double z = 0.0;
+        for (int j = (i > 0 ? i - 1 : 0); j < k; ++j) z += Hb[(int64_t)j * (m + 1) + i] * av[j];
+        zc[i] = z;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double ab = 0.0;
+        for (int j = 0; j < k; ++j) ab += av[j] * bv[j];
+        const double hk = ((bv[k] - ab) / rho - zc[k]) / rho;
+        hf[k] = hk;
+        sc[4] = (zc[k] / rho + hk) / rho;
+      }
+      __syncthreads();
+      const double cu = sc[4];
+      if (threadIdx.x < k) {
+        const int i = threadIdx.x;
+        const double h = (bv[i] - zc[i]) / rho;
+        hf[i] = h;
+        dv[i] = zc[i] / rho + h - cu * av[i];
+      }
+      __syncthreads();
+      pc.mark(PH_COEFS);
+      // 4. q_k = (u_k - Q_k a)/rho and u_{k+1} = v/rho - c u_k - Q_k d, one pass
+      {
+        const TK irho = (TK)(1.0 / rho), cuk = (TK)cu;
+        TK* un = a.Q + (int64_t)(k + 1) * n;
+        for (int64_t i = tid; i < n; i += gstride) {
+          const TK u = uk[i], v = a.w[i];
+          TK sa, sd;
+          lincomb2(a.Q, n, i, av, dv, k, sa, sd);
+          uk[i] = (u - sa) * irho;
+          un[i] = v * irho - cuk * u - sd;
+        }
+      }
+      pc.mark(PH_LINCOMB);
+      sg.sync();
+      pc.mark(PH_UPDATE);
+      if (sg.failed()) break;
+    }
+    // x += sum_j y_j q_j over the kd completed columns
+    if (threadIdx.x == 0) {
+      for (int i = kd - 1; i >= 0; --i) {
+        double s = gg[i];
+        for (int j = i + 1; j < kd; ++j) s -= R[(int64_t)j * (m + 1) + i] * y[j];
+        y[i] = s / R[(int64_t)i * (m + 1) + i];
+      }
+      for (int j = 0; j < kd; ++j) av[j] = y[j];
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < n; i += gstride) a.x[i] += (double)lincomb(a.Q, n, i, av, kd);
+    sg.sync();
+    pc.mark(PH_SOLUTION);
+    // plain FP64 GMRES trusts its residual estimate; the mixed form re-checks
+    // with the FP64 residual at the next restart
+    if (!mixed && sflag[1]) {
+      converged = true;
+      break;
+    }
+    if (kd == 0 || total >= a.max_iters || sg.failed()) break;  // kd = 0: no progress possible
+  }
+  if (sg.rank == 0 && threadIdx.x == 0) {
+    a.out[0] = total;
+    a.out[1] = rel;
+    a.out[2] = (converged && !sg.failed()) ? 1.0 : 0.0;
+    a.out[3] = bn;
+    if (pc.acc) a.phase[PH_ITERS] += (unsigned long long)total;
+  }
+}
+
+template <int DIM, int DEG, typename TK, class Sync>
+__device__ __forceinline__ void gmres_cgs2_body(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw,
+                                                bool record) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N;
   const int m = a.m;
@@ -260,28 +635,19 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
   double* sc = sred + 32;             // [8]: 0 ||b||, 1 resid, 2 beta, 3 1/hn, 4 ||w||^2 after
   double* spart = sc + 8;             // [512] staged block partials
   int* sflag = (int*)(spart + 512);   // [4]: 0 stop cycle, 1 converged, 2 reorth
-  double* t64 = (double*)(sflag + 4);  // FP64 tables D, Dw, It
+  double* t64 = (double*)(sflag + 4);  // FP64 tables D, Dw, I|It
   double* sD64 = t64;
   double* sDw64 = sD64 + N * N;
-  double* sIt64 = sDw64 + N * N;
-  double* scell64 = sIt64 + 2 * N * N;  // cell tile, CPB*NC doubles (reused as TK)
-  TK* tk = (TK*)(scell64 + S::CPB * S::NC);
+  double* sII64 = sDw64 + N * N;
+  double* scell64 = sII64 + 4 * N * N;  // cell tile, CPB*NC doubles (reused as TK)
+  double* sJ64 = scell64 + S::CPB * S::NC;  // coarse-pass buffer (reused as TK)
+  TK* tk = (TK*)(sJ64 + coarse_buffer<DIM, DEG, DIM>());
   TK* sDk = tk;
   TK* sDwk = sDk + N * N;
-  TK* sItk = sDwk + N * N;
+  TK* sIIk = sDwk + N * N;
   TK* scellk = (TK*)scell64;
-
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
-    sD64[q] = a.mv64.tab[S::T_D + q];
-    sDw64[q] = a.mv64.tab[S::T_DW + q];
-    sDk[q] = a.mvk.tab[S::T_D + q];
-    sDwk[q] = a.mvk.tab[S::T_DW + q];
-  }
-  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) {
-    sIt64[q] = a.mv64.tab[S::T_IT + q];
-    sItk[q] = a.mvk.tab[S::T_IT + q];
-  }
-  __syncthreads();
+  TK* sJk = (TK*)sJ64;
+  load_tables<DIM, DEG, TK>(a, sD64, sDw64, sII64, sDk, sDwk, sIIk);
   PhaseClock pc{record ? a.phase : nullptr, PhaseClock::now()};
 
   const int64_t n = a.n;
@@ -290,7 +656,6 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
   const int64_t gstride = (int64_t)G * blockDim.x;
   const int64_t chunk1 = (n + G - 1) / G;
   const bool mixed = sizeof(TK) != sizeof(double);
-  TK* Ghk = (TK*)a.Gh;
   TK* gvk = (TK*)a.gv;
 
   // ||b||
@@ -328,8 +693,8 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
   bool converged = false;
   while (true) {
     // r = b - A x with the FP64 operator -> q_0 (unnormalised), beta
-    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.Gh, a.gv, sg, scell64, sD64,
-                                    sDw64, sIt64, pc);
+    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.gv, sg, scell64, sJ64, sD64,
+                                    sDw64, sII64, pc);
     {
       const int64_t lo = (int64_t)sg.rank * chunk1;
       const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
@@ -371,8 +736,8 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
       const TK* qk = a.Q + (int64_t)k * n;
       // Arnoldi on B = A - I/(gamma-1): same Krylov space, Hessenberg of A = that of B
       // plus 1/(gamma-1) on the diagonal; w = B q_k has no large component along q_k
-      pmatvec<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(0), qk, (TK)sigma[k], a.w, Ghk, gvk, sg, scellk,
-                                  sDk, sDwk, sItk, pc);
+      pmatvec<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(0), qk, (TK)sigma[k], a.w, gvk, sg, scellk, sJk,
+                                  sDk, sDwk, sIIk, pc);
       // h_j = q_j . w (j <= k) and ||w||^2, one pass
       const int nv = k + 2;
       int C = G / nv;
@@ -519,23 +884,15 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
   double* spart = sc + 16;           // [3*512]
   double* sD64 = spart + 3 * 512;
   double* sDw64 = sD64 + N * N;
-  double* sIt64 = sDw64 + N * N;
-  double* scell64 = sIt64 + 2 * N * N;
-  TK* sDk = (TK*)(scell64 + S::CPB * S::NC);
+  double* sII64 = sDw64 + N * N;
+  double* scell64 = sII64 + 4 * N * N;
+  double* sJ64 = scell64 + S::CPB * S::NC;
+  TK* sDk = (TK*)(sJ64 + coarse_buffer<DIM, DEG, DIM>());
   TK* sDwk = sDk + N * N;
-  TK* sItk = sDwk + N * N;
+  TK* sIIk = sDwk + N * N;
   TK* scellk = (TK*)scell64;
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
-    sD64[q] = a.mv64.tab[S::T_D + q];
-    sDw64[q] = a.mv64.tab[S::T_DW + q];
-    sDk[q] = a.mvk.tab[S::T_D + q];
-    sDwk[q] = a.mvk.tab[S::T_DW + q];
-  }
-  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) {
-    sIt64[q] = a.mv64.tab[S::T_IT + q];
-    sItk[q] = a.mvk.tab[S::T_IT + q];
-  }
-  __syncthreads();
+  TK* sJk = (TK*)sJ64;
+  load_tables<DIM, DEG, TK>(a, sD64, sDw64, sII64, sDk, sDwk, sIIk);
   PhaseClock pc{record ? a.phase : nullptr, PhaseClock::now()};
   const int64_t n = a.n;
   const int G = sg.size;
@@ -550,7 +907,6 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
   TK* s = a.Q + 2 * n;
   TK* w = a.w;
   const TK* wJ = a.mvk.wJ;
-  TK* Ghk = (TK*)a.Gh;
   TK* gvk = (TK*)a.gv;
 
   {
@@ -584,8 +940,8 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
   bool converged = false;
   while (true) {
     // true residual with the FP64 operator
-    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.Gh, a.gv, sg, scell64, sD64,
-                                    sDw64, sIt64, pc);
+    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.gv, sg, scell64, sJ64, sD64,
+                                    sDw64, sII64, pc);
     {
       double acc = 0.0;
       for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
@@ -617,8 +973,8 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
     double alpha = 1.0, gamma = 1.0;
     bool first = true;
     for (;;) {
-      pmatvec<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(1), r, TK(1), w, Ghk, gvk, sg, scellk, sDk, sDwk,
-                                  sItk, pc);
+      pmatvec<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(1), r, TK(1), w, gvk, sg, scellk, sJk, sDk, sDwk,
+                                  sIIk, pc);
       {
         TK g0 = TK(0), d0 = TK(0), e0 = TK(0);
         for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
@@ -698,6 +1054,8 @@ __global__ void __launch_bounds__(256, 2) gmres_persistent_kernel(GmresPArgs<TK>
   GridSync sg;
   if (a.method == 1)
     cg_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
+  else if (a.method == 2)
+    gmres_cgs2_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
   else
     gmres_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
 }
@@ -715,7 +1073,7 @@ struct BatchMap {
 };
 
 template <int DIM, int DEG, typename TK>
-__global__ void __launch_bounds__(256, 3) gmres_batched_kernel(const GmresPArgs<TK>* __restrict__ args, BatchMap map) {
+__global__ void __launch_bounds__(256, 2) gmres_batched_kernel(const GmresPArgs<TK>* __restrict__ args, BatchMap map) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sfail;
   const int mem = map.cta_member[blockIdx.x];
@@ -726,6 +1084,8 @@ __global__ void __launch_bounds__(256, 3) gmres_batched_kernel(const GmresPArgs<
   const GmresPArgs<TK> a = args[mem];
   if (a.method == 1)
     cg_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
+  else if (a.method == 2)
+    gmres_cgs2_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
   else
     gmres_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
 }
@@ -736,10 +1096,13 @@ inline size_t gmres_smem_bytes(int m) {
   using S = Shape<DIM, DEG>;
   const size_t dbl = (size_t)(m + 1) + 2 * (size_t)(m + 2) + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m +
                      (m + 1) + 32 + 8 + 512;
-  const size_t tabs = (size_t)(4 * N * N + S::CPB * S::NC) * sizeof(double) + (size_t)(4 * N * N) * sizeof(TK);
+  const size_t tabs = (size_t)(6 * N * N + S::CPB * S::NC + coarse_buffer<DIM, DEG, DIM>()) * sizeof(double) +
+                      (size_t)(6 * N * N) * sizeof(TK);
   const size_t gm = dbl * sizeof(double) + 4 * sizeof(int) + tabs + 64;
+  const size_t d1 = 2 * (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 5 * (size_t)(m + 1) + 32 + 8 + 1024;
+  const size_t g1 = d1 * sizeof(double) + 4 * sizeof(int) + tabs + 64;
   const size_t cg = (size_t)(32 + 16 + 3 * 512) * sizeof(double) + tabs + 64;
-  return gm > cg ? gm : cg;
+  return std::max(gm, std::max(g1, cg));
 }
 
 }  // namespace dg

@@ -1,5 +1,6 @@
 // Operators of the implicit pressure stage (Sec. 2 IMEX split; Sec. 3.2
-// pressure loop), centred traces, in two passes each:
+// pressure loop), centred traces, in a one-pass cell form (persistent solves)
+// and a two-pass face + cell form (standalone launches):
 //
 //  gradient (strong form):  g_b = [ sum_a Ja^a_b (D_a p) + Gh_b / w_end ] / J,
 //      face value Gh_b = 1/2 |N| n_b (p+ - p-), added with + on both sides
@@ -10,8 +11,8 @@
 //  Helmholtz:  A p = p/(gamma-1) - alpha div(h grad p), as grad(h-scaled)
 //      followed by the divergence with the Helmholtz epilogue.
 //
-// The per-item work is written as device functions so that the standalone
-// kernels below and the persistent GMRES kernel (k_gmres.cuh) share it.
+// The per-batch work is written as device functions so that the persistent
+// Krylov kernels (k_gmres.cuh) can run it between their grid barriers.
 #pragma once
 
 #include "dg_device.cuh"
@@ -19,38 +20,342 @@
 
 namespace dg {
 
-// Interpolated coarse value of an NV-component field at fine face node k of subface f.
+// Interpolated coarse value of an NV-component field at fine face node k of
+// subface position s, from the coarse cell's values on its face lfp:
+// X[v * vstride + cbase + face_node(lfp, j)] (global memory or a shared tile).
 template <int DIM, int DEG, typename T, int NV>
-__device__ __forceinline__ void coarse_at(const MeshView<T>& mv, const T* __restrict__ X, int64_t Nn, int f,
-                                          int k, T* out) {
-  using S = Shape<DIM, DEG>;
-  constexpr int N = S::N, NC = S::NC;
-  const int cp = mv.face_p[f], lfp = mv.face_lfp[f], s = mv.face_s[f];
-  const T* I = mv.tab + S::T_I;
+__device__ __forceinline__ void coarse_interp(const T* __restrict__ X, int64_t vstride, int64_t cbase, int lfp,
+                                              int s, int k, const T* sI, T* out) {
+  constexpr int N = DEG + 1;
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v] = T(0);
   if (DIM == 2) {
-    const T* Is = I + s * N * N + k * N;
+    const T* Is = sI + s * N * N + k * N;
     for (int j = 0; j < N; ++j) {
-      const int64_t ic = (int64_t)cp * NC + face_node<DIM, DEG>(lfp, j);
+      const int64_t ic = cbase + face_node<DIM, DEG>(lfp, j);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) out[v] += Is[j] * X[(int64_t)v * Nn + ic];
+      for (int v = 0; v < NV; ++v) out[v] += Is[j] * X[(int64_t)v * vstride + ic];
     }
   } else {
     const int k1 = k % N, k2 = k / N;
-    const T* I1 = I + (s & 1) * N * N + k1 * N;
-    const T* I2 = I + ((s >> 1) & 1) * N * N + k2 * N;
+    const T* I1 = sI + (s & 1) * N * N + k1 * N;
+    const T* I2 = sI + ((s >> 1) & 1) * N * N + k2 * N;
+#pragma unroll 1
     for (int j2 = 0; j2 < N; ++j2)
       for (int j1 = 0; j1 < N; ++j1) {
-        const int64_t ic = (int64_t)cp * NC + face_node<DIM, DEG>(lfp, j1 + N * j2);
+        const int64_t ic = cbase + face_node<DIM, DEG>(lfp, j1 + N * j2);
         const T wgt = I1[j1] * I2[j2];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) out[v] += wgt * X[(int64_t)v * Nn + ic];
+        for (int v = 0; v < NV; ++v) out[v] += wgt * X[(int64_t)v * vstride + ic];
       }
   }
 }
 
+// Weight of fine face node q of subface position s in the coarse-side sum at
+// coarse face node kt: the weighted transposed interpolation It.
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ T coarse_weight(const T* sIt, int s, int kt, int q) {
+  constexpr int N = DEG + 1;
+  if (DIM == 2) return sIt[s * N * N + kt * N + q];
+  return sIt[(s & 1) * N * N + (kt % N) * N + (q % N)] * sIt[((s >> 1) & 1) * N * N + (kt / N) * N + (q / N)];
+}
+
 // ---------------------------------------------------------------- gradient
+//
+// Face terms are computed by the cells themselves (no face pass, no face
+// buffer).  A node on a conforming face takes the neighbour's node value; a
+// node on a fine subface interpolates the coarse neighbour's face polynomial
+// at its point.  Both sides evaluate the same expression on the same values,
+// so the face value is the same on both sides.  The coarse side of a 2:1 face
+// needs the face values at all fine points of its subfaces: the threads of the
+// coarse cell compute them once, one fine point each, into shared memory
+// (coarse_pass below), and each coarse face node then sums them through It.
+
+// Number of fine points behind one coarse face, and the shared-memory buffer
+// (elements) the coarse pass needs per cell batch for NV values per point.
+template <int DIM, int DEG>
+__host__ __device__ constexpr int coarse_points() {
+  return Shape<DIM, DEG>::NSUB * Shape<DIM, DEG>::NF;
+}
+template <int DIM, int DEG, int NV>
+__host__ __device__ constexpr int coarse_buffer() {
+  return Shape<DIM, DEG>::CPB * NV * coarse_points<DIM, DEG>();
+}
+
+// bit lf set if local face lf of cell c is the coarse side of a 2:1 face
+template <int DIM, typename T>
+__device__ __forceinline__ unsigned coarse_mask(const MeshView<T>& mv, int64_t c) {
+  unsigned m = 0;
+#pragma unroll
+  for (int lf = 0; lf < 2 * DIM; ++lf)
+    if ((mv.cell_face[c * 2 * DIM + lf] & 3) == 2) m |= 1u << lf;
+  return m;
+}
+
+// Coarse sides of the batch's 2:1 faces, one local face at a time.  For every
+// cell whose face lf is a coarse side, point(f, lf, s, q, j) writes the NV
+// face values of fine point q of subface s (face f + s) to the buffer at
+// sJ[(lc * NV + v) * NP + j], j = s * NF + q; then each node of that face adds
+// sum_s sum_q weight * value to acc[0..NV) with weight = sign * It.  Called by
+// the whole block (contains __syncthreads; returns at once if no cell of the
+// batch has a coarse side).
+template <int DIM, int DEG, typename T, int NV, class Point>
+__device__ __forceinline__ void coarse_pass(const MeshView<T>& mv, bool active, int64_t c, int lc, int i,
+                                            const int* id, unsigned cmask, const T* sIt, T sign, T* sJ, T* acc,
+                                            Point&& point) {
+  using S = Shape<DIM, DEG>;
+  constexpr int NF = S::NF, NC = S::NC, NP = coarse_points<DIM, DEG>();
+  if (!__syncthreads_or(active && cmask != 0u)) return;
+  for (int lf = 0; lf < 2 * DIM; ++lf) {
+    const bool mine = active && ((cmask >> lf) & 1u);
+    if (!__syncthreads_or(mine)) continue;
+    const int a = lf >> 1;
+    const int f = mine ? (mv.cell_face[c * 2 * DIM + lf] >> 2) : 0;
+    if (mine)
+      for (int j = i; j < NP; j += NC) point(f, lf, j / NF, j % NF, j);
+    __syncthreads();
+    if (mine && id[a] == ((lf & 1) ? DEG : 0)) {
+      const int kt = tangential_index<DIM, DEG>(a, id);
+      for (int s = 0; s < S::NSUB; ++s)
+        for (int q = 0; q < NF; ++q) {
+          const T wgt = sign * coarse_weight<DIM, DEG, T>(sIt, s, kt, q);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) acc[v] += wgt * sJ[(lc * NV + v) * NP + s * NF + q];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// sum over the node's conforming and fine-side faces of 1/2 |N| n_b (p+ - p-)
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void grad_face_terms(const MeshView<T>& mv, const T* __restrict__ p, const int* codes,
+                                                const int* id, T pv, const T* sI, T* facc) {
+  using S = Shape<DIM, DEG>;
+  constexpr int NF = S::NF, NC = S::NC;
+  const int64_t total = (int64_t)mv.nf * NF;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const int code = codes[a];
+    if (code < 0) continue;
+    const int f = code >> 2, side = code & 3;
+    if (side >= 2) continue;  // coarse side: coarse_pass; wall: p^ = p-, no jump
+    const int kt = tangential_index<DIM, DEG>(a, id);
+    const int64_t t = (int64_t)f * NF + kt;
+    T pm, pp;
+    if (side == 1) {
+      pp = pv;
+      pm = p[mv.fnode_m[t]];
+    } else {
+      pm = pv;
+      if (f < mv.nconf)
+        pp = p[mv.fnode_p[t]];
+      else
+        coarse_interp<DIM, DEG, T, 1>(p, 0, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], kt, sI, &pp);
+    }
+    const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) facc[b] += jmp * mv.fn[(int64_t)b * total + t];
+  }
+}
+
+// Cells [batch*CPB, batch*CPB + CPB): g_b = h [sum_a Ja^a_b (D_a p) + face_b / w_end] / J.
+// Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
+// sII holds the interpolation tables I (2 N^2) followed by It (2 N^2); sJ is
+// the coarse-pass buffer (coarse_buffer<DIM, DEG, DIM>() elements).
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
+                                                const T* __restrict__ h, T* __restrict__ g, int64_t batch, T* sp,
+                                                T* sJ, const T* sD, const T* sII) {
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
+  const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
+  const int64_t c = batch * CPB + lc;
+  const bool active = (lc < CPB) && (c < mv.n_cells);
+  const int64_t Nn = mv.n_nodes;
+  const int64_t idx = c * NC + i;
+  int id[3] = {i % N, (i / N) % N, i / (N * N)};
+  int codes[DIM];
+  T Jl[DIM][DIM];
+  T scale = T(0), pv = T(0);
+  unsigned cmask = 0u;
+  if (active) {
+    pv = p[idx];
+    sp[lc * NC + i] = pv;
+    load_face_codes<DIM, DEG, T>(mv, c, id, codes);
+    cmask = coarse_mask<DIM, T>(mv, c);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
+    scale = mv.invJ[idx] * (h ? h[idx] : T(1));
+  }
+  __syncthreads();
+  T facc[DIM], dp[DIM];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) facc[b] = dp[b] = T(0);
+  if (active) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+      const int i0 = lc * NC + i - id[a] * stride;
+      const T* D = sD + id[a] * N;
+      T s = T(0);
+#pragma unroll
+      for (int kk = 0; kk < N; ++kk) s += D[kk] * sp[i0 + kk * stride];
+      dp[a] = s;
+    }
+    grad_face_terms<DIM, DEG, T>(mv, p, codes, id, pv, sII, facc);
+  }
+  // coarse sides: jump at each fine point from the fine value and the cell's own polynomial
+  const int64_t total = (int64_t)mv.nf * NF;
+  coarse_pass<DIM, DEG, T, DIM>(mv, active, c, lc, i, id, cmask, sII + 2 * N * N, T(1), sJ, facc,
+                                [&](int f, int lf, int s, int q, int j) {
+                                  const int64_t t = (int64_t)(f + s) * NF + q;
+                                  const T pm = p[mv.fnode_m[t]];
+                                  T pp;
+                                  coarse_interp<DIM, DEG, T, 1>(sp + lc * NC, 0, 0, lf, s, q, sII, &pp);
+                                  const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
+#pragma unroll
+                                  for (int b = 0; b < DIM; ++b)
+                                    sJ[(lc * DIM + b) * NP + j] = jmp * mv.fn[(int64_t)b * total + t];
+                                });
+  if (active) {
+    const T iwend = mv.tab[S::T_IWEND];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      T s = facc[b] * iwend;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) s += Jl[a][b] * dp[a];
+      g[(int64_t)b * Nn + idx] = s * scale;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- divergence
+
+// sum over the node's conforming and fine-side faces of +-|N| {f}.n (+ on the
+// minus side, - on the plus side)
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void div_face_terms(const MeshView<T>& mv, const T* __restrict__ fld, const int* codes,
+                                               const int* id, const T* fv, const T* sI, T* facc) {
+  using S = Shape<DIM, DEG>;
+  constexpr int NF = S::NF, NC = S::NC;
+  const int64_t total = (int64_t)mv.nf * NF;
+  const int64_t Nn = mv.n_nodes;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const int code = codes[a];
+    if (code < 0) continue;
+    const int f = code >> 2, side = code & 3;
+    if (side >= 2) continue;  // coarse side: coarse_pass; wall: zero normal flux
+    const int kt = tangential_index<DIM, DEG>(a, id);
+    const int64_t t = (int64_t)f * NF + kt;
+    T fo[DIM];  // the other side's values
+    if (side == 1) {
+      const int64_t im = mv.fnode_m[t];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) fo[b] = fld[(int64_t)b * Nn + im];
+    } else if (f < mv.nconf) {
+      const int64_t ip = mv.fnode_p[t];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) fo[b] = fld[(int64_t)b * Nn + ip];
+    } else {
+      coarse_interp<DIM, DEG, T, DIM>(fld, Nn, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], kt, sI, fo);
+    }
+    // (minus + plus) in that order on both sides
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) s += (side == 1 ? fo[b] + fv[b] : fv[b] + fo[b]) * mv.fn[(int64_t)b * total + t];
+    const T dh = T(0.5) * mv.fsj[t] * s;
+    facc[0] += (side == 1) ? -dh : dh;
+  }
+}
+
+// Cells of one batch: out = HELM ? scale * (ident p/(gamma-1) - alpha div) : div.
+// Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
+// sJ: coarse-pass buffer (coarse_buffer<DIM, DEG, 1>() elements).
+template <int DIM, int DEG, typename T, bool HELM>
+__device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
+                                               const T* __restrict__ p, T alpha, T scale, T ident,
+                                               T* __restrict__ out, int64_t batch, T* sF, T* sJ, const T* sDw,
+                                               const T* sII) {
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
+  const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
+  const int64_t c = batch * CPB + lc;
+  const bool active = (lc < CPB) && (c < mv.n_cells);
+  const int64_t Nn = mv.n_nodes;
+  const int64_t idx = c * NC + i;
+  int id[3] = {i % N, (i / N) % N, i / (N * N)};
+  int codes[DIM];
+  T ft[DIM];  // Ja^a . f for each axis a
+  T fv[DIM];
+  T ij = T(0), pv = T(0);
+  unsigned cmask = 0u;
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) fv[b] = fld[(int64_t)b * Nn + idx];
+    load_face_codes<DIM, DEG, T>(mv, c, id, codes);
+    cmask = coarse_mask<DIM, T>(mv, c);
+    ij = mv.invJ[idx];
+    if (HELM) pv = p[idx];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * fv[b];
+      ft[a] = s;
+    }
+  }
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (active) sF[lc * NC + i] = ft[a];
+    __syncthreads();
+    if (active) {
+      const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+      const int i0 = lc * NC + i - id[a] * stride;
+      const T* Dw = sDw + id[a] * N;
+#pragma unroll
+      for (int kk = 0; kk < N; ++kk) acc -= Dw[kk] * sF[i0 + kk * stride];
+    }
+    __syncthreads();
+  }
+  T facc = T(0);
+  if (active) div_face_terms<DIM, DEG, T>(mv, fld, codes, id, fv, sII, &facc);
+  // coarse sides: |N| {f}.n at each fine point from the fine value and the cell's own polynomial
+  const int64_t total = (int64_t)mv.nf * NF;
+  coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, cmask, sII + 2 * N * N, T(-1), sJ, &facc,
+                              [&](int f, int lf, int s, int q, int j) {
+                                const int64_t t = (int64_t)(f + s) * NF + q;
+                                const int64_t im = mv.fnode_m[t];
+                                T fc[DIM];
+                                coarse_interp<DIM, DEG, T, DIM>(fld, Nn, c * NC, lf, s, q, sII, fc);
+                                T sum = T(0);
+#pragma unroll
+                                for (int b = 0; b < DIM; ++b)
+                                  sum += (fld[(int64_t)b * Nn + im] + fc[b]) * mv.fn[(int64_t)b * total + t];
+                                sJ[lc * NP + j] = T(0.5) * mv.fsj[t] * sum;
+                              });
+  if (active) {
+    const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
+    if (HELM)
+      out[idx] = scale * (ident * pv / gm1<T>() - alpha * dv);
+    else
+      out[idx] = dv;
+  }
+}
+
+// ---------------------------------------------------------------- two-pass form
+//
+// The standalone operators (dg_apply_grad / _div / _implicit and the
+// one-launch-per-kernel Krylov solve) run each operator as a face pass, which
+// evaluates every face value once into a face buffer, and a cell pass that
+// gathers them.  Launched on their own, these kernels keep more blocks
+// resident and shorter load chains than the one-pass cell form above, which
+// serves the persistent solves (where it saves two grid barriers per mat-vec).
 
 // face node t (< (nconf+nsub)*NF): Gh_b = 1/2 |N| n_b (p+ - p-)
 template <int DIM, int DEG, typename T>
@@ -65,7 +370,8 @@ __device__ __forceinline__ void grad_face_item(const MeshView<T>& mv, const T* _
   if (f < mv.nconf)
     pp = p[mv.fnode_p[t]];
   else
-    coarse_at<DIM, DEG, T, 1>(mv, p, mv.n_nodes, f, k, &pp);
+    coarse_interp<DIM, DEG, T, 1>(p, 0, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], k, mv.tab + S::T_I,
+                                  &pp);
   const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
 #pragma unroll
   for (int b = 0; b < DIM; ++b) Gh[(int64_t)b * total + t] = jmp * mv.fn[(int64_t)b * total + t];
@@ -76,7 +382,7 @@ __device__ __forceinline__ void grad_face_item(const MeshView<T>& mv, const T* _
 // Every global load that does not depend on the face values is issued before
 // the barrier so that the loads' latencies overlap.
 template <int DIM, int DEG, typename T>
-__device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
+__device__ __forceinline__ void grad_gather_batch(const MeshView<T>& mv, const T* __restrict__ p,
                                                 const T* __restrict__ h, const T* __restrict__ Gh,
                                                 T* __restrict__ g, int64_t batch, T* sp, const T* sD,
                                                 const T* sIt) {
@@ -129,8 +435,6 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   __syncthreads();
 }
 
-// ---------------------------------------------------------------- divergence
-
 // face node t (< (nconf+nsub)*NF): Dh = |N| {f}.n
 template <int DIM, int DEG, typename T>
 __device__ __forceinline__ void div_face_item(const MeshView<T>& mv, const T* __restrict__ fld, T* __restrict__ Dh,
@@ -147,7 +451,8 @@ __device__ __forceinline__ void div_face_item(const MeshView<T>& mv, const T* __
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fp[b] = fld[(int64_t)b * Nn + ip];
   } else {
-    coarse_at<DIM, DEG, T, DIM>(mv, fld, Nn, f, k, fp);
+    coarse_interp<DIM, DEG, T, DIM>(fld, Nn, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], k,
+                                    mv.tab + S::T_I, fp);
   }
   T s = T(0);
 #pragma unroll
@@ -158,7 +463,7 @@ __device__ __forceinline__ void div_face_item(const MeshView<T>& mv, const T* __
 // Cells of one batch: out = HELM ? scale * (ident p/(gamma-1) - alpha div) : div.
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 template <int DIM, int DEG, typename T, bool HELM>
-__device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
+__device__ __forceinline__ void div_gather_batch(const MeshView<T>& mv, const T* __restrict__ fld,
                                                const T* __restrict__ Dh, const T* __restrict__ p, T alpha, T scale,
                                                T ident, T* __restrict__ out, int64_t batch, T* sF, const T* sDw,
                                                const T* sIt) {
@@ -213,7 +518,6 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   }
 }
 
-// ---------------------------------------------------------------- standalone kernels
 
 template <int DIM, int DEG, typename T>
 __global__ void __launch_bounds__(256) grad_face_kernel(MeshView<T> mv, const T* __restrict__ p,
@@ -225,7 +529,7 @@ __global__ void __launch_bounds__(256) grad_face_kernel(MeshView<T> mv, const T*
 }
 
 template <int DIM, int DEG, typename T>
-__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_cell_kernel(MeshView<T> mv,
+__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_gather_kernel(MeshView<T> mv,
                                                                              const T* __restrict__ p,
                                                                              const T* __restrict__ h,
                                                                              const T* __restrict__ Gh,
@@ -239,7 +543,7 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_cell_kernel(Mes
   __shared__ T sIt[2 * N * N];
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sD[q] = mv.tab[S::T_D + q];
   for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
-  grad_cell_batch<DIM, DEG, T>(mv, p, h, Gh, g, blockIdx.x, sp, sD, sIt);
+  grad_gather_batch<DIM, DEG, T>(mv, p, h, Gh, g, blockIdx.x, sp, sD, sIt);
 }
 
 template <int DIM, int DEG, typename T>
@@ -252,7 +556,7 @@ __global__ void __launch_bounds__(256) div_face_kernel(MeshView<T> mv, const T* 
 }
 
 template <int DIM, int DEG, typename T, bool HELM>
-__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(MeshView<T> mv,
+__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_gather_kernel(MeshView<T> mv,
                                                                             const T* __restrict__ fld,
                                                                             const T* __restrict__ Dh,
                                                                             const T* __restrict__ p, T alpha,
@@ -266,7 +570,7 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(Mesh
   __shared__ T sIt[2 * N * N];
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sDw[q] = mv.tab[S::T_DW + q];
   for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
-  div_cell_batch<DIM, DEG, T, HELM>(mv, fld, Dh, p, alpha, T(1), T(1), out, blockIdx.x, sF, sDw, sIt);
+  div_gather_batch<DIM, DEG, T, HELM>(mv, fld, Dh, p, alpha, T(1), T(1), out, blockIdx.x, sF, sDw, sIt);
 }
 
 }  // namespace dg

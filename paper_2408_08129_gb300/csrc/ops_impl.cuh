@@ -48,7 +48,7 @@ int run_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* Gh, cudaStream_t
   const int64_t tf = (int64_t)(mv.nconf + mv.nsub) * S::NF;
   count_launches(m->ctx, tf ? 2 : 1);
   if (tf) grad_face_kernel<DIM, DEG, T><<<blocks_for(tf, 256), 256, 0, s>>>(mv, p, Gh, skip);
-  grad_cell_kernel<DIM, DEG, T><<<blocks_for(mv.n_cells, S::CPB), S::THREADS, 0, s>>>(mv, p, h, Gh, g, skip);
+  grad_gather_kernel<DIM, DEG, T><<<blocks_for(mv.n_cells, S::CPB), S::THREADS, 0, s>>>(mv, p, h, Gh, g, skip);
   return check_launch("gradient launch");
 }
 
@@ -59,8 +59,8 @@ int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, T* Dh, cu
   const int64_t tf = (int64_t)(mv.nconf + mv.nsub) * S::NF;
   count_launches(m->ctx, tf ? 2 : 1);
   if (tf) div_face_kernel<DIM, DEG, T><<<blocks_for(tf, 256), 256, 0, s>>>(mv, f, Dh, skip);
-  div_cell_kernel<DIM, DEG, T, HELM><<<blocks_for(mv.n_cells, S::CPB), S::THREADS, 0, s>>>(mv, f, Dh, p, alpha,
-                                                                                           out, skip);
+  div_gather_kernel<DIM, DEG, T, HELM><<<blocks_for(mv.n_cells, S::CPB), S::THREADS, 0, s>>>(mv, f, Dh, p, alpha,
+                                                                                             out, skip);
   return check_launch("divergence launch");
 }
 
@@ -78,7 +78,6 @@ int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b
   a.Q = Q;
   a.w = w;
   a.w64 = w64;
-  a.Gh = m->d_face_scratch64;
   a.gv = m->d_vec_scratch64;
   a.partial = partial;
   a.out = out;
@@ -160,7 +159,6 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
       a.Q = it[i].Q;
       a.w = it[i].w;
       a.w64 = it[i].w64;
-      a.Gh = m->d_face_scratch64;
       a.gv = m->d_vec_scratch64;
       a.partial = it[i].partial;
       a.out = it[i].out;

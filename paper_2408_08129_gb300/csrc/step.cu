@@ -613,7 +613,7 @@ int prepare_member(Member& M, dg_ctx* ctx, const dg_mesh* m, dg_state* S, double
   if (opts) M.o = *opts;
   if (M.o.precision != DG_FP64 && M.o.precision != DG_FP32) return fail(DG_EINVAL, "bad precision");
   if (M.o.picard < 1 || M.o.picard > 32) return fail(DG_EINVAL, "picard must be in 1..32");
-  if (M.o.krylov != DG_KRYLOV_GMRES && M.o.krylov != DG_KRYLOV_CG) return fail(DG_EINVAL, "bad Krylov method");
+  if (M.o.krylov < DG_KRYLOV_GMRES || M.o.krylov > DG_KRYLOV_GMRES_CGS2) return fail(DG_EINVAL, "bad Krylov method");
   M.S = S;
   M.m = m;
   M.dt = dt;

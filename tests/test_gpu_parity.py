@@ -262,10 +262,13 @@ def test_autotuner_times_both_solver_forms(dg, ctx):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_imex_steps_conjugate_gradients(dg, ctx, precision):
-    """CG in the w J inner product reaches the same step as the oracle's GMRES (M A is SPD)."""
+@pytest.mark.parametrize("krylov", ["cg", "gmres_cgs2"])
+def test_imex_steps_other_krylov_forms(dg, ctx, precision, krylov):
+    """CG in the w J inner product (M A is SPD) and GMRES with classical Gram-Schmidt twice per
+    step reach the same step as the oracle's GMRES."""
     prec = dg.DG_FP64 if precision == "fp64" else dg.DG_FP32
-    opts = dg.solver_opts(tol=1e-12, krylov=dg.DG_KRYLOV_CG, precision=prec, inner_tol=1e-4)
+    kry = dg.DG_KRYLOV_CG if krylov == "cg" else dg.DG_KRYLOV_GMRES_CGS2
+    opts = dg.solver_opts(tol=1e-12, krylov=kry, precision=prec, inner_tol=1e-4, fused=1)
     case = make_case("bubble2d", 0)
     U, Ur, ref = _run_steps(dg, ctx, case, 10, opts)
     assert _per_var_rel(U - ref.Ubg, Ur - ref.Ubg) < 1e-9

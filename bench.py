@@ -324,7 +324,8 @@ CONFIG = {
     "hill2d": {
         "workload": "hill2d: 2D x-z flow over a seeded Gaussian hill, 64x32 base quads over 40x20 km, "
                     "two 2:1 refinement levels near the ground (2912 cells), degree 4, FP64, "
-                    "constant-N atmosphere + 10 m/s inflow; IMEX-RK2 steps (GMRES tol 1e-12, 3 Picard)",
+                    "constant-N atmosphere + 10 m/s inflow; IMEX-RK2 steps, 3 Picard iterations per implicit "
+                    "stage, Helmholtz solves to relative residual 1e-12",
         "dof": 291200,
         "l2": "flushed between timed steps (256 MB write)",
     },
@@ -348,6 +349,12 @@ def main():
     ap.add_argument("--sweep-workload", default="hill3d_big")
     ap.add_argument("--sweep-only", action="store_true", help="run only the operator-apply sweep")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble and serving measurements")
+    ap.add_argument("--krylov", default="auto", choices=["auto", "gmres", "gmres_cgs2", "cg", "chebyshev"],
+                    help="linear solver of the timed steps (auto: autotuned among GMRES and Chebyshev; "
+                         "the other forms are timed beside it)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="fp32 = FP32 Krylov iterations inside FP64 refinement")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32-refined and other-solver comparisons")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -373,7 +380,10 @@ def main():
     case = make_case(args.workload, 0)
     ctx = dg.Context(local)
     mesh = dg.Mesh(ctx, case)
-    opts = dg.solver_opts(tol=1e-12, picard=3, restart=30)
+    kry = {"auto": dg.DG_KRYLOV_AUTO, "gmres": dg.DG_KRYLOV_GMRES, "gmres_cgs2": dg.DG_KRYLOV_GMRES_CGS2,
+           "cg": dg.DG_KRYLOV_CG, "chebyshev": dg.DG_KRYLOV_CHEBYSHEV}[args.krylov]
+    prec = dg.DG_FP64 if args.precision == "fp64" else dg.DG_FP32
+    opts = dg.solver_opts(tol=1e-12, picard=3, restart=30, krylov=kry, precision=prec, inner_tol=1e-4)
     state = dg.State(ctx, mesh, opts)
     init = case.init
     if init["kind"] == "bubble":
@@ -421,64 +431,81 @@ def main():
 
     U64 = state.download()
 
-    # the FP32-refined form from the same start: FP32 applies + FP32 inner GMRES, FP64 outer residual
-    opts32 = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=dg.DG_FP32, inner_tol=1e-4)
-    state.upload(U_start)
-    for _ in range(args.warmup):  # untimed: lazy loading and the autotuner's first FP32 solve
-        dg.imex_rk2_step(ctx, mesh, state, case.dt, opts32)
-    state.upload(U_start)
-    times32, its32 = [], 0
-    for _ in range(args.steps):
-        flush.zero_()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        its32 += dg.imex_rk2_step(ctx, mesh, state, case.dt, opts32)["gmres_iters"]
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        times32.append(ev0.elapsed_time(ev1))
-    U32 = state.download()
     Ubg = torch.empty(mesh.shape(), dtype=torch.float64, device="cuda")
     dg.dg_background(ctx, mesh, Ubg)
     Ubg = Ubg.cpu().numpy()
-    rel_full = max(np.linalg.norm(U32[v] - U64[v]) / np.linalg.norm(U64[v]) for v in range(mesh.n_vars))
-    rel_dev = max(np.linalg.norm(U32[v] - U64[v]) / max(np.linalg.norm(U64[v] - Ubg[v]), 1e-300)
-                  for v in range(mesh.n_vars))
-    fp32 = {"ms_per_step": sum(times32) / args.steps,
-            "value": world * dof * args.steps / (sum(times32) / 1e3),
-            "speedup_vs_fp64": sum(times) / sum(times32),
-            "inner_iters_per_step": its32 / args.steps,
-            "rel_err_vs_fp64_full_state": rel_full,
-            "rel_err_vs_fp64_deviation": rel_dev}
-    # other Krylov forms from the same start: GMRES with classical Gram-Schmidt twice per step, and
-    # conjugate gradients (the Helmholtz operator is self-adjoint in the w J inner product)
-    cg = {}
-    for name, prec, kry in (("gmres_cgs2_fp64", dg.DG_FP64, dg.DG_KRYLOV_GMRES_CGS2),
-                            ("cg_fp64", dg.DG_FP64, dg.DG_KRYLOV_CG),
-                            ("cg_fp32_refined", dg.DG_FP32, dg.DG_KRYLOV_CG)):
-        o = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=prec, inner_tol=1e-4, krylov=kry, fused=1)
+    tuned = mesh.autotuned()  # the headline's choice, before the other forms run
+    fp32, cg = None, None
+    if not args.no_forms:
+        # the FP32-refined form from the same start: FP32 applies + FP32 inner GMRES, FP64 outer residual
+        opts32 = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=dg.DG_FP32, inner_tol=1e-4)
         state.upload(U_start)
-        for _ in range(args.warmup):
-            dg.imex_rk2_step(ctx, mesh, state, case.dt, o)
+        for _ in range(args.warmup):  # untimed: lazy loading and the autotuner's first FP32 solve
+            dg.imex_rk2_step(ctx, mesh, state, case.dt, opts32)
         state.upload(U_start)
-        tms, its = [], 0
+        times32, its32 = [], 0
         for _ in range(args.steps):
             flush.zero_()
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             ev0.record(stream)
-            its += dg.imex_rk2_step(ctx, mesh, state, case.dt, o)["gmres_iters"]
+            its32 += dg.imex_rk2_step(ctx, mesh, state, case.dt, opts32)["gmres_iters"]
             ev1.record(stream)
             torch.cuda.synchronize()
-            tms.append(ev0.elapsed_time(ev1))
-        Uc = state.download()
-        cg[name] = {"ms_per_step": sum(tms) / args.steps, "value": world * dof * args.steps / (sum(tms) / 1e3),
-                    "speedup_vs_gmres_fp64": sum(times) / sum(tms), "iters_per_step": its / args.steps,
-                    "rel_err_vs_gmres_fp64_deviation": max(
-                        np.linalg.norm(Uc[v] - U64[v]) / max(np.linalg.norm(U64[v] - Ubg[v]), 1e-300)
-                        for v in range(mesh.n_vars))}
+            times32.append(ev0.elapsed_time(ev1))
+        U32 = state.download()
+        rel_full = max(np.linalg.norm(U32[v] - U64[v]) / np.linalg.norm(U64[v]) for v in range(mesh.n_vars))
+        rel_dev = max(np.linalg.norm(U32[v] - U64[v]) / max(np.linalg.norm(U64[v] - Ubg[v]), 1e-300)
+                      for v in range(mesh.n_vars))
+        fp32 = {"ms_per_step": sum(times32) / args.steps,
+                "value": world * dof * args.steps / (sum(times32) / 1e3),
+                "speedup_vs_fp64": sum(times) / sum(times32),
+                "inner_iters_per_step": its32 / args.steps,
+                "rel_err_vs_fp64_full_state": rel_full,
+                "rel_err_vs_fp64_deviation": rel_dev,
+                "solver": mesh.autotuned()["fp32"]["form"]}
+        # other Krylov forms from the same start: GMRES with classical Gram-Schmidt twice per step, and
+        # conjugate gradients (the Helmholtz operator is self-adjoint in the w J inner product)
+        cg = {}
+        for name, prec, kry in (("gmres_fp64", dg.DG_FP64, dg.DG_KRYLOV_GMRES),
+                                ("gmres_fp32_refined", dg.DG_FP32, dg.DG_KRYLOV_GMRES),
+                                ("gmres_cgs2_fp64", dg.DG_FP64, dg.DG_KRYLOV_GMRES_CGS2),
+                                ("cg_fp64", dg.DG_FP64, dg.DG_KRYLOV_CG),
+                                ("cg_fp32_refined", dg.DG_FP32, dg.DG_KRYLOV_CG),
+                                ("chebyshev_fp64", dg.DG_FP64, dg.DG_KRYLOV_CHEBYSHEV),
+                                ("chebyshev_fp32_refined", dg.DG_FP32, dg.DG_KRYLOV_CHEBYSHEV)):
+            o = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=prec, inner_tol=1e-4, krylov=kry,
+                               fused=-1 if kry == dg.DG_KRYLOV_GMRES else 1)
+            state.upload(U_start)
+            for _ in range(args.warmup):
+                dg.imex_rk2_step(ctx, mesh, state, case.dt, o)
+            state.upload(U_start)
+            tms, its = [], 0
+            for _ in range(args.steps):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                its += dg.imex_rk2_step(ctx, mesh, state, case.dt, o)["gmres_iters"]
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                tms.append(ev0.elapsed_time(ev1))
+            Uc = state.download()
+            cg[name] = {"ms_per_step": sum(tms) / args.steps, "value": world * dof * args.steps / (sum(tms) / 1e3),
+                        "speedup_vs_headline": sum(times) / sum(tms), "iters_per_step": its / args.steps,
+                        "rel_err_vs_headline_deviation": max(
+                            np.linalg.norm(Uc[v] - U64[v]) / max(np.linalg.norm(U64[v] - Ubg[v]), 1e-300)
+                            for v in range(mesh.n_vars))}
+            # one more (untimed) step with the per-phase clock of the persistent solve on
+            dg.dg_profile_reset(ctx)
+            dg.dg_profile_enable(ctx, True)
+            dg.imex_rk2_step(ctx, mesh, state, case.dt, o)
+            ph = dg.dg_profile_read_gmres_phases(ctx)
+            dg.dg_profile_enable(ctx, False)
+            cg[name]["phase_us_per_iteration"] = {k: round(1e3 * v / max(1, ph["iterations"]), 3) for k, v in ph.items()
+                                                  if k not in ("iterations", "second_passes") and v > 0}
     state.upload(U64)
 
     # end to end through the C ABI with host buffers: upload, step, download per step
@@ -506,12 +533,18 @@ def main():
     iters = sum(s["gmres_iters"] for s in stats)
     solves = sum(s["solves"] for s in stats)
     if dom == "gmres":
-        # one launch = one whole GMRES solve: per iteration one Helmholtz mat-vec and
-        # Gram-Schmidt twice over the k+1 basis vectors (two dots + two axpys, 8 (k+1)
-        # flops/node), plus the initial residual mat-vec; it = mean iterations per solve
+        # one launch = one whole solve; it = mean iterations per solve.  GMRES: per iteration
+        # one Helmholtz mat-vec and Gram-Schmidt twice over the k+1 basis vectors (two dots +
+        # two axpys, 8 (k+1) flops/node), plus the residual mat-vec.  Chebyshev: per iteration
+        # one mat-vec and the three-vector update (8 flops/node), plus the residual mat-vec.
         it = iters / max(1, solves)
-        flops = (it + 1) * helm_flops + n * (4.0 * it * (it + 1) + 4.0 * it)
-        name = "gmres_persistent_kernel (fused Helmholtz GMRES solve)"
+        form = (tuned[args.precision]["form"] or "") if args.krylov == "auto" else args.krylov
+        if "chebyshev" in form:
+            flops = (it + 1) * helm_flops + n * 8.0 * it
+            name = "gmres_persistent_kernel (persistent Chebyshev solve)"
+        else:
+            flops = (it + 1) * helm_flops + n * (4.0 * it * (it + 1) + 4.0 * it)
+            name = "gmres_persistent_kernel (persistent GMRES solve)"
     elif dom == "explicit":
         flops = expl_flops
         name = "explicit apply (face + cell kernels)"
@@ -529,14 +562,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(CONFIG[args.workload], replicas=world, precision="fp64"),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic", "config": dict(CONFIG[args.workload], replicas=world, precision=args.precision, krylov=args.krylov),
         "roofline": roof,
         "breakdown_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "gmres_phase_us_per_iteration": {k: 1e3 * v / max(1, phases["iterations"]) for k, v in phases.items()
                                          if k not in ("iterations", "second_passes")},
         "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in stats),
-        "autotuned_solver": mesh.autotuned(),
+        "autotuned_solver": tuned,
         "fp32_refined": fp32,
         "other_krylov_forms": cg,
         "e2e": e2e, "gpu_launches": launches,

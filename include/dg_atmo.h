@@ -62,7 +62,13 @@ typedef enum {
 } dg_status;
 
 typedef enum { DG_FP64 = 0, DG_FP32 = 1 } dg_precision;
-typedef enum { DG_KRYLOV_GMRES = 0, DG_KRYLOV_CG = 1, DG_KRYLOV_GMRES_CGS2 = 2 } dg_krylov;
+typedef enum {
+  DG_KRYLOV_AUTO = -1,
+  DG_KRYLOV_GMRES = 0,
+  DG_KRYLOV_CG = 1,
+  DG_KRYLOV_GMRES_CGS2 = 2,
+  DG_KRYLOV_CHEBYSHEV = 3
+} dg_krylov;
 typedef enum { DG_TERMS_FULL = 0, DG_TERMS_IMEX_EXPLICIT = 1 } dg_terms;
 typedef enum { DG_HILL_NONE = 0, DG_HILL_GAUSS = 1, DG_HILL_BELL = 2, DG_HILL_PARABOLA = 3 } dg_hill_kind;
 typedef enum { DG_ATM_NONE = 0, DG_ATM_ISOTHERMAL = 1, DG_ATM_STRATIFIED = 2 } dg_atm_kind;
@@ -147,9 +153,11 @@ typedef struct {
   double min_edge;                      /* smallest computational cell edge   */
   size_t device_bytes;                  /* device memory held by the mesh     */
   int solver_form[2];                   /* autotuned Helmholtz solver for FP64 */
-                                        /* [0] and FP32 [1]: 1 persistent, 0   */
-                                        /* multi-kernel, -1 not tuned yet      */
-  float solver_ms[2][2];                /* the timed solves: [precision][form] */
+                                        /* [0] and FP32 [1]: 0 GMRES one launch */
+                                        /* per kernel, 1 GMRES persistent, 2    */
+                                        /* Chebyshev persistent; -1 not tuned   */
+  float solver_ms[2][3];                /* the timed solves [precision][form]   */
+                                        /* (0 where a form was not timed)       */
 } dg_mesh_info;
 
 /* Build connectivity (conforming faces, 2:1 subfaces, walls), check the 2:1
@@ -238,16 +246,29 @@ typedef struct {
                        /*    kernel; 0: one launch per Krylov kernel; -1       */
                        /*    (default): autotuned per mesh and precision by     */
                        /*    timing both forms on the first solve               */
-  int krylov;          /* DG_KRYLOV_GMRES (Sec. 3.2, default): persistent form  */
-                       /*    with one reduction per Arnoldi step (second        */
-                       /*    Gram-Schmidt pass delayed into the next step);     */
-                       /*    DG_KRYLOV_GMRES_CGS2: classical Gram-Schmidt twice */
-                       /*    per step (two or three reductions);               */
-                       /*    DG_KRYLOV_CG: conjugate gradients in the w J inner */
+  int krylov;          /* DG_KRYLOV_AUTO (default): the first solve of a mesh  */
+                       /*    and precision is timed as GMRES (both forms) and   */
+                       /*    as Chebyshev, and the fastest is kept; in batched  */
+                       /*    steps (no timing) the mesh's tuned persistent form */
+                       /*    is used, else Chebyshev.                           */
+                       /*  DG_KRYLOV_GMRES (Sec. 3.2): persistent form with one */
+                       /*    reduction per Arnoldi step (second Gram-Schmidt    */
+                       /*    pass delayed into the next step); with fused = -1 */
+                       /*    the persistent and one-launch-per-kernel forms are */
+                       /*    timed and the faster kept.                         */
+                       /*  DG_KRYLOV_GMRES_CGS2: classical Gram-Schmidt twice   */
+                       /*    per step (two or three reductions).                */
+                       /*  DG_KRYLOV_CG: conjugate gradients in the w J inner   */
                        /*    product, in which the Helmholtz operator is        */
                        /*    self-adjoint and positive (persistent form only).  */
-                       /*    The one-launch-per-kernel form (fused = 0) runs    */
-                       /*    GMRES with classical Gram-Schmidt twice.           */
+                       /*  DG_KRYLOV_CHEBYSHEV: Chebyshev iteration on the      */
+                       /*    spectral interval [1/(gamma-1), lmax], lmax from   */
+                       /*    power iteration on the first solve, kept per state */
+                       /*    (persistent form only; no inner products, two grid */
+                       /*    barriers per step; falls back to GMRES if the      */
+                       /*    residual grows).                                   */
+                       /*  The one-launch-per-kernel form (fused = 0) runs      */
+                       /*  GMRES with classical Gram-Schmidt twice.             */
 } dg_solver_opts;
 
 typedef struct {
@@ -269,6 +290,14 @@ double* dg_state_data(dg_state* state);
  * state's stream; both wait for completion. */
 int dg_state_upload(dg_state* state, const double* host_U);
 int dg_state_download(dg_state* state, double* host_U);
+/* Upper spectral bound the state's DG_KRYLOV_CHEBYSHEV solves use, with the
+ * alpha = (a_ii dt)^2 it belongs to: get[2] (host, may be NULL) receives the
+ * current pair ({0, 0} before the first Chebyshev solve); set[2] (host, may
+ * be NULL) replaces it -- a caller who knows the spectrum can skip the power
+ * iteration; a bound with set[0] <= 1/(gamma-1) is cleared (re-estimated on the
+ * next solve).  A bound that is too low is detected and repaired by the solve
+ * (GMRES fallback, re-estimate).  Synchronises the device first. */
+int dg_state_chebyshev_bound(dg_state* state, double* get, const double* set);
 
 /* One IMEX-RK2 step U^n -> U^{n+1} of size dt (Sec. 2 scheme; readings: ARK2
  * tableau, Picard loop on the pressure with lagged enthalpy and kinetic

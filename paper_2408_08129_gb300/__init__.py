@@ -8,7 +8,9 @@ without the built library raises ImportError: there is no CPU fallback.
 from .api import (  # noqa: F401
     DG_FP32,
     DG_FP64,
+    DG_KRYLOV_AUTO,
     DG_KRYLOV_CG,
+    DG_KRYLOV_CHEBYSHEV,
     DG_KRYLOV_GMRES,
     DG_KRYLOV_GMRES_CGS2,
     DG_TERMS_FULL,

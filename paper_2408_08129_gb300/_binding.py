@@ -17,7 +17,7 @@ DG_STATUS = {
     -5: "DG_ENONFINITE", -6: "DG_EUNBALANCED", -7: "DG_EBUDGET", -8: "DG_ETIMEOUT",
 }
 DG_FP64, DG_FP32 = 0, 1
-DG_KRYLOV_GMRES, DG_KRYLOV_CG, DG_KRYLOV_GMRES_CGS2 = 0, 1, 2
+DG_KRYLOV_AUTO, DG_KRYLOV_GMRES, DG_KRYLOV_CG, DG_KRYLOV_GMRES_CGS2, DG_KRYLOV_CHEBYSHEV = -1, 0, 1, 2, 3
 DG_TERMS_FULL, DG_TERMS_IMEX_EXPLICIT = 0, 1
 DG_HILL = {"none": 0, "gauss": 1, "bell": 2, "parabola": 3}
 DG_ATM = {"none": 0, "isothermal": 1, "stratified": 2}
@@ -44,7 +44,7 @@ class MeshInfo(ctypes.Structure):
         ("n_cells", c_int64), ("n_nodes", c_int64), ("n_dof", c_int64),
         ("n_conforming", c_int64), ("n_subfaces", c_int64), ("n_walls", c_int64),
         ("max_level", c_int), ("min_edge", c_double), ("device_bytes", ctypes.c_size_t),
-        ("solver_form", c_int * 2), ("solver_ms", (ctypes.c_float * 2) * 2),
+        ("solver_form", c_int * 2), ("solver_ms", (ctypes.c_float * 3) * 2),
     ]
 
 
@@ -121,6 +121,7 @@ def _load():
         "dg_state_data": (P, [P]),
         "dg_state_upload": (c_int, [P, P]),
         "dg_state_download": (c_int, [P, P]),
+        "dg_state_chebyshev_bound": (c_int, [P, P, P]),
         "imex_rk2_step": (c_int, [P, P, P, c_double, ctypes.POINTER(SolverOpts), ctypes.POINTER(StepStats), P]),
         "dg_batch_step": (c_int, [P, c_int, P, P, P, ctypes.POINTER(SolverOpts), P, P, P]),
         "dg_batch_plan_create": (c_int, [P, c_int, P, P, P, ctypes.POINTER(SolverOpts), ctypes.POINTER(P)]),

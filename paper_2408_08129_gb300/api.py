@@ -12,7 +12,8 @@ import torch
 
 from . import _binding as B
 from ._binding import (  # noqa: F401
-    DG_ATM, DG_FP32, DG_FP64, DG_HILL, DG_INIT, DG_KRYLOV_CG, DG_KRYLOV_GMRES, DG_KRYLOV_GMRES_CGS2, DG_TERMS_FULL,
+    DG_ATM, DG_FP32, DG_FP64, DG_HILL, DG_INIT, DG_KRYLOV_AUTO, DG_KRYLOV_CG, DG_KRYLOV_CHEBYSHEV, DG_KRYLOV_GMRES, DG_KRYLOV_GMRES_CGS2,
+    DG_TERMS_FULL,
     DG_TERMS_IMEX_EXPLICIT, DGError, check, lib,
 )
 
@@ -126,9 +127,10 @@ class Mesh:
         """Autotuner outcome: per precision, the chosen Helmholtz solver form and the timed solves (ms)."""
         info = B.MeshInfo()
         check(lib.dg_mesh_get_info(self.handle, ctypes.byref(info)), "dg_mesh_get_info")
-        forms = {1: "persistent", 0: "multi-kernel", -1: None}
-        return {p: {"form": forms[info.solver_form[i]], "ms_multi_kernel": info.solver_ms[i][0],
-                    "ms_persistent": info.solver_ms[i][1]} for i, p in enumerate(("fp64", "fp32"))}
+        forms = {0: "gmres_multi_kernel", 1: "gmres_persistent", 2: "chebyshev", -1: None}
+        return {p: {"form": forms[info.solver_form[i]],
+                    "ms": {forms[f]: info.solver_ms[i][f] for f in range(3) if info.solver_ms[i][f] > 0}}
+                for i, p in enumerate(("fp64", "fp32"))}
 
     def faces(self):
         i = self.info
@@ -284,6 +286,14 @@ class State:
         a = np.zeros(self.mesh.shape())
         check(lib.dg_state_download(self.handle, a.ctypes.data), "dg_state_download")
         return a
+
+    def chebyshev_bound(self, set_to=None):
+        """(lmax, alpha) the state's Chebyshev solves use; set_to=(lmax, alpha) replaces it first."""
+        get = np.zeros(2)
+        st = None if set_to is None else np.asarray(set_to, dtype=np.float64)
+        check(lib.dg_state_chebyshev_bound(self.handle, get.ctypes.data,
+                                           None if st is None else st.ctypes.data), "dg_state_chebyshev_bound")
+        return (float(get[0]), float(get[1])) if set_to is None else self.chebyshev_bound()
 
     def close(self):
         if self.handle:

@@ -154,8 +154,9 @@ struct dg_mesh {
   double* d_face_scratch64 = nullptr;
   double* d_vec_scratch64 = nullptr;  // [dim][Nn]
   double* d_red_scratch = nullptr;    // [2*512] block partials of the conservation sums
-  // autotuned Helmholtz solver per precision (-1 = not tuned yet, 0 = one launch
-  // per Krylov kernel, 1 = persistent single-launch solve), chosen by timing
-  mutable int tuned_fused[2] = {-1, -1};
-  mutable float tuned_ms[2][2] = {{0, 0}, {0, 0}};
+  // autotuned Helmholtz solver per precision: the timed first solve of each
+  // form (0 = GMRES, one launch per Krylov kernel; 1 = GMRES persistent;
+  // 2 = Chebyshev persistent; 0 ms = not timed) and the form chosen last
+  mutable int tuned_form[2] = {-1, -1};
+  mutable float tuned_ms[2][3] = {{0, 0, 0}, {0, 0, 0}};
 };

@@ -526,8 +526,8 @@ extern "C" int dg_mesh_get_info(const dg_mesh* m, dg_mesh_info* info) {
   info->min_edge = m->min_edge;
   info->device_bytes = m->device_bytes;
   for (int p = 0; p < 2; ++p) {
-    info->solver_form[p] = m->tuned_fused[p];
-    for (int f = 0; f < 2; ++f) info->solver_ms[p][f] = m->tuned_ms[p][f];
+    info->solver_form[p] = m->tuned_form[p];
+    for (int f = 0; f < 3; ++f) info->solver_ms[p][f] = m->tuned_ms[p][f];
   }
   return DG_OK;
 }

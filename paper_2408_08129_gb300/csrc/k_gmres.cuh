@@ -59,7 +59,9 @@ struct GmresPArgs {
   int max_iters;
   int64_t n;
   int method;  // 0: GMRES(m), one reduction per step; 1: conjugate gradients in the M inner
-              // product (needs m >= 2); 2: GMRES(m) with classical Gram-Schmidt twice per step
+              // product (needs m >= 2); 2: GMRES(m) with classical Gram-Schmidt twice per step;
+              // 3: Chebyshev iteration on [1/(gamma-1), lmax] (needs m >= 1)
+  double* lmax;  // [2] device: Chebyshev upper bound (0 = not estimated yet) and the alpha it belongs to
 };
 
 enum GmresPhase {
@@ -138,16 +140,65 @@ struct SubSync {
   __device__ __forceinline__ bool failed() const { return *(volatile int*)sfail != 0; }
 };
 
+// On this part an FP64 instruction costs a whole warp issue slot on a pipe
+// with a few lanes per SM, so a chain of FP64 operations in one thread is
+// slow: every reduction below is a shuffle tree over the lanes (fixed order,
+// so the sums are bitwise reproducible), never a serial loop.
+
+// sum over the lanes of the values of warp 0 at lanes < cnt (<= 32); the result in lane 0
+__device__ __forceinline__ double warp0_tree(double r, int cnt) {
+  int top = 1;
+  while (top < cnt) top <<= 1;
+  for (int o = top >> 1; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  return r;
+}
+
+// FP64 sum over the block; the result in thread 0
 __device__ __forceinline__ double block_sum(double v, double* sred) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int nw = (int)(blockDim.x + 31) >> 5;
   __syncthreads();
   if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
   __syncthreads();
   double r = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sred[i];
+  if (threadIdx.x < 32) r = warp0_tree(threadIdx.x < nw ? sred[threadIdx.x] : 0.0, nw);
   return r;
+}
+
+// FP64 sum over the block, returned to every thread
+__device__ __forceinline__ double block_allsum(double v, double* sred) {
+  const double r = block_sum(v, sred);
+  if (threadIdx.x == 0) sred[0] = r;
+  __syncthreads();
+  return sred[0];
+}
+
+// sum of cnt partial sums in global memory (written by the CTAs before the
+// last barrier), returned to every thread of the block
+__device__ __forceinline__ double gather_allsum(const double* part, int cnt, double* sred) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) v += part[i];
+  return block_allsum(v, sred);
+}
+
+// the same for the strided sub-array part[off], part[off + stride], ... (cnt entries)
+__device__ __forceinline__ double gather_allsum_strided(const double* part, int cnt, int stride, int off,
+                                                        double* sred) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) v += part[(int64_t)i * stride + off];
+  return block_allsum(v, sred);
+}
+
+// 1/sqrt(x) for finite x > 0 in the FP32 range, in FP64: FP32 seed (relative
+// error ~1e-7), then two Newton steps y <- y (3 - x y^2) / 2, each of which
+// squares the relative error (1e-7 -> 1e-14 -> below FP64 rounding)
+__device__ __forceinline__ double rsqrt64(double x) {
+  double y = (double)rsqrtf((float)x);
+  const double hx = 0.5 * x;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) y = y * fma(-hx, y * y, 1.5);
+  return y;
 }
 
 // copy cnt global partial sums (no more than the staging area holds) into
@@ -158,26 +209,38 @@ __device__ __forceinline__ void stage_partials(const double* partial, int cnt, d
   __syncthreads();
 }
 
-// warp-level sum in TK, then FP64 across warps
+// warp-level sum in TK, then FP64 across warps; the result in thread 0
 template <typename TK>
 __device__ __forceinline__ double block_sum_k(TK v, double* sred) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int nw = (int)(blockDim.x + 31) >> 5;
   __syncthreads();
   if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = (double)v;
   __syncthreads();
   double r = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sred[i];
+  if (threadIdx.x < 32) r = warp0_tree(threadIdx.x < nw ? sred[threadIdx.x] : 0.0, nw);
   return r;
 }
 
-// out = scale * (ident p/(gamma-1) - alpha div(h grad p)) (two phases, two grid barriers;
-// the face terms are computed inside the cell passes)
-template <int DIM, int DEG, typename T, class Sync>
-__device__ __forceinline__ void pmatvec(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p, T scale,
-                                        T* out, T* gv, Sync& sg, T* scell, T* sJ, const T* sD, const T* sDw,
-                                        const T* sII, PhaseClock& pc) {
+// Stores the mat-vec result (the default epilogue of pmatvec).
+template <typename T>
+struct StoreEpi {
+  T* out;
+  __device__ __forceinline__ void operator()(int64_t i, T v) const { out[i] = v; }
+};
+struct NoFin {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// scale * (ident p/(gamma-1) - alpha div(h grad p)) (two phases, two grid
+// barriers; the face terms are computed inside the cell passes), handed node
+// by node to epi(i, value); fin() runs on every thread of every CTA after its
+// last divergence batch, before the closing barrier.
+template <int DIM, int DEG, typename T, class Sync, class Epi, class Fin>
+__device__ __forceinline__ void pmatvec_epi(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p,
+                                            T scale, Epi& epi, Fin& fin, T* gv, Sync& sg, T* scell, T* sJ,
+                                            const T* sD, const T* sDw, const T* sII, PhaseClock& pc) {
   using S = Shape<DIM, DEG>;
   const int64_t nb = (mv.n_cells + S::CPB - 1) / S::CPB;
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
@@ -185,9 +248,20 @@ __device__ __forceinline__ void pmatvec(const MeshView<T>& mv, const T* h, T alp
   sg.sync();
   pc.mark(PH_GRAD_CELL);
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-    div_cell_batch<DIM, DEG, T, true>(mv, gv, p, alpha, scale, ident, out, bt, scell, sJ, sDw, sII);
+    div_cell_batch<DIM, DEG, T, true, Epi>(mv, gv, p, alpha, scale, ident, epi, bt, scell, sJ, sDw, sII);
+  fin();
   sg.sync();
   pc.mark(PH_DIV_CELL);
+}
+
+// out = scale * (ident p/(gamma-1) - alpha div(h grad p))
+template <int DIM, int DEG, typename T, class Sync>
+__device__ __forceinline__ void pmatvec(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p, T scale,
+                                        T* out, T* gv, Sync& sg, T* scell, T* sJ, const T* sD, const T* sDw,
+                                        const T* sII, PhaseClock& pc) {
+  StoreEpi<T> epi{out};
+  NoFin fin;
+  pmatvec_epi<DIM, DEG, T, Sync>(mv, h, alpha, ident, p, scale, epi, fin, gv, sg, scell, sJ, sD, sDw, sII, pc);
 }
 
 // partial[j*C + c] = sum over chunk c of v_j . w for j < nv, where v_j = Q_j for
@@ -404,14 +478,7 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
     if (threadIdx.x == 0) a.partial[sg.rank] = s;
   }
   sg.sync();
-  stage_partials(a.partial, G, spart);
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < G; ++i) s += spart[i];
-    sc[0] = sqrt(s);
-  }
-  __syncthreads();
-  const double bn = sc[0];
+  const double bn = sqrt(gather_allsum(a.partial, G, sred));
   if (bn == 0.0) {
     for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
     if (sg.rank == 0 && threadIdx.x == 0) {
@@ -445,24 +512,20 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
     }
     sg.sync();
     pc.mark(PH_RESIDUAL);
-    stage_partials(a.partial, G, spart);
+    const double beta = sqrt(gather_allsum(a.partial, G, sred));
     if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int i = 0; i < G; ++i) s += spart[i];
-      const double beta = sqrt(s);
-      sc[2] = beta;
       sflag[1] = (beta <= a.tol * bn) ? 1 : 0;
       sflag[0] = 0;
     }
     __syncthreads();
-    rel = sc[2] / bn;
+    rel = beta / bn;
     if (sg.failed()) break;
     if (sflag[1]) {
       converged = true;
       break;
     }
     if (total >= a.max_iters) break;
-    const double cycle_floor = fmax(a.tol * bn, (mixed ? a.inner_tol : 0.0) * sc[2]);
+    const double cycle_floor = fmax(a.tol * bn, (mixed ? a.inner_tol : 0.0) * beta);
     int kd = 0;
     for (int k = 0; k <= m; ++k) {
       TK* uk = a.Q + (int64_t)k * n;
@@ -478,62 +541,109 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
       sg.sync();
       pc.mark(PH_DOTS);
       if (sg.failed()) break;
-      stage_partials(a.partial, 2 * nv * C, spart);
-      if (threadIdx.x < nv) {
-        double su = 0.0, sw = 0.0;
-        for (int c = 0; c < C; ++c) {
-          su += spart[2 * (threadIdx.x * C + c)];
-          sw += spart[2 * (threadIdx.x * C + c) + 1];
+      // sums of the chunk partials: warp w takes the pairs p = w, w + 8, ... (a_j for even
+      // p, b_j for odd), its lanes split the chunks (all loads issued first), and a
+      // shuffle tree adds them
+      {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+        constexpr int PG = 4;  // pairs per warp whose loads are in flight together
+        for (int q0 = 0; warp + q0 * nw < 2 * nv; q0 += PG) {
+          double v[PG];
+#pragma unroll
+          for (int q = 0; q < PG; ++q) {
+            const int pr = warp + (q0 + q) * nw;
+            v[q] = 0.0;
+            if (pr < 2 * nv)
+              for (int c = lane; c < C; c += 32) v[q] += a.partial[2 * ((pr >> 1) * C + c) + (pr & 1)];
+          }
+#pragma unroll
+          for (int q = 0; q < PG; ++q) {
+            const int pr = warp + (q0 + q) * nw;
+            if (pr < 2 * nv) {  // warp-uniform
+              double t = v[q];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+              if (lane == 0) (pr & 1 ? bv : av)[pr >> 1] = t;
+            }
+          }
         }
-        av[threadIdx.x] = su;
-        bv[threadIdx.x] = sw;
       }
       __syncthreads();
       pc.mark(PH_SUMS);
-      // 3. rho, column k-1 with its Givens rotation, stop test
-      if (threadIdx.x == 0) {
-        double ss = 0.0;
-        for (int j = 0; j < k; ++j) ss += av[j] * av[j];
-        const double uu = av[k];
-        const double rho2 = uu - ss;
-        // breakdown (u_k in the span of Q_k to working precision) ends the cycle
-        const double rho = (rho2 > 1e-24 * uu && rho2 > 0.0) ? sqrt(rho2) : 0.0;
-        sc[3] = rho;
-        int stop = 0;
-        if (k == 0) {
-          gg[0] = rho;
-          for (int j = 1; j <= m; ++j) gg[j] = 0.0;
-          if (rho == 0.0) stop = 1;
-        } else {
-          double* hb = Hb + (int64_t)(k - 1) * (m + 1);
-          double* col = R + (int64_t)(k - 1) * (m + 1);
-          for (int j = 0; j < k; ++j) {
-            hb[j] = hf[j] + av[j];
-            col[j] = hb[j];
-          }
-          hb[k] = rho;
-          col[k - 1] += shift;
-          col[k] = rho;
-          for (int j = 0; j < k - 1; ++j) {
-            const double t = cs[j] * col[j] + sn[j] * col[j + 1];
-            col[j + 1] = -sn[j] * col[j] + cs[j] * col[j + 1];
-            col[j] = t;
-          }
-          const double den = hypot(col[k - 1], col[k]);
-          const double c = den > 0.0 ? col[k - 1] / den : 1.0;
-          const double sgn = den > 0.0 ? col[k] / den : 0.0;
-          cs[k - 1] = c;
-          sn[k - 1] = sgn;
-          col[k - 1] = den;
-          col[k] = 0.0;
-          gg[k] = -sgn * gg[k - 1];
-          gg[k - 1] = c * gg[k - 1];
-          const double resid = fabs(gg[k]);
-          sc[1] = resid;
-          sflag[1] = resid <= a.tol * bn ? 1 : 0;
-          stop = (resid <= cycle_floor || rho == 0.0 || total + 1 >= a.max_iters || k == m) ? 1 : 0;
+      // 3. warp 0: |a|^2 and a.b by lanes, the new column hf + a (+ shift on the diagonal)
+      // by lanes, the products cs_j col_{j+1} of the earlier rotations by lanes; then lane 0
+      // runs the rotation chain x_{j+1} = cs_j col_{j+1} - sn_j x_j (one FMA per link), the
+      // new rotation and the stop test.  Threads 32..32+k-1 meanwhile form z = H a, taking
+      // the new column as hf + a directly.
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double s1 = 0.0, s2 = 0.0;
+        for (int j = lane; j < k; j += 32) {
+          s1 += av[j] * av[j];
+          s2 += av[j] * bv[j];
         }
-        sflag[0] = stop;
+        s1 = warp0_tree(s1, 32);
+        s2 = warp0_tree(s2, 32);
+        double* hb = Hb + (int64_t)(k > 0 ? k - 1 : 0) * (m + 1);
+        double* col = R + (int64_t)(k > 0 ? k - 1 : 0) * (m + 1);
+        if (k > 0) {
+          for (int j = lane; j < k; j += 32) {
+            const double hj = hf[j] + av[j];
+            hb[j] = hj;
+            col[j] = hj + (j == k - 1 ? shift : 0.0);
+          }
+          __syncwarp();
+          for (int j = lane; j < k - 1; j += 32) y[j] = cs[j] * col[j + 1];  // y: scratch until the cycle ends
+          __syncwarp();
+        }
+        if (lane == 0) {
+          const double uu = av[k];
+          const double rho2 = uu - s1;
+          // breakdown (u_k in the span of Q_k to working precision) ends the cycle
+          const bool ok = rho2 > 1e-24 * uu && rho2 > 0.0;
+          const double irho = ok ? rsqrt64(rho2) : 0.0;
+          const double rho = ok ? rho2 * irho : 0.0;
+          sc[3] = rho;
+          sc[5] = irho;
+          sc[6] = s2;
+          int stop = 0;
+          if (k == 0) {
+            gg[0] = rho;
+            for (int j = 1; j <= m; ++j) gg[j] = 0.0;
+            if (!ok) stop = 1;
+          } else {
+            hb[k] = rho;
+            // chain: x_0 = col_0, x_{j+1} = cs_j col_{j+1} - sn_j x_j; the rotated entries
+            // R_j = cs_j x_j + sn_j col_{j+1} are written back off the chain
+            double x = col[0];
+            for (int j = 0; j < k - 1; ++j) {
+              const double xn = fma(-sn[j], x, y[j]);
+              col[j] = fma(cs[j], x, sn[j] * col[j + 1]);
+              x = xn;
+            }
+            const double x1 = rho;
+            const double r2 = x * x + x1 * x1;
+            const double ir = r2 > 0.0 ? rsqrt64(r2) : 0.0;
+            const double c = r2 > 0.0 ? x * ir : 1.0;
+            const double sgn = r2 > 0.0 ? x1 * ir : 0.0;
+            cs[k - 1] = c;
+            sn[k - 1] = sgn;
+            col[k - 1] = r2 * ir;
+            col[k] = 0.0;
+            gg[k] = -sgn * gg[k - 1];
+            gg[k - 1] = c * gg[k - 1];
+            const double resid = fabs(gg[k]);
+            sc[1] = resid;
+            sflag[1] = resid <= a.tol * bn ? 1 : 0;
+            stop = (resid <= cycle_floor || !ok || total + 1 >= a.max_iters || k == m) ? 1 : 0;
+          }
+          sflag[0] = stop;
+        }
+      } else if ((int)threadIdx.x < 32 + k) {
+        const int i = threadIdx.x - 32;
+        double z = (hf[i] + av[i]) * av[k - 1];
+        for (int j = (i > 0 ? i - 1 : 0); j < k - 1; ++j) z += Hb[(int64_t)j * (m + 1) + i] * av[j];
+        zc[i] = z;
       }
       __syncthreads();
       pc.mark(PH_GIVENS);
@@ -543,42 +653,31 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
       }
       kd = k;
       if (sflag[0]) break;
-      const double rho = sc[3];
-      // z = H a over the completed columns 0..k-1 (z_k = rho a_{k-1})
-      if (threadIdx.x <= k) {
+      // first pass of column k and the weights of u_{k+1}; every thread forms the scalars
+      const double irho = sc[5];
+      const double zk = k > 0 ? sc[3] * av[k - 1] : 0.0;
+      const double hk = ((bv[k] - sc[6]) * irho - zk) * irho;
+      const double cu = (zk * irho + hk) * irho;
+      if ((int)threadIdx.x < k) {
         const int i = threadIdx.x;
-        double z = 0.0;
-        for (int j = (i > 0 ? i - 1 : 0); j < k; ++j) z += Hb[(int64_t)j * (m + 1) + i] * av[j];
-        zc[i] = z;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double ab = 0.0;
-        for (int j = 0; j < k; ++j) ab += av[j] * bv[j];
-        const double hk = ((bv[k] - ab) / rho - zc[k]) / rho;
-        hf[k] = hk;
-        sc[4] = (zc[k] / rho + hk) / rho;
-      }
-      __syncthreads();
-      const double cu = sc[4];
-      if (threadIdx.x < k) {
-        const int i = threadIdx.x;
-        const double h = (bv[i] - zc[i]) / rho;
+        const double h = (bv[i] - zc[i]) * irho;
         hf[i] = h;
-        dv[i] = zc[i] / rho + h - cu * av[i];
+        dv[i] = zc[i] * irho + h - cu * av[i];
+      } else if ((int)threadIdx.x == k) {
+        hf[k] = hk;
       }
       __syncthreads();
       pc.mark(PH_COEFS);
       // 4. q_k = (u_k - Q_k a)/rho and u_{k+1} = v/rho - c u_k - Q_k d, one pass
       {
-        const TK irho = (TK)(1.0 / rho), cuk = (TK)cu;
+        const TK irk = (TK)irho, cuk = (TK)cu;
         TK* un = a.Q + (int64_t)(k + 1) * n;
         for (int64_t i = tid; i < n; i += gstride) {
           const TK u = uk[i], v = a.w[i];
           TK sa, sd;
           lincomb2(a.Q, n, i, av, dv, k, sa, sd);
-          uk[i] = (u - sa) * irho;
-          un[i] = v * irho - cuk * u - sd;
+          uk[i] = (u - sa) * irk;
+          un[i] = v * irk - cuk * u - sd;
         }
       }
       pc.mark(PH_LINCOMB);
@@ -668,14 +767,7 @@ __device__ __forceinline__ void gmres_cgs2_body(const GmresPArgs<TK>& a, Sync& s
     if (threadIdx.x == 0) a.partial[sg.rank] = s;
   }
   sg.sync();
-  stage_partials(a.partial, G, spart);
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < G; ++i) s += spart[i];
-    sc[0] = sqrt(s);
-  }
-  __syncthreads();
-  const double bn = sc[0];
+  const double bn = sqrt(gather_allsum(a.partial, G, sred));
   if (bn == 0.0) {
     for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
     if (sg.rank == 0 && threadIdx.x == 0) {
@@ -709,11 +801,8 @@ __device__ __forceinline__ void gmres_cgs2_body(const GmresPArgs<TK>& a, Sync& s
     }
     sg.sync();
     pc.mark(PH_RESIDUAL);
-    stage_partials(a.partial, G, spart);
+    const double beta = sqrt(gather_allsum(a.partial, G, sred));
     if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int i = 0; i < G; ++i) s += spart[i];
-      const double beta = sqrt(s);
       sc[2] = beta;
       sflag[1] = (beta <= a.tol * bn) ? 1 : 0;
       sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
@@ -916,14 +1005,7 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
     if (threadIdx.x == 0) a.partial[sg.rank] = t;
   }
   sg.sync();
-  stage_partials(a.partial, G, spart);
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < G; ++i) t += spart[i];
-    sc[0] = sqrt(t);
-  }
-  __syncthreads();
-  const double bn = sc[0];
+  const double bn = sqrt(gather_allsum(a.partial, G, sred));
   if (bn == 0.0) {
     for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
     if (sg.rank == 0 && threadIdx.x == 0) {
@@ -954,14 +1036,7 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
     }
     sg.sync();
     pc.mark(PH_RESIDUAL);
-    stage_partials(a.partial, G, spart);
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < G; ++i) t += spart[i];
-      sc[1] = sqrt(t);
-    }
-    __syncthreads();
-    const double beta0 = sc[1];
+    const double beta0 = sqrt(gather_allsum(a.partial, G, sred));
     rel = beta0 / bn;
     if (sg.failed()) break;
     if (beta0 <= a.tol * bn) {
@@ -994,20 +1069,9 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
       }
       sg.sync();
       pc.mark(PH_DOTS);
-      stage_partials(a.partial, 3 * G, spart);
-      if (threadIdx.x == 0) {
-        double tg = 0.0, td = 0.0, te = 0.0;
-        for (int i = 0; i < G; ++i) {
-          tg += spart[3 * i];
-          td += spart[3 * i + 1];
-          te += spart[3 * i + 2];
-        }
-        sc[2] = tg;
-        sc[3] = td;
-        sc[4] = sqrt(te);
-      }
-      __syncthreads();
-      const double gnew = sc[2], delta = sc[3], rn = sc[4];
+      const double gnew = gather_allsum_strided(a.partial, G, 3, 0, sred);
+      const double delta = gather_allsum_strided(a.partial, G, 3, 1, sred);
+      const double rn = sqrt(gather_allsum_strided(a.partial, G, 3, 2, sred));
       ++total;
       rel = rn / bn;
       if (sg.failed() || rn <= floor || total >= a.max_iters || !(delta > 0.0) || !(gnew > 0.0)) break;
@@ -1048,6 +1112,235 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
   }
 }
 
+// Chebyshev iteration on the Helmholtz system.  A is self-adjoint in the w J
+// inner product and A >= I/(gamma-1) (the operator -div h grad is positive
+// semi-definite there, with the constants in its null space), so its
+// spectrum is real and lies in [1/(gamma-1), lmax].  With these bounds the
+// Chebyshev recurrence (Saad, Iterative Methods for Sparse Linear Systems,
+// Alg. 12.1) needs no inner product: one step is one mat-vec whose epilogue
+// updates x, r and the direction in the same pass, two grid barriers in all;
+// the residual norm for the stopping test comes from block partial sums read
+// after the barrier.  lmax is estimated in the kernel by power iteration in the
+// w J norm (the ratio ||A p|| / ||p|| approaches lmax from below), widened by
+// kLmaxMargin, and kept in a.lmax for later solves with the same alpha.  If
+// the residual grows (an estimate too low), the bound is cleared and the solve
+// finishes with GMRES from the current iterate.  The FP64 residual is
+// recomputed at every restart; TK = float restarts whenever the residual has
+// dropped by inner_tol (iterative refinement).
+constexpr int kPowerIters = 24;
+constexpr double kLmaxMargin = 1.05;
+
+template <int DIM, int DEG, typename TK, class Sync>
+__device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw, bool record) {
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N;
+  double* sred = (double*)smem_raw;  // [32]
+  double* sc = sred + 32;            // [16]
+  double* spart = sc + 16;           // [512]
+  double* sD64 = spart + 3 * 512;
+  double* sDw64 = sD64 + N * N;
+  double* sII64 = sDw64 + N * N;
+  double* scell64 = sII64 + 4 * N * N;
+  double* sJ64 = scell64 + S::CPB * S::NC;
+  TK* sDk = (TK*)(sJ64 + coarse_buffer<DIM, DEG, DIM>());
+  TK* sDwk = sDk + N * N;
+  TK* sIIk = sDwk + N * N;
+  TK* scellk = (TK*)scell64;
+  TK* sJk = (TK*)sJ64;
+  load_tables<DIM, DEG, TK>(a, sD64, sDw64, sII64, sDk, sDwk, sIIk);
+  PhaseClock pc{record ? a.phase : nullptr, PhaseClock::now()};
+  const int64_t n = a.n;
+  const int G = sg.size;
+  const int64_t tid = (int64_t)sg.rank * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)G * blockDim.x;
+  const int64_t chunk1 = (n + G - 1) / G;
+  const int64_t lo = (int64_t)sg.rank * chunk1;
+  const int64_t hi = lo + chunk1 < n ? lo + chunk1 : n;
+  const bool mixed = sizeof(TK) != sizeof(double);
+  TK* r = a.Q;          // residual (recurrence)
+  TK* d = a.Q + n;      // direction
+  TK* w = a.w;          // power-iteration partner
+  const TK* wJ = a.mvk.wJ;
+  TK* gvk = (TK*)a.gv;
+  // sum of the G block partials, the same in every CTA
+  auto gather_sum = [&]() -> double { return gather_allsum(a.partial, G, sred); };
+
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += a.b[i] * a.b[i];
+  {
+    const double t = block_sum(acc, sred);
+    if (threadIdx.x == 0) a.partial[sg.rank] = t;
+  }
+  sg.sync();
+  const double bn = sqrt(gather_sum());
+  if (bn == 0.0) {
+    for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
+    if (sg.rank == 0 && threadIdx.x == 0) {
+      a.out[0] = 0;
+      a.out[1] = 0;
+      a.out[2] = 1;
+      a.out[3] = 0;
+    }
+    return;
+  }
+  sg.sync();  // partial reused below
+
+  // upper spectral bound: stored, or estimated here by power iteration
+  const double lmin = 1.0 / (kGamma - 1.0);
+  double lmax = a.lmax[0];
+  if (!(lmax > lmin) || fabs(a.lmax[1] - a.alpha) > 1e-12 * a.alpha) {
+    // deterministic start vector with every mode present; TK buffers r (p) and w
+    acc = 0.0;
+    for (int64_t i = tid; i < n; i += gstride) {
+      unsigned int hsh = (unsigned int)i * 2654435761u + 0x9e3779b9u;
+      hsh ^= hsh >> 16;
+      hsh *= 0x85ebca6bu;
+      hsh ^= hsh >> 13;
+      const TK v = (TK)((double)(hsh & 0xffffffu) / 8388608.0 - 1.0);
+      r[i] = v;
+      acc += (double)wJ[i] * (double)v * (double)v;
+    }
+    {
+      const double t = block_sum(acc, sred);
+      if (threadIdx.x == 0) a.partial[sg.rank] = t;
+    }
+    sg.sync();
+    double inv = 1.0 / sqrt(gather_sum());
+    TK* pin = r;
+    TK* pout = w;
+    double est = 0.0;
+    for (int it = 0; it < kPowerIters; ++it) {
+      double nacc = 0.0;
+      auto epi = [&](int64_t i, TK v) {
+        pout[i] = v;
+        nacc += (double)wJ[i] * (double)v * (double)v;
+      };
+      auto fin = [&]() {
+        const double t = block_sum(nacc, sred);
+        if (threadIdx.x == 0) a.partial[sg.rank] = t;
+      };
+      pmatvec_epi<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(1), pin, (TK)inv, epi, fin, gvk, sg, scellk, sJk,
+                                      sDk, sDwk, sIIk, pc);
+      est = sqrt(gather_sum());  // ||A p^|| with ||p^|| = 1 in the w J norm
+      inv = est > 0.0 ? 1.0 / est : 0.0;
+      TK* t = pin;
+      pin = pout;
+      pout = t;
+      if (sg.failed()) break;
+    }
+    lmax = kLmaxMargin * est;
+    if (!(lmax > lmin)) lmax = 2.0 * lmin;
+    if (sg.rank == 0 && threadIdx.x == 0) {
+      a.lmax[0] = lmax;
+      a.lmax[1] = a.alpha;
+    }
+  }
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma1 = theta / delta;
+
+  int total = 0;
+  double rel = 1.0;
+  bool converged = false, diverged = false;
+  while (!sg.failed()) {
+    // FP64 residual r = b - A x; d = r / theta in the same pass
+    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.gv, sg, scell64, sJ64, sD64,
+                                    sDw64, sII64, pc);
+    acc = 0.0;
+    const TK ith = (TK)(1.0 / theta);
+    for (int64_t i = tid; i < n; i += gstride) {
+      const double ri = a.b[i] - a.w64[i];
+      r[i] = (TK)ri;
+      d[i] = (TK)ri * ith;
+      acc += ri * ri;
+    }
+    {
+      const double t = block_sum(acc, sred);
+      if (threadIdx.x == 0) a.partial[sg.rank] = t;
+    }
+    sg.sync();
+    pc.mark(PH_RESIDUAL);
+    const double beta = sqrt(gather_sum());
+    rel = beta / bn;
+    if (beta <= a.tol * bn) {
+      converged = true;
+      break;
+    }
+    if (total >= a.max_iters) break;
+    const double floor = fmax(a.tol * bn, (mixed ? a.inner_tol : 0.0) * beta);
+    // steps the Chebyshev bound 2 q^k (q = (sqrt(kappa)-1)/(sqrt(kappa)+1)) needs to reach the
+    // floor; well past that, the residual has stalled or grows slowly (a bound a little low)
+    const double sk = sqrt(lmax / lmin), q = (sk - 1.0) / (sk + 1.0);
+    const int cycle_cap = 2 * (int)ceil(log(0.5 * floor / beta) / log(q)) + 20;
+    int cycle_its = 0;
+    double rho = 1.0 / sigma1;
+    const int64_t nb = (a.mvk.n_cells + S::CPB - 1) / S::CPB;
+    bool have_prev = false;  // residual partials of the previous step are waiting in a.partial
+    while (true) {
+      // gradient pass of A d_k; the previous step's residual norm is summed meanwhile
+      // (its partial loads are issued before the pass, the sum after it)
+      double pv = 0.0;
+      if (have_prev)
+        for (int i = threadIdx.x; i < G; i += blockDim.x) pv += a.partial[i];
+      for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
+        grad_cell_batch<DIM, DEG, TK>(a.mvk, d, a.hk, gvk, bt, scellk, sJk, sDk, sIIk);
+      if (have_prev) {
+        const double rn = sqrt(block_allsum(pv, sred));
+        pc.mark(PH_UPDATE);
+        if (!(rn <= 1e4 * beta) || (cycle_its > cycle_cap && rn > floor)) {  // growth, stall or NaN: bound too low
+          diverged = true;
+          break;
+        }
+        if (rn <= floor || total >= a.max_iters || sg.failed()) break;  // same decision in every CTA
+      }
+      sg.sync();
+      pc.mark(PH_GRAD_CELL);
+      // divergence pass with the update: x += d, r -= A d, d = c1 d + c2 r
+      const double rho1 = 1.0 / (2.0 * sigma1 - rho);
+      const TK c1 = (TK)(rho1 * rho), c2 = (TK)(2.0 * rho1 / delta);
+      double racc = 0.0;
+      auto epi = [&](int64_t i, TK ad) {
+        const TK di = d[i];
+        const TK ri = r[i] - ad;
+        r[i] = ri;
+        a.x[i] += (double)di;
+        d[i] = c1 * di + c2 * ri;
+        racc += (double)ri * (double)ri;
+      };
+      for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
+        div_cell_batch<DIM, DEG, TK, true>(a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi, bt, scellk, sJk, sDwk,
+                                           sIIk);
+      {
+        const double t = block_sum(racc, sred);
+        if (threadIdx.x == 0) a.partial[sg.rank] = t;
+      }
+      sg.sync();
+      pc.mark(PH_DIV_CELL);
+      rho = rho1;
+      ++total;
+      ++cycle_its;
+      have_prev = true;
+    }
+    // CTAs may leave the loop inside a gradient pass (whose scratch aliases the
+    // FP64 residual's): meet before the next pass
+    sg.sync();
+    if (diverged || total >= a.max_iters) break;
+  }
+  if (diverged) {
+    if (sg.rank == 0 && threadIdx.x == 0) a.lmax[0] = 0.0;  // re-estimate on the next solve
+    sg.sync();
+    gmres_body<DIM, DEG, TK, Sync>(a, sg, smem_raw, record);
+    if (sg.rank == 0 && threadIdx.x == 0) a.out[0] += total;
+    return;
+  }
+  if (sg.rank == 0 && threadIdx.x == 0) {
+    a.out[0] = total;
+    a.out[1] = rel;
+    a.out[2] = (converged && !sg.failed()) ? 1.0 : 0.0;
+    a.out[3] = bn;
+    if (pc.acc) a.phase[PH_ITERS] += (unsigned long long)total;
+  }
+}
+
 template <int DIM, int DEG, typename TK>
 __global__ void __launch_bounds__(256, 2) gmres_persistent_kernel(GmresPArgs<TK> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1056,6 +1349,8 @@ __global__ void __launch_bounds__(256, 2) gmres_persistent_kernel(GmresPArgs<TK>
     cg_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
   else if (a.method == 2)
     gmres_cgs2_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
+  else if (a.method == 3)
+    cheb_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
   else
     gmres_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
 }
@@ -1086,6 +1381,8 @@ __global__ void __launch_bounds__(256, 2) gmres_batched_kernel(const GmresPArgs<
     cg_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
   else if (a.method == 2)
     gmres_cgs2_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
+  else if (a.method == 3)
+    cheb_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
   else
     gmres_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);
 }

@@ -273,14 +273,14 @@ __device__ __forceinline__ void div_face_terms(const MeshView<T>& mv, const T* _
   }
 }
 
-// Cells of one batch: out = HELM ? scale * (ident p/(gamma-1) - alpha div) : div.
+// Cells of one batch: epi(idx, v) receives v = HELM ? scale * (ident p/(gamma-1) - alpha div) : div
+// at every node of the batch (the caller stores it, or fuses further pointwise work).
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 // sJ: coarse-pass buffer (coarse_buffer<DIM, DEG, 1>() elements).
-template <int DIM, int DEG, typename T, bool HELM>
+template <int DIM, int DEG, typename T, bool HELM, class Epi>
 __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
-                                               const T* __restrict__ p, T alpha, T scale, T ident,
-                                               T* __restrict__ out, int64_t batch, T* sF, T* sJ, const T* sDw,
-                                               const T* sII) {
+                                               const T* __restrict__ p, T alpha, T scale, T ident, Epi& epi,
+                                               int64_t batch, T* sF, T* sJ, const T* sDw, const T* sII) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
@@ -342,9 +342,9 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   if (active) {
     const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
     if (HELM)
-      out[idx] = scale * (ident * pv / gm1<T>() - alpha * dv);
+      epi(idx, scale * (ident * pv / gm1<T>() - alpha * dv));
     else
-      out[idx] = dv;
+      epi(idx, dv);
   }
 }
 

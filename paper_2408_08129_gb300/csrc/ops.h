@@ -42,7 +42,8 @@ int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T
 template <int DIM, typename TK>
 int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
                  double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
-                 double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s);
+                 double* partial, int npartial, double* out, double* lmax, unsigned long long* phase,
+                 cudaStream_t s);
 // One member of a batched solve (see launch_gmres_batched).
 template <typename TK>
 struct GmresItem {
@@ -53,13 +54,14 @@ struct GmresItem {
   double* x;
   double alpha, tol, inner_tol;
   int max_iters;
-  int method;  // 0 GMRES, 1 CG
+  int method;  // dg_krylov
   TK* Q;
   TK* w;
   double* w64;
   double* partial;
   int npartial;
   double* out;
+  double* lmax;  // [2] Chebyshev bound of this member (device)
 };
 
 // upper bound of one member's entry in a batched launch's argument table
@@ -84,11 +86,12 @@ inline int op_gmres_batched(dg_ctx* ctx, int dim, const GmresItem<TK>* items, in
 template <typename TK>
 inline int op_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
                     double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
-                    double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
+                    double* partial, int npartial, double* out, double* lmax, unsigned long long* phase,
+                    cudaStream_t s) {
   return m->dim == 2 ? launch_gmres<2, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart, max_iters, method, Q,
-                                           w, w64, partial, npartial, out, phase, s)
+                                           w, w64, partial, npartial, out, lmax, phase, s)
                      : launch_gmres<3, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart, max_iters, method, Q,
-                                           w, w64, partial, npartial, out, phase, s);
+                                           w, w64, partial, npartial, out, lmax, phase, s);
 }
 
 // dimension dispatch (with optional event timing per operator category)

@@ -67,7 +67,8 @@ int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, T* Dh, cu
 template <int DIM, int DEG, typename TK>
 int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
               double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
-              double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
+              double* partial, int npartial, double* out, double* lmax, unsigned long long* phase,
+              cudaStream_t s) {
   GmresPArgs<TK> a;
   a.mv64 = m->v64;
   a.mvk = view<TK>(m);
@@ -81,6 +82,8 @@ int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b
   a.gv = m->d_vec_scratch64;
   a.partial = partial;
   a.out = out;
+  a.lmax = lmax;
+  a.lmax = lmax;
   a.phase = phase;
   a.alpha = alpha;
   a.tol = tol;
@@ -90,6 +93,7 @@ int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b
   a.n = m->Nn;
   a.method = method;
   if (method == 1 && restart < 2) return fail(DG_EINVAL, "CG needs restart >= 2 (three work vectors)");
+  if (method == 3 && !lmax) return fail(DG_EINVAL, "Chebyshev needs a bound buffer");
   auto kern = gmres_persistent_kernel<DIM, DEG, TK>;
   const size_t smem = gmres_smem_bytes<DIM, DEG, TK>(restart);
   if (smem > 48 * 1024) {
@@ -162,6 +166,8 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
       a.gv = m->d_vec_scratch64;
       a.partial = it[i].partial;
       a.out = it[i].out;
+      a.lmax = it[i].lmax;
+      a.lmax = it[i].lmax;
       a.phase = nullptr;
       a.alpha = it[i].alpha;
       a.tol = it[i].tol;
@@ -269,10 +275,11 @@ int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T
 template <int DIM, typename TK>
 int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
                  double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
-                 double* partial, int npartial, double* out, unsigned long long* phase, cudaStream_t s) {
+                 double* partial, int npartial, double* out, double* lmax, unsigned long long* phase,
+                 cudaStream_t s) {
   DG_DEGREE_SWITCH(m->degree, return (run_gmres<DIM, DEG, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart,
                                                                max_iters, method, Q, w, w64, partial, npartial, out,
-                                                               phase, s)))
+                                                               lmax, phase, s)))
 }
 
 template <int DIM, typename TK>
@@ -290,7 +297,7 @@ int launch_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, i
                                         const int*);                                                            \
   template int launch_gmres<DIM, T>(const dg_mesh*, const double*, const T*, const double*, double*, double,     \
                                     double, double, int, int, int, T*, T*, double*, double*, int, double*,       \
-                                    unsigned long long*, cudaStream_t);                                         \
+                                    double*, unsigned long long*, cudaStream_t);                                \
   template int launch_gmres_batched<DIM, T>(dg_ctx*, const GmresItem<T>*, int, int, int*, cudaStream_t);
 
 }  // namespace dg

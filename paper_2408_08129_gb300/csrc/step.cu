@@ -43,6 +43,7 @@ struct dg_state {
   double* r64 = nullptr;  // FP64 outer residual
   double* solve_out = nullptr;  // [64][4] per-solve results of one step
   double* p_save = nullptr;     // initial guess kept while the autotuner tries both solver forms
+  double* lmax = nullptr;       // [2] Chebyshev upper spectral bound and the alpha it was estimated for
   float* f32 = nullptr;   // FP32 Krylov: h, rhs, delta [3 Nn]
   int* flag = nullptr;    // non-finite flag
   dg::Gmres<double> gm64;
@@ -218,6 +219,9 @@ int check(const char* what) {
   return e == cudaSuccess ? DG_OK : cuda_fail(e, what);
 }
 
+// Krylov forms that exist only as persistent kernels
+inline bool persistent_only(int krylov) { return krylov == DG_KRYLOV_CG || krylov == DG_KRYLOV_CHEBYSHEV; }
+
 // Helmholtz solve A(h) p = rhs (p holds the initial guess), FP64 or FP32-refined.
 // The fused FP64 path leaves its (iterations, residual, converged, ||b||) in
 // out[0..3] on the device and does not wait; the caller reads them later.
@@ -233,14 +237,15 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
   int rc;
   unsigned long long* phase = S->ctx->prof ? S->ctx->d_phase : nullptr;
   const int npart = (restart + 1) * kDotBlocks;
-  if (o->fused || o->krylov == DG_KRYLOV_CG) {  // CG exists only in the persistent form
+  if (o->fused || persistent_only(o->krylov)) {
     ProfScope ps(S->ctx, DG_PROF_GMRES, s);
     if (o->precision == DG_FP64)
       return op_gmres<double>(m, S->h, S->h, S->rhs, S->p, alpha, o->tol, 0.0, restart, o->max_iters, o->krylov,
-                              S->gm64.Q, S->gm64.w, S->gm64.w, S->gm64.d.partial, npart, out, phase, s);
+                              S->gm64.Q, S->gm64.w, S->gm64.w, S->gm64.d.partial, npart, out, S->lmax, phase, s);
     float* h32 = S->f32;  // converted by phase_picard_pre
     return op_gmres<float>(m, S->h, h32, S->rhs, S->p, alpha, o->tol, o->inner_tol, restart, o->max_iters,
-                           o->krylov, S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, npart, out, phase, s);
+                           o->krylov, S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, npart, out, S->lmax,
+                           phase, s);
   }
   if (o->precision == DG_FP64) {
     rc = S->gm64.solve(S->ctx, A64, S->rhs, S->p, o->tol, o->max_iters, s, &res);
@@ -327,7 +332,7 @@ extern "C" void dg_solver_opts_default(dg_solver_opts* o) {
   o->inner_tol = 1e-4;
   o->max_refine = 20;
   o->fused = -1;
-  o->krylov = DG_KRYLOV_GMRES;
+  o->krylov = DG_KRYLOV_AUTO;
 }
 
 extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_opts* opts, dg_state** out) {
@@ -346,9 +351,9 @@ extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_op
   S->restart = o.restart;
   const int64_t Nn = S->Nn;
   const int V = S->V, dim = S->dim;
-  // every buffer is rounded up to 32 doubles (256 bytes); 20 buffers in all
+  // every buffer is rounded up to 32 doubles (256 bytes); 21 buffers in all
   auto rup = [](size_t n) { return (n + 31) & ~(size_t)31; };
-  const size_t nd = 7 * rup((size_t)V * Nn) + 4 * rup((size_t)dim * Nn) + 9 * rup((size_t)Nn) + rup(8) + rup(256);
+  const size_t nd = 7 * rup((size_t)V * Nn) + 4 * rup((size_t)dim * Nn) + 9 * rup((size_t)Nn) + 2 * rup(8) + rup(256);
   cudaError_t e = cudaSetDevice(ctx->device);
   const size_t nf32 = (size_t)Nn * 3 + 256;
   if (e == cudaSuccess) e = cudaMalloc(&S->block, nd * sizeof(double) + nf32 * sizeof(float) + 1024);
@@ -381,6 +386,7 @@ extern "C" int dg_state_create(dg_ctx* ctx, const dg_mesh* m, const dg_solver_op
   S->flag = (int*)take(8);
   S->solve_out = take(256);
   S->p_save = take(Nn);
+  S->lmax = take(8);
   S->f32 = (float*)p;
   int rc = S->gm64.init(Nn, o.restart);
   if (rc == DG_OK) rc = S->gm32.init(Nn, o.restart);
@@ -420,6 +426,18 @@ extern "C" int dg_state_download(dg_state* S, double* host_U) {
   if (!S || !host_U) return fail(DG_EINVAL, "null argument");
   DG_CUDA(cudaMemcpyAsync(host_U, S->U, (size_t)S->V * S->Nn * sizeof(double), cudaMemcpyDeviceToHost, S->stream));
   DG_CUDA(cudaStreamSynchronize(S->stream));
+  return DG_OK;
+}
+
+extern "C" int dg_state_chebyshev_bound(dg_state* S, double* get, const double* set) {
+  if (!S) return fail(DG_EINVAL, "null argument");
+  DG_CUDA(cudaDeviceSynchronize());
+  if (get) DG_CUDA(cudaMemcpy(get, S->lmax, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (set) {
+    double v[2] = {set[0], set[1]};
+    if (!(v[0] > 1.0 / (kGamma - 1.0))) v[0] = v[1] = 0.0;
+    DG_CUDA(cudaMemcpy(S->lmax, v, 2 * sizeof(double), cudaMemcpyHostToDevice));
+  }
   return DG_OK;
 }
 
@@ -500,56 +518,81 @@ int phase_picard_pre(Member& M, int i, cudaStream_t s) {
   return check("picard");
 }
 
-// Autotuner: with fused = -1 the first solve of a (mesh, precision) is run
-// both as the persistent single-launch kernel and as one launch per Krylov
-// kernel, from the same initial guess (two rounds, the second one timed), and
-// the faster form is kept for every later solve on that mesh (the persistent form wins on small meshes, where
-// launch latency dominates; the multi-kernel form on large FP64 meshes, where
-// full occupancy hides the FP64 pipe's latency).
+// Solver forms the autotuner chooses among
+enum SolverForm { FORM_GMRES_MULTI = 0, FORM_GMRES_PERSISTENT = 1, FORM_CHEBYSHEV = 2, N_FORMS = 3 };
+
+inline void apply_form(dg_solver_opts& o, int form) {
+  o.krylov = form == FORM_CHEBYSHEV ? DG_KRYLOV_CHEBYSHEV : DG_KRYLOV_GMRES;
+  o.fused = form == FORM_GMRES_MULTI ? 0 : 1;
+}
+
+// Autotuner.  With krylov = AUTO the first solve of a (mesh, precision) is
+// run as GMRES in both forms (one persistent launch; one launch per Krylov
+// kernel) and as Chebyshev; with krylov = GMRES and fused = -1, as GMRES in
+// both forms.  Every candidate starts from the same initial guess, in two
+// rounds (the first pays the one-off costs -- lazy module loading, occupancy
+// queries, the Chebyshev bound -- and is not timed; the second is), and the
+// fastest is kept for every later solve on that mesh.  The persistent forms
+// win on small meshes, where launch latency dominates; the multi-kernel form
+// can win on large FP64 meshes, where full occupancy hides the FP64 pipe's
+// latency; Chebyshev needs no inner products.
 int phase_solve_single(Member& M, int i, cudaStream_t s) {
   const double dta = stage_dta(M, i);
   double* out = M.S->solve_out + 4 * M.nsolve;
   ++M.nsolve;
-  if (M.o.fused >= 0 || M.o.krylov == DG_KRYLOV_CG) return helmholtz_solve(M.S, &M.o, dta * dta, &M.st, out, s);
+  const bool auto_k = M.o.krylov == DG_KRYLOV_AUTO;
+  if (!auto_k && (M.o.fused >= 0 || persistent_only(M.o.krylov)))
+    return helmholtz_solve(M.S, &M.o, dta * dta, &M.st, out, s);
   const int pi = M.o.precision == DG_FP32 ? 1 : 0;
+  const int ncand = auto_k ? 3 : 2;
+  float* ms = M.m->tuned_ms[pi];
+  bool timed = true;
+  for (int f = 0; f < ncand; ++f) timed = timed && ms[f] > 0.0f;
   dg_solver_opts o = M.o;
-  if (M.m->tuned_fused[pi] >= 0) {
-    o.fused = M.m->tuned_fused[pi];
+  if (timed) {
+    int best = 0;
+    for (int f = 1; f < ncand; ++f)
+      if (ms[f] < ms[best]) best = f;
+    M.m->tuned_form[pi] = best;
+    apply_form(o, best);
     return helmholtz_solve(M.S, &o, dta * dta, &M.st, out, s);
   }
   dg_state* S = M.S;
   DG_CUDA(cudaMemcpyAsync(S->p_save, S->p, S->Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  cudaEvent_t e[3];
+  cudaEvent_t e[N_FORMS + 1];
   for (auto& ev : e) DG_CUDA(cudaEventCreate(&ev));
-  int rc;
-  float ms[2] = {0, 0};
-  // Two rounds, each form from the same initial guess: the first round pays
-  // the one-off costs (lazy module loading, occupancy queries, first-touch of
-  // the Krylov workspace) and is not timed; the second is.
+  int rc = DG_OK;
   bool first = true;
   const dg_step_stats st0 = M.st;  // only the last (kept) solve counts in the step's statistics
-  for (int round = 0; round < 2; ++round) {
-    for (int f = 1; f >= 0; --f) {
+  // candidates in the order persistent GMRES, Chebyshev, multi-kernel GMRES (the last one's result is kept)
+  int order[N_FORMS], no = 0;
+  order[no++] = FORM_GMRES_PERSISTENT;
+  if (auto_k) order[no++] = FORM_CHEBYSHEV;
+  order[no++] = FORM_GMRES_MULTI;
+  for (int round = 0; round < 2 && rc == DG_OK; ++round) {
+    for (int c = 0; c < no && rc == DG_OK; ++c) {
       M.st = st0;
       if (!first) DG_CUDA(cudaMemcpyAsync(S->p, S->p_save, S->Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
       first = false;
-      o.fused = f;
-      if (round == 1) DG_CUDA(cudaEventRecord(e[f == 1 ? 0 : 1], s));
-      if ((rc = helmholtz_solve(S, &o, dta * dta, &M.st, out, s)) != DG_OK) {
-        for (auto& ev : e) cudaEventDestroy(ev);
-        return rc;
-      }
+      apply_form(o, order[c]);
+      if (round == 1) DG_CUDA(cudaEventRecord(e[c], s));
+      rc = helmholtz_solve(S, &o, dta * dta, &M.st, out, s);
     }
   }
-  DG_CUDA(cudaEventRecord(e[2], s));
-  DG_CUDA(cudaEventSynchronize(e[2]));
-  cudaEventElapsedTime(&ms[1], e[0], e[1]);
-  cudaEventElapsedTime(&ms[0], e[1], e[2]);
+  if (rc == DG_OK) {
+    DG_CUDA(cudaEventRecord(e[no], s));
+    DG_CUDA(cudaEventSynchronize(e[no]));
+    int best = -1;
+    for (int c = 0; c < no; ++c) {
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e[c], e[c + 1]);
+      ms[order[c]] = t > 0.0f ? t : 1e-6f;
+      if (best < 0 || ms[order[c]] < ms[best]) best = order[c];
+    }
+    M.m->tuned_form[pi] = best;
+  }
   for (auto& ev : e) cudaEventDestroy(ev);
-  M.m->tuned_ms[pi][0] = ms[0];
-  M.m->tuned_ms[pi][1] = ms[1];
-  M.m->tuned_fused[pi] = ms[1] <= ms[0] ? 1 : 0;
-  return DG_OK;
+  return rc;
 }
 
 int phase_picard_post(Member& M, int i, cudaStream_t s) {
@@ -613,7 +656,7 @@ int prepare_member(Member& M, dg_ctx* ctx, const dg_mesh* m, dg_state* S, double
   if (opts) M.o = *opts;
   if (M.o.precision != DG_FP64 && M.o.precision != DG_FP32) return fail(DG_EINVAL, "bad precision");
   if (M.o.picard < 1 || M.o.picard > 32) return fail(DG_EINVAL, "picard must be in 1..32");
-  if (M.o.krylov < DG_KRYLOV_GMRES || M.o.krylov > DG_KRYLOV_GMRES_CGS2) return fail(DG_EINVAL, "bad Krylov method");
+  if (M.o.krylov < DG_KRYLOV_AUTO || M.o.krylov > DG_KRYLOV_CHEBYSHEV) return fail(DG_EINVAL, "bad Krylov method");
   M.S = S;
   M.m = m;
   M.dt = dt;
@@ -668,6 +711,19 @@ struct Branches {
   cudaEvent_t fork = nullptr;
 };
 
+// Krylov method of a member's solves inside a batched launch: krylov = AUTO
+// takes the mesh's tuned persistent form, else Chebyshev (a batch cannot time
+// candidates one by one).
+int batch_method(const Member& M) {
+  if (M.o.krylov != DG_KRYLOV_AUTO) return M.o.krylov;
+  const int pi = M.o.precision == DG_FP32 ? 1 : 0;
+  return M.m->tuned_form[pi] == FORM_GMRES_PERSISTENT ? DG_KRYLOV_GMRES : DG_KRYLOV_CHEBYSHEV;
+}
+// Members that run alone (one launch per Krylov kernel) instead of batched
+bool batch_alone(const Member& M) {
+  return M.o.krylov != DG_KRYLOV_AUTO && M.o.fused == 0 && !persistent_only(M.o.krylov);
+}
+
 // Batched Helmholtz solves of one Picard iteration: the persistent solves
 // grouped by (dim, degree, precision), one batched launch per group; members
 // that asked for the one-launch-per-kernel form are solved alone.
@@ -681,7 +737,7 @@ int solve_all(dg_ctx* ctx, std::vector<Member>& M, const dg_solver_opts& o, int 
   std::vector<std::pair<std::pair<int, int>, int>> keys;
   for (int i = 0; i < n; ++i) {
     // members of a batch use the batched persistent solve unless told otherwise
-    if (M[i].o.fused == 0 && M[i].o.krylov != DG_KRYLOV_CG) {
+    if (batch_alone(M[i])) {
       rest.push_back(i);
       continue;
     }
@@ -704,9 +760,10 @@ int solve_all(dg_ctx* ctx, std::vector<Member>& M, const dg_solver_opts& o, int 
       for (int i : groups[g]) {
         dg_state* S = M[i].S;
         const double dta = stage_dta(M[i], stage);
-        items.push_back({M[i].m, S->h, S->h, S->rhs, S->p, dta * dta, o.tol, 0.0, o.max_iters, o.krylov, S->gm64.Q,
+        items.push_back({M[i].m, S->h, S->h, S->rhs, S->p, dta * dta, o.tol, 0.0, o.max_iters, batch_method(M[i]),
+                         S->gm64.Q,
                          S->gm64.w, S->gm64.w, S->gm64.d.partial, (restart + 1) * kDotBlocks,
-                         S->solve_out + 4 * M[i].nsolve});
+                         S->solve_out + 4 * M[i].nsolve, S->lmax});
       }
       if ((rc = op_gmres_batched<double>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)
         return rc;
@@ -715,9 +772,9 @@ int solve_all(dg_ctx* ctx, std::vector<Member>& M, const dg_solver_opts& o, int 
       for (int i : groups[g]) {
         dg_state* S = M[i].S;
         const double dta = stage_dta(M[i], stage);
-        items.push_back({M[i].m, S->h, S->f32, S->rhs, S->p, dta * dta, o.tol, o.inner_tol, o.max_iters, o.krylov,
-                         S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, (restart + 1) * kDotBlocks,
-                         S->solve_out + 4 * M[i].nsolve});
+        items.push_back({M[i].m, S->h, S->f32, S->rhs, S->p, dta * dta, o.tol, o.inner_tol, o.max_iters,
+                         batch_method(M[i]), S->gm32.Q, S->gm32.w, S->r64, S->gm32.d.partial, (restart + 1) * kDotBlocks,
+                         S->solve_out + 4 * M[i].nsolve, S->lmax});
       }
       if ((rc = op_gmres_batched<float>(ctx, dim, items.data(), (int)items.size(), restart, err, s)) != DG_OK)
         return rc;
@@ -891,7 +948,7 @@ extern "C" int dg_batch_plan_create(dg_ctx* ctx, int n, const dg_mesh* const* me
     return rc;
   }
   for (auto& mm : P->M)
-    if (mm.o.fused == 0 && mm.o.krylov != DG_KRYLOV_CG) {
+    if (batch_alone(mm)) {
       delete P;
       return fail(DG_EINVAL, "a batch plan needs the persistent solve (fused != 0)");
     }

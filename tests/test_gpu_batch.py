@@ -39,7 +39,8 @@ def _rel_dev(a, b, bg):
     return max(np.linalg.norm(a[v] - b[v]) / max(np.linalg.norm(b[v] - bg[v]), 1e-300) for v in range(a.shape[0]))
 
 
-@pytest.mark.parametrize("precision,krylov", [("fp64", 0), ("fp32", 0), ("fp64", 1), ("fp32", 1)])
+@pytest.mark.parametrize("precision,krylov", [("fp64", 0), ("fp32", 0), ("fp64", 1), ("fp32", 1), ("fp64", 3),
+                                             ("fp32", 3)])
 def test_batch_equals_alone(dg, ctx, precision, krylov):
     prec = dg.DG_FP64 if precision == "fp64" else dg.DG_FP32
     opts = dg.solver_opts(tol=1e-12, precision=prec, inner_tol=1e-4, krylov=krylov, fused=1)
@@ -127,4 +128,4 @@ def test_plan_rejects_multi_kernel_solves(dg, ctx):
     mesh = dg.Mesh(ctx, case)
     st = dg.State(ctx, mesh)
     with pytest.raises(dg.DGError, match="persistent solve"):
-        dg.BatchPlan(ctx, [mesh], [st], [case.dt], dg.solver_opts(fused=0))
+        dg.BatchPlan(ctx, [mesh], [st], [case.dt], dg.solver_opts(fused=0, krylov=dg.DG_KRYLOV_GMRES))

@@ -245,29 +245,36 @@ def test_rest_state_stays_at_rest(dg, ctx):
     assert _rel(U[0], ref.Ubg[0]) < 1e-14 and _rel(U[4], ref.Ubg[4]) < 1e-14
 
 
-def test_autotuner_times_both_solver_forms(dg, ctx):
-    """fused = -1 times the persistent and the multi-kernel solve once and keeps the faster."""
+@pytest.mark.parametrize("krylov,forms", [("gmres", ("gmres_persistent", "gmres_multi_kernel")),
+                                          ("auto", ("gmres_persistent", "gmres_multi_kernel", "chebyshev"))])
+def test_autotuner_times_the_solver_forms(dg, ctx, krylov, forms):
+    """krylov = GMRES with fused = -1 times both GMRES forms; krylov = AUTO adds Chebyshev; the
+    fastest is kept, and the tuned step still matches the oracle."""
     case = make_case("bubble2d", 0)
     ref = DG(case)
     mesh = dg.Mesh(ctx, case)
     st = dg.State(ctx, mesh)
     st.upload(ref.state())
     assert mesh.autotuned()["fp64"]["form"] is None
-    dg.imex_rk2_step(ctx, mesh, st, case.dt, dg.solver_opts(tol=1e-12, fused=-1))
+    kry = dg.DG_KRYLOV_GMRES if krylov == "gmres" else dg.DG_KRYLOV_AUTO
+    opts = dg.solver_opts(tol=1e-12, fused=-1, krylov=kry)
+    dg.imex_rk2_step(ctx, mesh, st, case.dt, opts)
     t = mesh.autotuned()["fp64"]
-    assert t["form"] in ("persistent", "multi-kernel")
-    assert t["ms_persistent"] > 0 and t["ms_multi_kernel"] > 0
-    faster = "persistent" if t["ms_persistent"] <= t["ms_multi_kernel"] else "multi-kernel"
-    assert t["form"] == faster
+    assert sorted(t["ms"]) == sorted(forms)
+    assert t["form"] == min(t["ms"], key=t["ms"].get)
+    dg.imex_rk2_step(ctx, mesh, st, case.dt, opts)
+    Ur = Stepper(ref, tol=1e-12).step(Stepper(ref, tol=1e-12).step(ref.state(), case.dt), case.dt)
+    assert _per_var_rel(st.download() - ref.Ubg, Ur - ref.Ubg) < 1e-9
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("krylov", ["cg", "gmres_cgs2"])
+@pytest.mark.parametrize("krylov", ["cg", "gmres_cgs2", "chebyshev"])
 def test_imex_steps_other_krylov_forms(dg, ctx, precision, krylov):
-    """CG in the w J inner product (M A is SPD) and GMRES with classical Gram-Schmidt twice per
-    step reach the same step as the oracle's GMRES."""
+    """CG in the w J inner product (M A is SPD), GMRES with classical Gram-Schmidt twice per step
+    and Chebyshev iteration on [1/(gamma-1), lmax] reach the same step as the oracle's GMRES."""
     prec = dg.DG_FP64 if precision == "fp64" else dg.DG_FP32
-    kry = dg.DG_KRYLOV_CG if krylov == "cg" else dg.DG_KRYLOV_GMRES_CGS2
+    kry = {"cg": dg.DG_KRYLOV_CG, "gmres_cgs2": dg.DG_KRYLOV_GMRES_CGS2,
+           "chebyshev": dg.DG_KRYLOV_CHEBYSHEV}[krylov]
     opts = dg.solver_opts(tol=1e-12, krylov=kry, precision=prec, inner_tol=1e-4, fused=1)
     case = make_case("bubble2d", 0)
     U, Ur, ref = _run_steps(dg, ctx, case, 10, opts)
@@ -275,3 +282,39 @@ def test_imex_steps_other_krylov_forms(dg, ctx, precision, krylov):
     case = make_case("hill2d", 0)
     U, Ur, ref = _run_steps(dg, ctx, case, 2, opts)
     assert _per_var_rel(U - ref.Ubg, Ur - ref.Ubg) < 1e-9
+
+
+def test_chebyshev_bound_estimate_and_repair(dg, ctx):
+    """The power-iteration bound sits just above the Helmholtz spectrum (<= 1.05 x lmax, and above
+    the largest Ritz value GMRES finds); a bound set too low is caught: the solve falls back to
+    GMRES, still matches the oracle, and the bound is re-estimated on the next solve."""
+    case = make_case("bubble2d", 0)
+    opts = dg.solver_opts(tol=1e-12, krylov=dg.DG_KRYLOV_CHEBYSHEV, fused=1)
+    mesh = dg.Mesh(ctx, case)
+    st = dg.State(ctx, mesh, opts)
+    assert st.chebyshev_bound() == (0.0, 0.0)
+    # a fresh state: estimate on the first solve
+    r = DG(case)
+    st.upload(r.state())
+    dg.imex_rk2_step(ctx, mesh, st, case.dt, opts)
+    lmax, alpha = st.chebyshev_bound()
+    assert alpha > 0 and lmax > 2.5
+    # dense spectrum of the oracle's operator at the initial enthalpy: the bound covers it
+    K, nc = r.mesh.K, r.mesh.nc
+    h = r.enthalpy(r.state())
+    n = K * nc
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = r.helmholtz(e.reshape(K, nc), h, alpha).ravel()
+    ev = np.linalg.eigvals(A).real.max()
+    assert ev <= lmax <= 1.06 * ev, (ev, lmax)
+    # too low a bound: repaired
+    st.upload(r.state())
+    st.chebyshev_bound((2.6, alpha))
+    stats = dg.imex_rk2_step(ctx, mesh, st, case.dt, opts)
+    assert stats["status"] == 0
+    Uref = Stepper(r, tol=1e-12).step(r.state(), case.dt)
+    assert _per_var_rel(st.download() - r.Ubg, Uref - r.Ubg) < 1e-9
+    assert st.chebyshev_bound()[0] > 2.6 + 1e-9

@@ -38,8 +38,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 4 FP64 flop/clk/SM x 2.0
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel as it
-# stands (profiles/gmres_persistent_hill2d.md); set to None whenever that kernel changes
-NCU_TRAFFIC_BYTES = {}  # (workload, kernel) -> dram read+write bytes per launch from one ncu capture
+# stands (profiles/persistent_solve_hill2d.md: the persistent solve with the autotuned Chebyshev
+# body, FP64); set to None whenever that kernel changes
+NCU_TRAFFIC_BYTES = {("hill2d", "chebyshev", "fp64"): 5.851648e6 + 0.152576e6}
 
 
 def algorithmic(dim, degree, n_nodes, kind, s=8):
@@ -532,6 +533,7 @@ def main():
     expl_flops, expl_bytes = algorithmic(case.dim, case.degree, n, "explicit")
     iters = sum(s["gmres_iters"] for s in stats)
     solves = sum(s["solves"] for s in stats)
+    traffic_key = (args.workload, dom, args.precision)
     if dom == "gmres":
         # one launch = one whole solve; it = mean iterations per solve.  GMRES: per iteration
         # one Helmholtz mat-vec and Gram-Schmidt twice over the k+1 basis vectors (two dots +
@@ -542,9 +544,11 @@ def main():
         if "chebyshev" in form:
             flops = (it + 1) * helm_flops + n * 8.0 * it
             name = "gmres_persistent_kernel (persistent Chebyshev solve)"
+            traffic_key = (args.workload, "chebyshev", args.precision)
         else:
             flops = (it + 1) * helm_flops + n * (4.0 * it * (it + 1) + 4.0 * it)
             name = "gmres_persistent_kernel (persistent GMRES solve)"
+            traffic_key = (args.workload, "gmres", args.precision)
     elif dom == "explicit":
         flops = expl_flops
         name = "explicit apply (face + cell kernels)"
@@ -555,7 +559,7 @@ def main():
     roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "peak_source": "derived FP64 rate: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
-            "traffic": NCU_TRAFFIC_BYTES.get((args.workload, dom)), "traffic_unit": "bytes per launch",
+            "traffic": NCU_TRAFFIC_BYTES.get(traffic_key), "traffic_unit": "bytes per launch",
             "avg_launch_us": avg_ms * 1e3, "launches": cats[dom]["count"],
             "hbm_peak_gbs": hbm, "hbm_peak_source": peak_src}
 

@@ -217,14 +217,14 @@ def apply_sweep(dg, torch, case_name, reps=10):
     return out
 
 
-def ensemble_bench(dg, torch, n_members=64, steps=10):
+def ensemble_bench(dg, torch, n_members=64, steps=10, inner_tol=1e-6):
     """64 uneven 2D members (16x8..128x64 base, 0-2 levels, degree 2-5), FP32-refined: one
     dg_batch_step per ensemble step, then the same step as a captured batch plan (CUDA graph)."""
     from workloads.cases import member2d
 
     ctx = dg.Context(torch.cuda.current_device())
     cases = [member2d(1000 + i) for i in range(n_members)]
-    opts = dg.solver_opts(tol=1e-12, precision=dg.DG_FP32, inner_tol=1e-4)
+    opts = dg.solver_opts(tol=1e-12, precision=dg.DG_FP32, inner_tol=inner_tol)
     meshes = [dg.Mesh(ctx, c) for c in cases]
     states = [dg.State(ctx, m, opts) for m in meshes]
     for c, m, st in zip(cases, meshes, states):
@@ -280,7 +280,7 @@ def ensemble_bench(dg, torch, n_members=64, steps=10):
     return out
 
 
-def serving_bench(dg, torch, n_requests=40, rate=20.0, dof_hi=3e5, steps_hi=40, budget=160e9):
+def serving_bench(dg, torch, n_requests=40, rate=20.0, dof_hi=3e5, steps_hi=40, budget=160e9, inner_tol=1e-6):
     """Config-5 shape, bounded sample: Poisson arrivals, 2D/3D, degree 2-5, FP64 or FP32-refined."""
     from workloads.cases import serving_trace
 
@@ -293,7 +293,7 @@ def serving_bench(dg, torch, n_requests=40, rate=20.0, dof_hi=3e5, steps_hi=40, 
         now = time.perf_counter() - t0
         if t_arr > now:
             time.sleep(t_arr - now)
-        o = dg.solver_opts(tol=1e-10, precision=dg.DG_FP64 if prec == "fp64" else dg.DG_FP32, inner_tol=1e-4)
+        o = dg.solver_opts(tol=1e-10, precision=dg.DG_FP64 if prec == "fp64" else dg.DG_FP32, inner_tol=inner_tol)
         ids.append((sv.submit(case, steps, opts=o), case, steps))
     for rid, _, _ in ids:
         sv.wait(rid, 900)
@@ -356,6 +356,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="fp32 = FP32 Krylov iterations inside FP64 refinement")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32-refined and other-solver comparisons")
+    ap.add_argument("--inner-tol", type=float, default=1e-6,
+                    help="FP32-refined forms: residual reduction of each FP32 inner cycle")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -384,7 +386,7 @@ def main():
     kry = {"auto": dg.DG_KRYLOV_AUTO, "gmres": dg.DG_KRYLOV_GMRES, "gmres_cgs2": dg.DG_KRYLOV_GMRES_CGS2,
            "cg": dg.DG_KRYLOV_CG, "chebyshev": dg.DG_KRYLOV_CHEBYSHEV}[args.krylov]
     prec = dg.DG_FP64 if args.precision == "fp64" else dg.DG_FP32
-    opts = dg.solver_opts(tol=1e-12, picard=3, restart=30, krylov=kry, precision=prec, inner_tol=1e-4)
+    opts = dg.solver_opts(tol=1e-12, picard=3, restart=30, krylov=kry, precision=prec, inner_tol=args.inner_tol)
     state = dg.State(ctx, mesh, opts)
     init = case.init
     if init["kind"] == "bubble":
@@ -439,7 +441,7 @@ def main():
     fp32, cg = None, None
     if not args.no_forms:
         # the FP32-refined form from the same start: FP32 applies + FP32 inner GMRES, FP64 outer residual
-        opts32 = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=dg.DG_FP32, inner_tol=1e-4)
+        opts32 = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=dg.DG_FP32, inner_tol=args.inner_tol)
         state.upload(U_start)
         for _ in range(args.warmup):  # untimed: lazy loading and the autotuner's first FP32 solve
             dg.imex_rk2_step(ctx, mesh, state, case.dt, opts32)
@@ -476,7 +478,7 @@ def main():
                                 ("cg_fp32_refined", dg.DG_FP32, dg.DG_KRYLOV_CG),
                                 ("chebyshev_fp64", dg.DG_FP64, dg.DG_KRYLOV_CHEBYSHEV),
                                 ("chebyshev_fp32_refined", dg.DG_FP32, dg.DG_KRYLOV_CHEBYSHEV)):
-            o = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=prec, inner_tol=1e-4, krylov=kry,
+            o = dg.solver_opts(tol=1e-12, picard=3, restart=30, precision=prec, inner_tol=args.inner_tol, krylov=kry,
                                fused=-1 if kry == dg.DG_KRYLOV_GMRES else 1)
             state.upload(U_start)
             for _ in range(args.warmup):
@@ -582,8 +584,8 @@ def main():
     if rank == 0 and not args.no_sweep:
         line["applies"] = apply_sweep(dg, torch, args.sweep_workload)
     if rank == 0 and not args.no_ensemble:
-        line["ensemble"] = ensemble_bench(dg, torch)
-        line["serving"] = serving_bench(dg, torch)
+        line["ensemble"] = ensemble_bench(dg, torch, inner_tol=args.inner_tol)
+        line["serving"] = serving_bench(dg, torch, inner_tol=args.inner_tol)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(args.workload, 12.0)
     if rank == 0:

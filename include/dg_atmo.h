@@ -143,6 +143,18 @@ typedef struct {
   double atm_N;           /* buoyancy frequency of the stratified case (1/s)    */
   double atm_p_ref;       /* surface pressure (Pa)                              */
   double gravity;         /* g (9.81 in Eq. (1)); 0 turns gravity off           */
+  /* Rayleigh damping layer below the top boundary (absorbs upward-going waves;
+   * the paper's non-reflecting boundaries are described elsewhere, this is a
+   * reading): in the top sponge_depth metres of physical height the time step
+   * adds -tau(z) (U - U_ref) to the explicit tendency, with
+   * tau(z) = sponge_rate sin^2(pi/2 (z - z_d)/sponge_depth) for z > z_d =
+   * H - sponge_depth (0 below) and U_ref the hydrostatic background with the
+   * uniform x-velocity sponge_u0 (rho_bar, rho_bar u0, 0, p_bar/(gamma-1) +
+   * rho_bar u0^2/2).  sponge_depth = 0 turns it off.  Explicit treatment:
+   * keep sponge_rate dt <= 1. */
+  double sponge_depth;    /* (m), 0..H                                          */
+  double sponge_rate;     /* tau at the top (1/s), >= 0                         */
+  double sponge_u0;       /* reference x-velocity (m/s)                         */
 } dg_mesh_desc;
 
 typedef struct {
@@ -240,7 +252,7 @@ typedef struct {
   double tol;          /* relative residual target ||b - A x|| / ||b|| (1e-12)   */
   int precision;       /* DG_FP64, or DG_FP32 = FP32 applies + inner GMRES      */
                        /*   inside FP64 iterative refinement                    */
-  double inner_tol;    /* DG_FP32: relative tolerance of each inner solve (1e-4) */
+  double inner_tol;    /* DG_FP32: relative tolerance of each inner solve (1e-6) */
   int max_refine;      /* DG_FP32: outer refinement steps cap (20)              */
   int fused;           /* 1: each GMRES solve is one persistent cooperative     */
                        /*    kernel; 0: one launch per Krylov kernel; -1       */

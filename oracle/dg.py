@@ -45,7 +45,36 @@ class DG:
         self.Ubg = np.zeros((self.V, m.K, m.nc))
         self.Ubg[0] = self.rhobar
         self.Ubg[self.V - 1] = self.pbar / (ph.GAMMA - 1.0)
+        self._sponge(getattr(case, "sponge", None), z)
         self._faces()
+
+    # ------------------------------------------------------------------ damping layer
+    def _sponge(self, sp, z):
+        """Rayleigh damping layer below the top boundary.
+
+        The paper's runs use non-reflecting boundaries whose method it defers
+        to earlier work; this reading relaxes the state towards a reference
+        state in the top ``depth`` metres of physical height, with the rate
+        rising as sin^2 from 0 at z_d = H - depth to ``rate`` at the top
+        (the usual profile of upper absorbing layers).  The reference state is
+        the hydrostatic background carrying the uniform x-velocity ``u0``.
+        """
+        self.tau = None
+        if not sp or not (sp.get("depth", 0.0) > 0.0) or not (sp.get("rate", 0.0) > 0.0):
+            return
+        depth, rate, u0 = sp["depth"], sp["rate"], sp.get("u0", 0.0)
+        top = self.case.extent[self.d - 1]
+        frac = np.clip((z - (top - depth)) / depth, 0.0, 1.0)
+        self.tau = rate * np.sin(0.5 * np.pi * frac) ** 2
+        self.Uref = self.Ubg.copy()
+        self.Uref[1] = self.rhobar * u0
+        self.Uref[self.V - 1] = self.pbar / (ph.GAMMA - 1.0) + 0.5 * self.rhobar * u0 * u0
+
+    def damping(self, U):
+        """Tendency of the damping layer, -tau (U - U_ref) (zero without a layer)."""
+        if self.tau is None:
+            return np.zeros_like(U)
+        return -self.tau[None] * (U - self.Uref)
 
     # ------------------------------------------------------------------ tables
     def _faces(self):

@@ -19,6 +19,8 @@ Readings (the paper cites the method only):
   momentum stage equation into the energy one gives the Helmholtz problem
   p'/(gamma-1) - (dt at_ii)^2 div_h(h grad_h p') = rhs, with h and the
   kinetic energy lagged by the fixed-point loop.
+* A Rayleigh damping layer below the top (a reading; see DG.damping) is an
+  explicit source, added to the explicit tendencies.
 * GMRES(m) with classical Gram-Schmidt applied twice, Givens rotations,
   relative tolerance on ||b - A x|| / ||b||, previous iterate as initial guess.
 """
@@ -120,7 +122,8 @@ class Stepper:
     def step(self, U, dt):
         dg, d = self.dg, self.dg.d
         gm1 = ph.GAMMA - 1.0
-        E = [dg.explicit(U, "imex")]
+        # the damping layer (if any) is an explicit source
+        E = [dg.explicit(U, "imex") + dg.damping(U)]
         p0 = dg.pprime(U)
         I = [self.implicit_terms(U, p0, dg.enthalpy(U))]
         p_prev = p0
@@ -148,7 +151,7 @@ class Stepper:
             Ui[0] = rho
             Ui[1:1 + d] = mk
             Ui[1 + d] = (dg.pbar + p) / gm1 + 0.5 * np.sum(mk * mk, axis=0) / rho
-            E.append(dg.explicit(Ui, "imex"))
+            E.append(dg.explicit(Ui, "imex") + dg.damping(Ui))
             if i == 1:
                 Ii = np.zeros_like(U)
                 Ii[1:1 + d] = -gp

@@ -35,6 +35,7 @@ class MeshDesc(ctypes.Structure):
         ("hill_xc", c_double), ("hill_yc", c_double),
         ("atm_kind", c_int), ("atm_T", c_double), ("atm_N", c_double), ("atm_p_ref", c_double),
         ("gravity", c_double),
+        ("sponge_depth", c_double), ("sponge_rate", c_double), ("sponge_u0", c_double),
     ]
 
 

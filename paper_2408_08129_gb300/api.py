@@ -87,6 +87,10 @@ def mesh_desc(case, gravity=None):
     d.atm_N = atm.get("N", 0.0)
     d.atm_p_ref = atm.get("p_ref", 0.0)
     d.gravity = case.gravity if gravity is None else gravity
+    sp = getattr(case, "sponge", None) or {}
+    d.sponge_depth = sp.get("depth", 0.0)
+    d.sponge_rate = sp.get("rate", 0.0)
+    d.sponge_u0 = sp.get("u0", 0.0)
     return d, (level, ijk)
 
 

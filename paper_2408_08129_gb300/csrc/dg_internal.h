@@ -154,6 +154,7 @@ struct dg_mesh {
   double* d_face_scratch64 = nullptr;
   double* d_vec_scratch64 = nullptr;  // [dim][Nn]
   double* d_red_scratch = nullptr;    // [2*512] block partials of the conservation sums
+  double* d_tau = nullptr;            // [Nn] Rayleigh damping rate per node (NULL: no sponge layer)
   // autotuned Helmholtz solver per precision: the timed first solve of each
   // form (0 = GMRES, one launch per Krylov kernel; 1 = GMRES persistent;
   // 2 = Chebyshev persistent; 0 ms = not timed) and the form chosen last

@@ -378,6 +378,22 @@ int build_mesh(dg_mesh* m) {
       if (f < m->nconf) fnode_p[(size_t)f * NF + k] = face_p[f] * nc + host_face_node(dim, n, face_lfp[f], k);
     }
 
+  // Rayleigh damping rate per node: sin^2 profile over the top sponge_depth of physical height
+  std::vector<double> tau;
+  if (d.sponge_depth > 0.0 && d.sponge_rate > 0.0) {
+    const double H = d.extent[dim - 1], zd = H - d.sponge_depth;
+    const double half_pi = 0.5 * 3.14159265358979323846;
+    tau.assign(m->Nn, 0.0);
+    for (int64_t i = 0; i < m->Nn; ++i) {
+      const int64_t c = i / nc, q = i % nc;
+      const double z = m->X[((size_t)(dim - 1) * K + c) * nc + q];
+      if (z > zd) {
+        const double s = std::sin(half_pi * std::min(1.0, (z - zd) / d.sponge_depth));
+        tau[i] = d.sponge_rate * s * s;
+      }
+    }
+  }
+
   // ---------------------------------------------------------------- upload
   const std::vector<double> tabp = tab.packed();
   const size_t n_int = (size_t)5 * nf + cell_face.size() + 2 * (size_t)nf * NF;
@@ -390,6 +406,11 @@ int build_mesh(dg_mesh* m) {
   m->scratch_bytes = (pad((size_t)m->V * nf * NF) + pad((size_t)dim * m->Nn) + 2 * 512) * sizeof(double);
   DG_CUDA(cudaMalloc(&m->d_scratch, m->scratch_bytes));
   m->device_bytes = pad(n_int) * 4 + pad(n_real) * 12 + 1024 + m->scratch_bytes;
+  if (!tau.empty()) {
+    DG_CUDA(cudaMalloc(&m->d_tau, tau.size() * sizeof(double)));
+    DG_CUDA(cudaMemcpy(m->d_tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice));
+    m->device_bytes += tau.size() * sizeof(double);
+  }
   m->d_face_scratch64 = (double*)m->d_scratch;
   m->d_vec_scratch64 = (double*)m->d_scratch + pad((size_t)m->V * nf * NF);
   m->d_red_scratch = m->d_vec_scratch64 + pad((size_t)dim * m->Nn);
@@ -473,6 +494,9 @@ extern "C" int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* desc, dg_mesh** o
   if (desc->atm_kind != DG_ATM_NONE && (!(desc->atm_T > 0) || !(desc->atm_p_ref > 0)))
     return fail(DG_EINVAL, "bad atmosphere parameters");
   if (desc->atm_kind == DG_ATM_STRATIFIED && !(desc->atm_N > 0)) return fail(DG_EINVAL, "bad buoyancy frequency");
+  if (!(desc->sponge_depth >= 0.0) || !(desc->sponge_rate >= 0.0) ||
+      desc->sponge_depth > desc->extent[desc->dim - 1] || !std::isfinite(desc->sponge_u0))
+    return fail(DG_EINVAL, "bad sponge layer parameters");
   dg_mesh* m = new (std::nothrow) dg_mesh();
   if (!m) return fail(DG_ENOMEM, "host allocation failed");
   m->ctx = ctx;
@@ -506,6 +530,7 @@ extern "C" int dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->d_f64);
   cudaFree(m->d_f32);
   cudaFree(m->d_scratch);
+  if (m->d_tau) cudaFree(m->d_tau);
   delete m;
   return DG_OK;
 }

@@ -1120,7 +1120,7 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
 // Alg. 12.1) needs no inner product: one step is one mat-vec whose epilogue
 // updates x, r and the direction in the same pass, two grid barriers in all;
 // the residual norm for the stopping test comes from block partial sums read
-// after the barrier.  lmax is estimated in the kernel by power iteration in the
+// during the next step's gradient pass.  lmax is estimated in the kernel by power iteration in the
 // w J norm (the ratio ||A p|| / ||p|| approaches lmax from below), widened by
 // kLmaxMargin, and kept in a.lmax for later solves with the same alpha.  If
 // the residual grows (an estimate too low), the bound is cleared and the solve
@@ -1160,6 +1160,10 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
   TK* r = a.Q;          // residual (recurrence)
   TK* d = a.Q + n;      // direction
   TK* w = a.w;          // power-iteration partner
+  // TK = float: the cycle's correction is summed in TK and added to the FP64 x
+  // once per cycle (no FP64 work in the steps themselves)
+  const bool fold = mixed && a.m >= 2;
+  TK* dx = a.Q + 2 * n;
   const TK* wJ = a.mvk.wJ;
   TK* gvk = (TK*)a.gv;
   // sum of the G block partials, the same in every CTA
@@ -1251,6 +1255,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       const double ri = a.b[i] - a.w64[i];
       r[i] = (TK)ri;
       d[i] = (TK)ri * ith;
+      if (fold) dx[i] = TK(0);
       acc += ri * ri;
     }
     {
@@ -1297,20 +1302,23 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       // divergence pass with the update: x += d, r -= A d, d = c1 d + c2 r
       const double rho1 = 1.0 / (2.0 * sigma1 - rho);
       const TK c1 = (TK)(rho1 * rho), c2 = (TK)(2.0 * rho1 / delta);
-      double racc = 0.0;
+      TK racc = TK(0);
       auto epi = [&](int64_t i, TK ad) {
         const TK di = d[i];
         const TK ri = r[i] - ad;
         r[i] = ri;
-        a.x[i] += (double)di;
+        if (fold)
+          dx[i] += di;
+        else
+          a.x[i] += (double)di;
         d[i] = c1 * di + c2 * ri;
-        racc += (double)ri * (double)ri;
+        racc += ri * ri;
       };
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         div_cell_batch<DIM, DEG, TK, true>(a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi, bt, scellk, sJk, sDwk,
                                            sIIk);
       {
-        const double t = block_sum(racc, sred);
+        const double t = block_sum_k<TK>(racc, sred);
         if (threadIdx.x == 0) a.partial[sg.rank] = t;
       }
       sg.sync();
@@ -1320,6 +1328,8 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       ++cycle_its;
       have_prev = true;
     }
+    if (fold)
+      for (int64_t i = tid; i < n; i += gstride) a.x[i] += (double)dx[i];
     // CTAs may leave the loop inside a gradient pass (whose scratch aliases the
     // FP64 residual's): meet before the next pass
     sg.sync();

@@ -204,6 +204,23 @@ __global__ void final_kernel(const double* __restrict__ Ui, const double* __rest
   }
 }
 
+// Rayleigh damping layer: E -= tau (U - U_ref), U_ref = background with the
+// uniform x-velocity u0 (rho_b, rho_b u0, 0.., p_b/(gamma-1) + rho_b u0^2/2)
+__global__ void sponge_kernel(const double* __restrict__ U, const double* __restrict__ tau,
+                              const double* __restrict__ rhob, const double* __restrict__ pb, double u0, int64_t n,
+                              int dim, double* __restrict__ E) {
+  GRID_LOOP(i, n) {
+    const double t = tau[i];
+    if (t == 0.0) continue;
+    const double rb = rhob[i];
+    E[i] -= t * (U[i] - rb);
+    E[n + i] -= t * (U[n + i] - rb * u0);
+    for (int b = 1; b < dim; ++b) E[(int64_t)(1 + b) * n + i] -= t * U[(int64_t)(1 + b) * n + i];
+    const int64_t ie = (int64_t)(dim + 1) * n + i;
+    E[ie] -= t * (U[ie] - (pb[i] / (kGamma - 1.0) + 0.5 * rb * u0 * u0));
+  }
+}
+
 __global__ void to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
   GRID_LOOP(i, n) { y[i] = (float)x[i]; }
 }
@@ -307,7 +324,12 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
 // FP64 in both precision modes; the FP32 form puts the Krylov mat-vecs (the
 // bulk of the work) in FP32 and recovers FP64 accuracy by the FP64 residual.
 int step_explicit(dg_state* S, const double* U, double* E, cudaStream_t s) {
-  return op_explicit<double>(S->mesh, U, E, S->mesh->d_face_scratch64, false, s, nullptr);
+  const dg_mesh* m = S->mesh;
+  int rc = op_explicit<double>(m, U, E, m->d_face_scratch64, false, s, nullptr);
+  if (rc != DG_OK || !m->d_tau) return rc;
+  sponge_kernel<<<gridn(S->Nn), 256, 0, s>>>(U, m->d_tau, m->v64.rhob, m->v64.pb, m->desc.sponge_u0, S->Nn, S->dim, E);
+  count_launches(S->ctx, 1);
+  return check("sponge layer");
 }
 int step_grad(dg_state* S, const double* p, double* g, cudaStream_t s) {
   return op_grad<double>(S->mesh, p, nullptr, g, S->mesh->d_face_scratch64, s, nullptr);
@@ -329,7 +351,7 @@ extern "C" void dg_solver_opts_default(dg_solver_opts* o) {
   o->max_iters = 2000;
   o->tol = 1e-12;
   o->precision = DG_FP64;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-6;
   o->max_refine = 20;
   o->fused = -1;
   o->krylov = DG_KRYLOV_AUTO;

@@ -62,6 +62,8 @@ class Case:
     steps: int
     seed: int
     gravity: float = GRAV
+    # Rayleigh damping layer below the top: {"depth": m, "rate": 1/s, "u0": m/s}, or None
+    sponge: Optional[Dict[str, float]] = None
 
     @property
     def n_cells(self) -> int:

@@ -63,6 +63,7 @@ struct MeshView {
   const int* cell_face;  // [n_cells*2*dim] (face << 2) | side; side 0 minus, 1 plus, 2 coarse, 3 wall
   const int* fnode_m;    // [nf*NF] node index of each face node on the minus side
   const int* fnode_p;    // [nf*NF] node index on the plus side (conforming faces; -1 otherwise)
+  const int* cell_cmask; // [n_cells] bit lf set if local face lf is the coarse side of a 2:1 face
   const T* tab;     // packed Tables1D of the mesh's degree
   T gravity;
 };

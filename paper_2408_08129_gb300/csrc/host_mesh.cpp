@@ -396,7 +396,11 @@ int build_mesh(dg_mesh* m) {
 
   // ---------------------------------------------------------------- upload
   const std::vector<double> tabp = tab.packed();
-  const size_t n_int = (size_t)5 * nf + cell_face.size() + 2 * (size_t)nf * NF;
+  std::vector<int> cell_cmask(K, 0);
+  for (int64_t c = 0; c < K; ++c)
+    for (int lf = 0; lf < 2 * dim; ++lf)
+      if ((cell_face[c * 2 * dim + lf] & 3) == 2) cell_cmask[c] |= 1 << lf;
+  const size_t n_int = (size_t)5 * nf + cell_face.size() + 2 * (size_t)nf * NF + (size_t)K;
   const size_t n_real = (size_t)dim * dim * m->Nn + 4 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size();
   auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
   DG_CUDA(cudaSetDevice(m->ctx->device));
@@ -421,6 +425,7 @@ int build_mesh(dg_mesh* m) {
   ibuf.insert(ibuf.end(), cell_face.begin(), cell_face.end());
   ibuf.insert(ibuf.end(), fnode_m.begin(), fnode_m.end());
   ibuf.insert(ibuf.end(), fnode_p.begin(), fnode_p.end());
+  ibuf.insert(ibuf.end(), cell_cmask.begin(), cell_cmask.end());
   DG_CUDA(cudaMemcpy(m->d_int, ibuf.data(), ibuf.size() * sizeof(int), cudaMemcpyHostToDevice));
 
   std::vector<double> rbuf;
@@ -469,6 +474,7 @@ int build_mesh(dg_mesh* m) {
     v.cell_face = ib + 5 * (size_t)nf;
     v.fnode_m = v.cell_face + cell_face.size();
     v.fnode_p = v.fnode_m + (size_t)nf * NF;
+    v.cell_cmask = v.fnode_p + (size_t)nf * NF;
     v.gravity = (decltype(v.gravity))d.gravity;
   };
   fill(m->v64, (const double*)m->d_f64);

@@ -448,8 +448,8 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
   double* sD64 = t64;
   double* sDw64 = sD64 + N * N;
   double* sII64 = sDw64 + N * N;
-  double* scell64 = sII64 + 4 * N * N;      // cell tile, CPB*NC doubles (reused as TK)
-  double* sJ64 = scell64 + S::CPB * S::NC;  // coarse-pass buffer (reused as TK)
+  double* scell64 = sII64 + 4 * N * N;      // cell tile, DIM*CPB*NC doubles (reused as TK)
+  double* sJ64 = scell64 + DIM * S::CPB * S::NC;  // coarse-pass buffer (reused as TK)
   TK* tk = (TK*)(sJ64 + coarse_buffer<DIM, DEG, DIM>());
   TK* sDk = tk;
   TK* sDwk = sDk + N * N;
@@ -738,8 +738,8 @@ __device__ __forceinline__ void gmres_cgs2_body(const GmresPArgs<TK>& a, Sync& s
   double* sD64 = t64;
   double* sDw64 = sD64 + N * N;
   double* sII64 = sDw64 + N * N;
-  double* scell64 = sII64 + 4 * N * N;  // cell tile, CPB*NC doubles (reused as TK)
-  double* sJ64 = scell64 + S::CPB * S::NC;  // coarse-pass buffer (reused as TK)
+  double* scell64 = sII64 + 4 * N * N;  // cell tile, DIM*CPB*NC doubles (reused as TK)
+  double* sJ64 = scell64 + DIM * S::CPB * S::NC;  // coarse-pass buffer (reused as TK)
   TK* tk = (TK*)(sJ64 + coarse_buffer<DIM, DEG, DIM>());
   TK* sDk = tk;
   TK* sDwk = sDk + N * N;
@@ -975,7 +975,7 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
   double* sDw64 = sD64 + N * N;
   double* sII64 = sDw64 + N * N;
   double* scell64 = sII64 + 4 * N * N;
-  double* sJ64 = scell64 + S::CPB * S::NC;
+  double* sJ64 = scell64 + DIM * S::CPB * S::NC;
   TK* sDk = (TK*)(sJ64 + coarse_buffer<DIM, DEG, DIM>());
   TK* sDwk = sDk + N * N;
   TK* sIIk = sDwk + N * N;
@@ -1141,7 +1141,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
   double* sDw64 = sD64 + N * N;
   double* sII64 = sDw64 + N * N;
   double* scell64 = sII64 + 4 * N * N;
-  double* sJ64 = scell64 + S::CPB * S::NC;
+  double* sJ64 = scell64 + DIM * S::CPB * S::NC;
   TK* sDk = (TK*)(sJ64 + coarse_buffer<DIM, DEG, DIM>());
   TK* sDwk = sDk + N * N;
   TK* sIIk = sDwk + N * N;
@@ -1403,7 +1403,7 @@ inline size_t gmres_smem_bytes(int m) {
   using S = Shape<DIM, DEG>;
   const size_t dbl = (size_t)(m + 1) + 2 * (size_t)(m + 2) + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m +
                      (m + 1) + 32 + 8 + 512;
-  const size_t tabs = (size_t)(6 * N * N + S::CPB * S::NC + coarse_buffer<DIM, DEG, DIM>()) * sizeof(double) +
+  const size_t tabs = (size_t)(6 * N * N + DIM * S::CPB * S::NC + coarse_buffer<DIM, DEG, DIM>()) * sizeof(double) +
                       (size_t)(6 * N * N) * sizeof(TK);
   const size_t gm = dbl * sizeof(double) + 4 * sizeof(int) + tabs + 64;
   const size_t d1 = 2 * (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 5 * (size_t)(m + 1) + 32 + 8 + 1024;

@@ -82,14 +82,19 @@ __host__ __device__ constexpr int coarse_buffer() {
   return Shape<DIM, DEG>::CPB * NV * coarse_points<DIM, DEG>();
 }
 
-// bit lf set if local face lf of cell c is the coarse side of a 2:1 face
-template <int DIM, typename T>
-__device__ __forceinline__ unsigned coarse_mask(const MeshView<T>& mv, int64_t c) {
-  unsigned m = 0;
-#pragma unroll
-  for (int lf = 0; lf < 2 * DIM; ++lf)
-    if ((mv.cell_face[c * 2 * DIM + lf] & 3) == 2) m |= 1u << lf;
-  return m;
+// OR over the cells of batch `batch` of their coarse-side face masks, formed by
+// every warp on its own (lanes load one or two cells' masks and reduce), so
+// that the whole block agrees without a barrier
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ unsigned batch_coarse_mask(const MeshView<T>& mv, int64_t batch) {
+  constexpr int CPB = Shape<DIM, DEG>::CPB;
+  const int lane = threadIdx.x & 31;
+  unsigned m = 0u;
+  for (int j = lane; j < CPB; j += 32) {
+    const int64_t c = batch * CPB + j;
+    if (c < mv.n_cells) m |= (unsigned)mv.cell_cmask[c];
+  }
+  return __reduce_or_sync(0xffffffffu, m);
 }
 
 // Coarse sides of the batch's 2:1 faces, one local face at a time.  For every
@@ -97,18 +102,19 @@ __device__ __forceinline__ unsigned coarse_mask(const MeshView<T>& mv, int64_t c
 // face values of fine point q of subface s (face f + s) to the buffer at
 // sJ[(lc * NV + v) * NP + j], j = s * NF + q; then each node of that face adds
 // sum_s sum_q weight * value to acc[0..NV) with weight = sign * It.  Called by
-// the whole block (contains __syncthreads; returns at once if no cell of the
-// batch has a coarse side).
+// the whole block with the batch's mask bmask (the same in every thread);
+// contains __syncthreads only for the faces some cell of the batch has.
 template <int DIM, int DEG, typename T, int NV, class Point>
 __device__ __forceinline__ void coarse_pass(const MeshView<T>& mv, bool active, int64_t c, int lc, int i,
-                                            const int* id, unsigned cmask, const T* sIt, T sign, T* sJ, T* acc,
+                                            const int* id, unsigned bmask, const T* sIt, T sign, T* sJ, T* acc,
                                             Point&& point) {
   using S = Shape<DIM, DEG>;
   constexpr int NF = S::NF, NC = S::NC, NP = coarse_points<DIM, DEG>();
-  if (!__syncthreads_or(active && cmask != 0u)) return;
+  if (bmask == 0u) return;
+  const unsigned cmask = active ? (unsigned)mv.cell_cmask[c] : 0u;
   for (int lf = 0; lf < 2 * DIM; ++lf) {
-    const bool mine = active && ((cmask >> lf) & 1u);
-    if (!__syncthreads_or(mine)) continue;
+    if (!((bmask >> lf) & 1u)) continue;
+    const bool mine = (cmask >> lf) & 1u;
     const int a = lf >> 1;
     const int f = mine ? (mv.cell_face[c * 2 * DIM + lf] >> 2) : 0;
     if (mine)
@@ -178,12 +184,11 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   int codes[DIM];
   T Jl[DIM][DIM];
   T scale = T(0), pv = T(0);
-  unsigned cmask = 0u;
+  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch);
   if (active) {
     pv = p[idx];
     sp[lc * NC + i] = pv;
     load_face_codes<DIM, DEG, T>(mv, c, id, codes);
-    cmask = coarse_mask<DIM, T>(mv, c);
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
@@ -209,7 +214,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   }
   // coarse sides: jump at each fine point from the fine value and the cell's own polynomial
   const int64_t total = (int64_t)mv.nf * NF;
-  coarse_pass<DIM, DEG, T, DIM>(mv, active, c, lc, i, id, cmask, sII + 2 * N * N, T(1), sJ, facc,
+  coarse_pass<DIM, DEG, T, DIM>(mv, active, c, lc, i, id, bmask, sII + 2 * N * N, T(1), sJ, facc,
                                 [&](int f, int lf, int s, int q, int j) {
                                   const int64_t t = (int64_t)(f + s) * NF + q;
                                   const T pm = p[mv.fnode_m[t]];
@@ -276,7 +281,7 @@ __device__ __forceinline__ void div_face_terms(const MeshView<T>& mv, const T* _
 // Cells of one batch: epi(idx, v) receives v = HELM ? scale * (ident p/(gamma-1) - alpha div) : div
 // at every node of the batch (the caller stores it, or fuses further pointwise work).
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
-// sJ: coarse-pass buffer (coarse_buffer<DIM, DEG, 1>() elements).
+// sF: DIM * CPB * NC elements; sJ: coarse-pass buffer (coarse_buffer<DIM, DEG, 1>() elements).
 template <int DIM, int DEG, typename T, bool HELM, class Epi>
 __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
                                                const T* __restrict__ p, T alpha, T scale, T ident, Epi& epi,
@@ -293,12 +298,11 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   T ft[DIM];  // Ja^a . f for each axis a
   T fv[DIM];
   T ij = T(0), pv = T(0);
-  unsigned cmask = 0u;
+  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch);
   if (active) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fv[b] = fld[(int64_t)b * Nn + idx];
     load_face_codes<DIM, DEG, T>(mv, c, id, codes);
-    cmask = coarse_mask<DIM, T>(mv, c);
     ij = mv.invJ[idx];
     if (HELM) pv = p[idx];
 #pragma unroll
@@ -309,25 +313,28 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       ft[a] = s;
     }
   }
-  T acc = T(0);
+  // all DIM contravariant components staged at once (sF holds DIM * CPB * NC)
+  if (active) {
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    if (active) sF[lc * NC + i] = ft[a];
-    __syncthreads();
-    if (active) {
+    for (int a = 0; a < DIM; ++a) sF[(a * CPB + lc) * NC + i] = ft[a];
+  }
+  __syncthreads();
+  T acc = T(0);
+  if (active) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
       const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
-      const int i0 = lc * NC + i - id[a] * stride;
+      const int i0 = (a * CPB + lc) * NC + i - id[a] * stride;
       const T* Dw = sDw + id[a] * N;
 #pragma unroll
       for (int kk = 0; kk < N; ++kk) acc -= Dw[kk] * sF[i0 + kk * stride];
     }
-    __syncthreads();
   }
   T facc = T(0);
   if (active) div_face_terms<DIM, DEG, T>(mv, fld, codes, id, fv, sII, &facc);
   // coarse sides: |N| {f}.n at each fine point from the fine value and the cell's own polynomial
   const int64_t total = (int64_t)mv.nf * NF;
-  coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, cmask, sII + 2 * N * N, T(-1), sJ, &facc,
+  coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, bmask, sII + 2 * N * N, T(-1), sJ, &facc,
                               [&](int f, int lf, int s, int q, int j) {
                                 const int64_t t = (int64_t)(f + s) * NF + q;
                                 const int64_t im = mv.fnode_m[t];
@@ -346,6 +353,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     else
       epi(idx, dv);
   }
+  __syncthreads();  // sF and sJ are rewritten by the next batch
 }
 
 // ---------------------------------------------------------------- two-pass form

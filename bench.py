@@ -55,6 +55,20 @@ def algorithmic(dim, degree, n_nodes, kind, s=8):
     return flops * n_nodes, byts * n_nodes
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' x (the job's time is that of its slowest replica)."""
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, dof, steps, total_ms):
+    """DoF-steps per second of the whole job: every rank advances its own replica of `dof` DoF."""
+    return world * dof * steps / (total_ms / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -425,12 +439,10 @@ def main():
     dg.dg_profile_enable(ctx, False)
     total_ms = sum(times)
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
         dist.barrier()
     dof = mesh.n_dof
-    value = world * dof * args.steps / (total_ms / 1e3)
+    value = whole_job_value(world, dof, args.steps, total_ms)
 
     U64 = state.download()
 

@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel as it
 # stands (profiles/persistent_solve_hill2d.md: the persistent solve with the autotuned Chebyshev
 # body, FP64); set to None whenever that kernel changes
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {("hill2d", "chebyshev", "fp64"): 5.85984e6 + 0.137984e6}
 
 
 def algorithmic(dim, degree, n_nodes, kind, s=8):
@@ -168,6 +168,53 @@ def run_reference(args):
         "e2e": {"value": cb["value"], "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+def precision_forms_3d(dg, torch, case_name="hill3d", steps=2, inner_tol=1e-6):
+    """The 3D workload stepped in FP64 and in the FP32-refined form from the same start (autotuned
+    solver each): time per step and the FP32 form's deviation from the FP64 result."""
+    import numpy as np
+    from workloads import make_case
+
+    case = make_case(case_name, 0)
+    ctx = dg.Context(torch.cuda.current_device())
+    mesh = dg.Mesh(ctx, case)
+    st = dg.State(ctx, mesh)
+    kind, params = dg.api.init_params(case)
+    dg.dg_init_state(ctx, mesh, kind, params, st.U)
+    U0 = st.download()
+    bg = torch.empty(mesh.shape(), dtype=torch.float64, device="cuda")
+    dg.dg_background(ctx, mesh, bg)
+    bg = bg.cpu().numpy()
+    stream = torch.cuda.current_stream()
+    out, res = {}, {}
+    for name, prec in (("fp64", dg.DG_FP64), ("fp32_refined", dg.DG_FP32)):
+        o = dg.solver_opts(tol=1e-12, precision=prec, inner_tol=inner_tol)
+        st.upload(U0)
+        dg.imex_rk2_step(ctx, mesh, st, case.dt, o)  # warm-up (and the autotuner's first solve)
+        st.upload(U0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            dg.imex_rk2_step(ctx, mesh, st, case.dt, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = st.download()
+        out[name] = {"ms_per_step": ms, "dof_steps_per_s": mesh.n_dof / (ms / 1e3),
+                     "solver": mesh.autotuned()[name[:4]]["form"]}
+    dev = max(np.linalg.norm(res["fp32_refined"][v] - res["fp64"][v])
+              / max(np.linalg.norm(res["fp64"][v] - bg[v]), 1e-300) for v in range(mesh.n_vars))
+    out["fp32_refined"]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32_refined"]["ms_per_step"]
+    out["fp32_refined"]["rel_err_vs_fp64_deviation"] = dev
+    out["workload"] = "%s: %d cells, degree %d, %d DoF, %d IMEX-RK2 steps per form" % (
+        case_name, mesh.n_cells, case.degree, mesh.n_dof, steps)
+    st.close()
+    mesh.close()
+    ctx.close()
+    return out
 
 
 def apply_sweep(dg, torch, case_name, reps=10):
@@ -595,6 +642,7 @@ def main():
     }
     if rank == 0 and not args.no_sweep:
         line["applies"] = apply_sweep(dg, torch, args.sweep_workload)
+        line["precision_forms_3d"] = precision_forms_3d(dg, torch, inner_tol=args.inner_tol)
     if rank == 0 and not args.no_ensemble:
         line["ensemble"] = ensemble_bench(dg, torch, inner_tol=args.inner_tol)
         line["serving"] = serving_bench(dg, torch, inner_tol=args.inner_tol)

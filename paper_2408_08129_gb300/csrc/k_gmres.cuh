@@ -166,6 +166,33 @@ __device__ __forceinline__ double block_sum(double v, double* sred) {
   return r;
 }
 
+// FP32 sum over the block (shuffle tree per warp, then over the warp sums);
+// the result in thread 0; sred is used as float storage
+__device__ __forceinline__ float block_sum_f(float v, double* sred) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int nw = (int)(blockDim.x + 31) >> 5;
+  float* sf = (float*)sred;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = 0.0f;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < nw ? sf[threadIdx.x] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
+// the same, returned to every thread
+__device__ __forceinline__ float block_allsum_f(float v, double* sred) {
+  const float r = block_sum_f(v, sred);
+  if (threadIdx.x == 0) ((float*)sred)[0] = r;
+  __syncthreads();
+  return ((float*)sred)[0];
+}
+
 // FP64 sum over the block, returned to every thread
 __device__ __forceinline__ double block_allsum(double v, double* sred) {
   const double r = block_sum(v, sred);
@@ -1277,19 +1304,22 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     const double sk = sqrt(lmax / lmin), q = (sk - 1.0) / (sk + 1.0);
     const int cycle_cap = 2 * (int)ceil(log(0.5 * floor / beta) / log(q)) + 20;
     int cycle_its = 0;
+    const TK ibeta = (TK)(1.0 / beta);
     double rho = 1.0 / sigma1;
     const int64_t nb = (a.mvk.n_cells + S::CPB - 1) / S::CPB;
     bool have_prev = false;  // residual partials of the previous step are waiting in a.partial
     while (true) {
       // gradient pass of A d_k; the previous step's residual norm is summed meanwhile
       // (its partial loads are issued before the pass, the sum after it)
-      double pv = 0.0;
+      // The stop test needs the residual norm to a few digits only: its sums run in FP32 on
+      // the residual scaled by 1/beta (no FP64 shuffle trees on the step's critical path)
+      float pv = 0.0f;
       if (have_prev)
-        for (int i = threadIdx.x; i < G; i += blockDim.x) pv += a.partial[i];
+        for (int i = threadIdx.x; i < G; i += blockDim.x) pv += (float)a.partial[i];
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         grad_cell_batch<DIM, DEG, TK>(a.mvk, d, a.hk, gvk, bt, scellk, sJk, sDk, sIIk);
       if (have_prev) {
-        const double rn = sqrt(block_allsum(pv, sred));
+        const double rn = beta * sqrt((double)block_allsum_f(pv, sred));
         pc.mark(PH_UPDATE);
         if (!(rn <= 1e4 * beta) || (cycle_its > cycle_cap && rn > floor)) {  // growth, stall or NaN: bound too low
           diverged = true;
@@ -1302,7 +1332,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       // divergence pass with the update: x += d, r -= A d, d = c1 d + c2 r
       const double rho1 = 1.0 / (2.0 * sigma1 - rho);
       const TK c1 = (TK)(rho1 * rho), c2 = (TK)(2.0 * rho1 / delta);
-      TK racc = TK(0);
+      float racc = 0.0f;
       auto epi = [&](int64_t i, TK ad) {
         const TK di = d[i];
         const TK ri = r[i] - ad;
@@ -1312,14 +1342,15 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         else
           a.x[i] += (double)di;
         d[i] = c1 * di + c2 * ri;
-        racc += ri * ri;
+        const float rs = (float)(ri * ibeta);
+        racc += rs * rs;
       };
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         div_cell_batch<DIM, DEG, TK, true>(a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi, bt, scellk, sJk, sDwk,
                                            sIIk);
       {
-        const double t = block_sum_k<TK>(racc, sred);
-        if (threadIdx.x == 0) a.partial[sg.rank] = t;
+        const float t = block_sum_f(racc, sred);
+        if (threadIdx.x == 0) a.partial[sg.rank] = (double)t;
       }
       sg.sync();
       pc.mark(PH_DIV_CELL);

@@ -114,6 +114,12 @@ int dg_profile_reset(dg_ctx* ctx);
  * column and Givens rotation, 12 update coefficients, 13 basis update (work);
  * ns[14] = second passes, ns[15] = GMRES iterations.  Synchronises the device. */
 int dg_profile_read_gmres_phases(dg_ctx* ctx, double* ns);
+/* Self-test of the library's own FP64 math on the device (no counterpart in
+ * the paper): op 0 writes y[i] = 1/sqrt(x[i]) as computed by the Newton
+ * iteration the solvers use (FP32 seed, two Newton steps), for device arrays
+ * x, y of n doubles, x[i] > 0 and within the FP32 range.  Enqueued on stream.
+ * DG_EINVAL for another op or null arrays. */
+int dg_math_selftest(int op, const double* x, double* y, int64_t n, void* stream);
 /* Number of CUDA kernels the library has launched through this context so far. */
 int dg_launch_count(const dg_ctx* ctx, long long* out);
 

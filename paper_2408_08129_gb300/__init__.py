@@ -31,6 +31,7 @@ from .api import (  # noqa: F401
     dg_conservation,
     dg_init_state,
     dg_launch_count,
+    dg_math_selftest,
     dg_profile_enable,
     dg_profile_read,
     dg_profile_read_gmres_phases,

@@ -197,6 +197,12 @@ def dg_profile_read_gmres_phases(ctx):
     return out
 
 
+def dg_math_selftest(op, x, y, stream=None):
+    """Device self-test of the library's FP64 math (op 0: the Newton 1/sqrt); x, y: CUDA float64 tensors."""
+    check(lib.dg_math_selftest(int(op), _ptr(x), _ptr(y), x.numel(), _stream(stream)), "dg_math_selftest")
+    return y
+
+
 def dg_launch_count(ctx):
     n = ctypes.c_longlong(0)
     check(lib.dg_launch_count(ctx.handle, ctypes.byref(n)), "dg_launch_count")

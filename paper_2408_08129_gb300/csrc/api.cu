@@ -4,6 +4,7 @@
 #include <string>
 #include <vector>
 
+#include "dg_device.cuh"
 #include "ops.h"
 
 namespace dg {
@@ -319,5 +320,19 @@ extern "C" int dg_init_state(dg_ctx* ctx, const dg_mesh* m, int kind, const doub
   }
   DG_CUDA(cudaMemcpyAsync(U, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
   DG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return DG_OK;
+}
+
+__global__ void dg_newton_selftest_kernel(int op, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (op == 0) y[i] = dg::rsqrt64(x[i]);
+}
+
+extern "C" int dg_math_selftest(int op, const double* x, double* y, int64_t n, void* stream) {
+  if (op != 0 || n < 0 || (n > 0 && (!x || !y))) return dg::fail(DG_EINVAL, "bad arguments");
+  if (n == 0) return DG_OK;
+  dg_newton_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(op, x, y, n);
+  DG_CUDA(cudaGetLastError());
   return DG_OK;
 }

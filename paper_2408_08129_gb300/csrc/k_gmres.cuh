@@ -217,16 +217,6 @@ __device__ __forceinline__ double gather_allsum_strided(const double* part, int 
   return block_allsum(v, sred);
 }
 
-// 1/sqrt(x) for finite x > 0 in the FP32 range, in FP64: FP32 seed (relative
-// error ~1e-7), then two Newton steps y <- y (3 - x y^2) / 2, each of which
-// squares the relative error (1e-7 -> 1e-14 -> below FP64 rounding)
-__device__ __forceinline__ double rsqrt64(double x) {
-  double y = (double)rsqrtf((float)x);
-  const double hx = 0.5 * x;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) y = y * fma(-hx, y * y, 1.5);
-  return y;
-}
 
 // copy cnt global partial sums (no more than the staging area holds) into
 // shared memory with all threads

@@ -349,7 +349,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   if (active) {
     const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
     if (HELM)
-      epi(idx, scale * (ident * pv / gm1<T>() - alpha * dv));
+      epi(idx, scale * (ident * pv * inv_gm1<T>() - alpha * dv));
     else
       epi(idx, dv);
   }
@@ -520,7 +520,7 @@ __device__ __forceinline__ void div_gather_batch(const MeshView<T>& mv, const T*
     gather_faces_codes<DIM, DEG, T, 1>(mv, Dh, codes, id, sIt, T(1), T(-1), true, &facc);
     const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
     if (HELM)
-      out[idx] = scale * (ident * pv / gm1<T>() - alpha * dv);
+      out[idx] = scale * (ident * pv * inv_gm1<T>() - alpha * dv);
     else
       out[idx] = dv;
   }

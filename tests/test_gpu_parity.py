@@ -370,3 +370,16 @@ def test_damping_layer_parameters_validated(dg, ctx):
     for bad in (dict(depth=2e4, rate=0.1), dict(depth=1e3, rate=-1.0)):
         with pytest.raises(dg.DGError, match="sponge"):
             dg.Mesh(ctx, dataclasses.replace(case, sponge=bad))
+
+
+def test_newton_rsqrt_against_cuda(dg):
+    """The solvers' own FP64 1/sqrt (FP32 seed + two Newton steps) against CUDA's 1/sqrt: within
+    2 ulp over the whole FP32 exponent range the solvers use it on."""
+    rng = np.random.default_rng(5)
+    x = torch.from_numpy(10.0 ** rng.uniform(-30, 30, 1 << 16)).cuda()
+    y = torch.empty_like(x)
+    dg.dg_math_selftest(0, x, y)
+    ref = torch.rsqrt(x)
+    torch.cuda.synchronize()
+    ulp = torch.abs(y - ref) / (torch.abs(ref) * 2.0 ** -52)
+    assert float(ulp.max()) <= 2.0

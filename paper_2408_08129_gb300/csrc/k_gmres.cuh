@@ -459,8 +459,7 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
   double* dv = zc + (m + 1);         // [m+1] d
   double* sred = dv + (m + 1);       // [32]
   double* sc = sred + 32;            // [8]: 0 ||b||, 1 resid, 2 beta, 3 rho, 4 c
-  double* spart = sc + 8;            // [1024] staged block partials
-  int* sflag = (int*)(spart + 1024);  // [4]: 0 stop cycle, 1 converged
+  int* sflag = (int*)(sc + 8);       // [4]: 0 stop cycle, 1 converged
   double* t64 = (double*)(sflag + 4);  // FP64 tables D, Dw, I|It
   double* sD64 = t64;
   double* sDw64 = sD64 + N * N;
@@ -987,8 +986,7 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
   constexpr int N = S::N;
   double* sred = (double*)smem_raw;  // [32]
   double* sc = sred + 32;            // [16]
-  double* spart = sc + 16;           // [3*512]
-  double* sD64 = spart + 3 * 512;
+  double* sD64 = sc + 16;
   double* sDw64 = sD64 + N * N;
   double* sII64 = sDw64 + N * N;
   double* scell64 = sII64 + 4 * N * N;
@@ -1153,8 +1151,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
   constexpr int N = S::N;
   double* sred = (double*)smem_raw;  // [32]
   double* sc = sred + 32;            // [16]
-  double* spart = sc + 16;           // [512]
-  double* sD64 = spart + 3 * 512;
+  double* sD64 = sc + 16;
   double* sDw64 = sD64 + N * N;
   double* sII64 = sDw64 + N * N;
   double* scell64 = sII64 + 4 * N * N;
@@ -1427,9 +1424,9 @@ inline size_t gmres_smem_bytes(int m) {
   const size_t tabs = (size_t)(6 * N * N + DIM * S::CPB * S::NC + coarse_buffer<DIM, DEG, DIM>()) * sizeof(double) +
                       (size_t)(6 * N * N) * sizeof(TK);
   const size_t gm = dbl * sizeof(double) + 4 * sizeof(int) + tabs + 64;
-  const size_t d1 = 2 * (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 5 * (size_t)(m + 1) + 32 + 8 + 1024;
+  const size_t d1 = 2 * (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 5 * (size_t)(m + 1) + 32 + 8;
   const size_t g1 = d1 * sizeof(double) + 4 * sizeof(int) + tabs + 64;
-  const size_t cg = (size_t)(32 + 16 + 3 * 512) * sizeof(double) + tabs + 64;
+  const size_t cg = (size_t)(32 + 16) * sizeof(double) + tabs + 64;
   return std::max(gm, std::max(g1, cg));
 }
 

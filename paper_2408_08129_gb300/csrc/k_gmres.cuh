@@ -1291,34 +1291,50 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     const double sk = sqrt(lmax / lmin), q = (sk - 1.0) / (sk + 1.0);
     const int cycle_cap = 2 * (int)ceil(log(0.5 * floor / beta) / log(q)) + 20;
     int cycle_its = 0;
-    const TK ibeta = (TK)(1.0 / beta);
+    const float ibeta = (float)(1.0 / beta);
+    // the stop test compares (||r|| / beta)^2 with squared limits (no square root per step);
+    // the floor is kept above FP32 underflow (a cycle then ends at a 1e-15 reduction and the
+    // FP64 restart decides)
+    const double fr = floor / beta;
+    const float floor2 = fmaxf((float)(fr * fr), 1e-30f);
+    constexpr float kGrowth2 = 1e8f;  // (1e4)^2
+    const double two_idelta = 2.0 / delta;
     double rho = 1.0 / sigma1;
     const int64_t nb = (a.mvk.n_cells + S::CPB - 1) / S::CPB;
     bool have_prev = false;  // residual partials of the previous step are waiting in a.partial
     while (true) {
+      // the next step's recurrence coefficients, by one thread, while the others start the
+      // gradient pass (the FP64 division is off the critical path); read after the grid
+      // barrier, and rewritten only after the divergence pass's block barriers
+      if (threadIdx.x == blockDim.x - 1) {
+        const double rho1 = 1.0 / (2.0 * sigma1 - rho);
+        sc[0] = rho1;
+        sc[1] = rho1 * rho;
+        sc[2] = rho1 * two_idelta;
+      }
       // gradient pass of A d_k; the previous step's residual norm is summed meanwhile
       // (its partial loads are issued before the pass, the sum after it)
       // The stop test needs the residual norm to a few digits only: its sums run in FP32 on
       // the residual scaled by 1/beta (no FP64 shuffle trees on the step's critical path)
       float pv = 0.0f;
       if (have_prev)
-        for (int i = threadIdx.x; i < G; i += blockDim.x) pv += (float)a.partial[i];
+        for (int i = threadIdx.x; i < G; i += blockDim.x) pv += ((const float*)a.partial)[i];
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         grad_cell_batch<DIM, DEG, TK>(a.mvk, d, a.hk, gvk, bt, scellk, sJk, sDk, sIIk);
       if (have_prev) {
-        const double rn = beta * sqrt((double)block_allsum_f(pv, sred));
+        const float rn2 = block_allsum_f(pv, sred);  // (||r|| / beta)^2
         pc.mark(PH_UPDATE);
-        if (!(rn <= 1e4 * beta) || (cycle_its > cycle_cap && rn > floor)) {  // growth, stall or NaN: bound too low
+        if (!(rn2 <= kGrowth2) || (cycle_its > cycle_cap && rn2 > floor2)) {  // growth, stall or NaN: bound too low
           diverged = true;
           break;
         }
-        if (rn <= floor || total >= a.max_iters || sg.failed()) break;  // same decision in every CTA
+        if (rn2 <= floor2 || total >= a.max_iters || sg.failed()) break;  // same decision in every CTA
       }
       sg.sync();
       pc.mark(PH_GRAD_CELL);
       // divergence pass with the update: x += d, r -= A d, d = c1 d + c2 r
-      const double rho1 = 1.0 / (2.0 * sigma1 - rho);
-      const TK c1 = (TK)(rho1 * rho), c2 = (TK)(2.0 * rho1 / delta);
+      const double rho1 = sc[0];
+      const TK c1 = (TK)sc[1], c2 = (TK)sc[2];
       float racc = 0.0f;
       auto epi = [&](int64_t i, TK ad) {
         const TK di = d[i];
@@ -1329,7 +1345,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         else
           a.x[i] += (double)di;
         d[i] = c1 * di + c2 * ri;
-        const float rs = (float)(ri * ibeta);
+        const float rs = (float)ri * ibeta;  // FP32: no FP64 instruction for the stop test
         racc += rs * rs;
       };
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
@@ -1337,7 +1353,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
                                            sIIk);
       {
         const float t = block_sum_f(racc, sred);
-        if (threadIdx.x == 0) a.partial[sg.rank] = (double)t;
+        if (threadIdx.x == 0) ((float*)a.partial)[sg.rank] = t;  // FP32 partials for the stop test
       }
       sg.sync();
       pc.mark(PH_DIV_CELL);

@@ -1190,7 +1190,16 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     if (threadIdx.x == 0) a.partial[sg.rank] = t;
   }
   sg.sync();
-  const double bn = sqrt(gather_sum());
+  // Scalar functions of block-uniform values (square roots, divisions, logarithms) are
+  // evaluated by thread 0 and read by the others from sc[3..15]: evaluated by every warp,
+  // each would occupy the FP64 pipe once per warp.  Every slot is read right after the
+  // barrier that follows its write, and rewritten only after further block barriers.
+  {
+    const double bsum = gather_sum();
+    if (threadIdx.x == 0) sc[13] = sqrt(bsum);
+    __syncthreads();
+  }
+  const double bn = sc[13];
   if (bn == 0.0) {
     for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
     if (sg.rank == 0 && threadIdx.x == 0) {
@@ -1223,7 +1232,12 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       if (threadIdx.x == 0) a.partial[sg.rank] = t;
     }
     sg.sync();
-    double inv = 1.0 / sqrt(gather_sum());
+    {
+      const double s0 = gather_sum();
+      if (threadIdx.x == 0) sc[14] = 1.0 / sqrt(s0);
+      __syncthreads();
+    }
+    double inv = sc[14];
     TK* pin = r;
     TK* pout = w;
     double est = 0.0;
@@ -1239,8 +1253,17 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       };
       pmatvec_epi<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(1), pin, (TK)inv, epi, fin, gvk, sg, scellk, sJk,
                                       sDk, sDwk, sIIk, pc);
-      est = sqrt(gather_sum());  // ||A p^|| with ||p^|| = 1 in the w J norm
-      inv = est > 0.0 ? 1.0 / est : 0.0;
+      {
+        const double s1 = gather_sum();
+        if (threadIdx.x == 0) {
+          const double e = sqrt(s1);  // ||A p^|| with ||p^|| = 1 in the w J norm
+          sc[15] = e;
+          sc[14] = e > 0.0 ? 1.0 / e : 0.0;
+        }
+        __syncthreads();
+      }
+      est = sc[15];
+      inv = sc[14];
       TK* t = pin;
       pin = pout;
       pout = t;
@@ -1253,8 +1276,19 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       a.lmax[1] = a.alpha;
     }
   }
-  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
-  const double sigma1 = theta / delta;
+  // theta, delta: centre and half width of [lmin, lmax]; sigma1 = theta / delta; q the
+  // Chebyshev convergence factor (sqrt(kappa) - 1) / (sqrt(kappa) + 1)
+  if (threadIdx.x == 0) {
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    const double sk = sqrt(lmax / lmin);
+    sc[8] = theta / delta;
+    sc[9] = 1.0 / theta;
+    sc[10] = 2.0 / delta;
+    sc[11] = delta / theta;
+    sc[12] = log((sk - 1.0) / (sk + 1.0));
+  }
+  __syncthreads();
+  const double sigma1 = sc[8], itheta = sc[9], two_idelta = sc[10], rho0 = sc[11], logq = sc[12];
 
   int total = 0;
   double rel = 1.0;
@@ -1264,7 +1298,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.gv, sg, scell64, sJ64, sD64,
                                     sDw64, sII64, pc);
     acc = 0.0;
-    const TK ith = (TK)(1.0 / theta);
+    const TK ith = (TK)itheta;
     for (int64_t i = tid; i < n; i += gstride) {
       const double ri = a.b[i] - a.w64[i];
       r[i] = (TK)ri;
@@ -1278,28 +1312,37 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     }
     sg.sync();
     pc.mark(PH_RESIDUAL);
-    const double beta = sqrt(gather_sum());
-    rel = beta / bn;
+    {
+      const double rsum = gather_sum();
+      if (threadIdx.x == 0) {
+        const double beta = sqrt(rsum);
+        const double floor = fmax(a.tol * bn, (mixed ? a.inner_tol : 0.0) * beta);
+        const double ib = 1.0 / beta, fr = floor * ib;
+        sc[3] = beta;
+        // steps the Chebyshev bound 2 q^k needs to reach the floor; well past that, the
+        // residual has stalled or grows slowly (a bound a little low)
+        sc[4] = fmin(2.0 * ceil(log(0.5 * fr) / logq) + 20.0, 1e9);
+        sc[5] = ib;
+        sc[6] = fr * fr;
+        rel = beta / bn;  // reported by thread 0
+      }
+      __syncthreads();
+    }
+    const double beta = sc[3];
     if (beta <= a.tol * bn) {
       converged = true;
       break;
     }
     if (total >= a.max_iters) break;
-    const double floor = fmax(a.tol * bn, (mixed ? a.inner_tol : 0.0) * beta);
-    // steps the Chebyshev bound 2 q^k (q = (sqrt(kappa)-1)/(sqrt(kappa)+1)) needs to reach the
-    // floor; well past that, the residual has stalled or grows slowly (a bound a little low)
-    const double sk = sqrt(lmax / lmin), q = (sk - 1.0) / (sk + 1.0);
-    const int cycle_cap = 2 * (int)ceil(log(0.5 * floor / beta) / log(q)) + 20;
+    const int cycle_cap = (int)sc[4];
     int cycle_its = 0;
-    const float ibeta = (float)(1.0 / beta);
+    const float ibeta = (float)sc[5];
     // the stop test compares (||r|| / beta)^2 with squared limits (no square root per step);
     // the floor is kept above FP32 underflow (a cycle then ends at a 1e-15 reduction and the
     // FP64 restart decides)
-    const double fr = floor / beta;
-    const float floor2 = fmaxf((float)(fr * fr), 1e-30f);
+    const float floor2 = fmaxf((float)sc[6], 1e-30f);
     constexpr float kGrowth2 = 1e8f;  // (1e4)^2
-    const double two_idelta = 2.0 / delta;
-    double rho = 1.0 / sigma1;
+    double rho = rho0;
     const int64_t nb = (a.mvk.n_cells + S::CPB - 1) / S::CPB;
     bool have_prev = false;  // residual partials of the previous step are waiting in a.partial
     while (true) {

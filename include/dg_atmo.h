@@ -120,6 +120,18 @@ int dg_profile_read_gmres_phases(dg_ctx* ctx, double* ns);
  * x, y of n doubles, x[i] > 0 and within the FP32 range.  Enqueued on stream.
  * DG_EINVAL for another op or null arrays. */
 int dg_math_selftest(int op, const double* x, double* y, int64_t n, void* stream);
+/* Test hook for the bounded barrier of batched launches (dg_batch_step and
+ * batch plans captured afterwards; no counterpart in the paper).  Every wait
+ * at a member's barrier inside a batched launch gives up after
+ * barrier_limit_s seconds (2 s by default; accepted range 1e-3 .. 10), raises
+ * the launch's error flag and lets every later barrier of the launch return
+ * at once, so the step returns DG_ETIMEOUT instead of hanging.  With
+ * missing_cta_member >= 0, the member at that position in each batched
+ * launch's member list is told it has one CTA more than the launch gives it,
+ * so its first barrier can never complete and its wait runs out (nothing
+ * faults: the kernel only returns early); -1 turns this off.  Host-side
+ * setting of the context, read when a batched launch is enqueued. */
+int dg_batch_barrier_test(dg_ctx* ctx, double barrier_limit_s, int missing_cta_member);
 /* Number of CUDA kernels the library has launched through this context so far. */
 int dg_launch_count(const dg_ctx* ctx, long long* out);
 

@@ -22,6 +22,7 @@ from .api import (  # noqa: F401
     Server,
     State,
     dg_apply_div,
+    dg_batch_barrier_test,
     dg_batch_step,
     dg_apply_explicit,
     dg_apply_grad,

@@ -203,6 +203,12 @@ def dg_math_selftest(op, x, y, stream=None):
     return y
 
 
+def dg_batch_barrier_test(ctx, barrier_limit_s=2.0, missing_cta_member=-1):
+    """Bounded-barrier test hook of batched launches (see include/dg_atmo.h)."""
+    check(lib.dg_batch_barrier_test(ctx.handle, float(barrier_limit_s), int(missing_cta_member)),
+          "dg_batch_barrier_test")
+
+
 def dg_launch_count(ctx):
     n = ctypes.c_longlong(0)
     check(lib.dg_launch_count(ctx.handle, ctypes.byref(n)), "dg_launch_count")
@@ -457,3 +463,8 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def last_error():
+    """Message of the last non-OK status returned by the library on this thread."""
+    return lib.dg_last_error().decode(errors="replace")

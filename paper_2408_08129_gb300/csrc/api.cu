@@ -184,6 +184,15 @@ extern "C" int dg_profile_read(dg_ctx* c, double* ms, long long* counts) {
   return DG_OK;
 }
 
+extern "C" int dg_batch_barrier_test(dg_ctx* c, double barrier_limit_s, int missing_cta_member) {
+  if (!c) return fail(DG_EINVAL, "null context");
+  if (!(barrier_limit_s >= 1e-3 && barrier_limit_s <= 10.0)) return fail(DG_EINVAL, "barrier limit must be in 1e-3..10 s");
+  if (missing_cta_member < -1) return fail(DG_EINVAL, "missing_cta_member must be >= -1");
+  c->batch_timeout_ns = (unsigned long long)(barrier_limit_s * 1e9);
+  c->batch_missing_cta_member = missing_cta_member;
+  return DG_OK;
+}
+
 extern "C" int dg_launch_count(const dg_ctx* c, long long* out) {
   if (!c || !out) return fail(DG_EINVAL, "null argument");
   *out = c->launches;

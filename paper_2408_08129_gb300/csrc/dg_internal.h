@@ -105,6 +105,10 @@ struct dg_ctx {
   void* d_batch = nullptr;  // workspace of batched solves (argument table, CTA map, barriers)
   size_t batch_bytes = 0;
   int* d_batch_err = nullptr;  // barrier-timeout flag of batched launches
+  // bounded barrier of batched launches: the wait limit, and a test hook that
+  // declares one CTA more for one member than its launch gives it (-1: off)
+  unsigned long long batch_timeout_ns = 2000000000ull;
+  int batch_missing_cta_member = -1;
   dg::BatchArena* arena = nullptr;  // set while a batch plan is being captured
 };
 

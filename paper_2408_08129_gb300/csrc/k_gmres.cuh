@@ -90,9 +90,9 @@ struct PhaseClock {
 // cooperative launch (cooperative-groups barrier).  SubSync: the CTAs of one
 // member of a batched launch (a generation barrier on two global counters;
 // all CTAs of a cooperative launch are co-resident, so it cannot deadlock).
-// Its wait is bounded: after kBarrierTimeoutNs it raises the launch's error
-// flag and every barrier of the launch returns at once from then on, so a
-// fault can only end the kernel early, never hang it.
+// Its wait is bounded: after limit_ns (a launch parameter, 2 s by default) it
+// raises the launch's error flag and every barrier of the launch returns at
+// once from then on, so a fault can only end the kernel early, never hang it.
 struct GridSync {
   cooperative_groups::grid_group grid;
   int rank, size;
@@ -101,7 +101,7 @@ struct GridSync {
   __device__ __forceinline__ bool failed() const { return false; }
 };
 
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s, the default limit
 
 struct SubSync {
   int rank, size;
@@ -109,6 +109,7 @@ struct SubSync {
   unsigned int* gen;    // barrier generation
   int* err;             // launch-wide error flag
   int* sfail;           // shared-memory copy of err, read by every thread
+  unsigned long long limit_ns;  // bound of one wait
   __device__ __forceinline__ void sync() {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -124,7 +125,7 @@ struct SubSync {
           const unsigned long long t0 = PhaseClock::now();
           while (*(volatile unsigned int*)gen == g) {
             if (*(volatile int*)err) break;
-            if (PhaseClock::now() - t0 > kBarrierTimeoutNs) {
+            if (PhaseClock::now() - t0 > limit_ns) {
               atomicExch(err, 1);
               break;
             }
@@ -1408,9 +1409,10 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     if (fold)
       for (int64_t i = tid; i < n; i += gstride) a.x[i] += (double)dx[i];
     // CTAs may leave the loop inside a gradient pass (whose scratch aliases the
-    // FP64 residual's): meet before the next pass
+    // FP64 residual's): meet before the next pass.  At max_iters the loop still
+    // goes round once more, so that the reported residual is the final one.
     sg.sync();
-    if (diverged || total >= a.max_iters) break;
+    if (diverged) break;
   }
   if (diverged) {
     if (sg.rank == 0 && threadIdx.x == 0) a.lmax[0] = 0.0;  // re-estimate on the next solve
@@ -1452,6 +1454,7 @@ struct BatchMap {
   unsigned int* bar_count;  // [members]
   unsigned int* bar_gen;    // [members]
   int* err;                 // [1]
+  unsigned long long timeout_ns;  // bound of every barrier wait
 };
 
 template <int DIM, int DEG, typename TK>
@@ -1462,7 +1465,7 @@ __global__ void __launch_bounds__(256, 2) gmres_batched_kernel(const GmresPArgs<
   if (threadIdx.x == 0) sfail = 0;
   __syncthreads();
   SubSync sg{map.cta_rank[blockIdx.x], map.member_ctas[mem], map.bar_count + mem, map.bar_gen + mem, map.err,
-             &sfail};
+             &sfail, map.timeout_ns};
   const GmresPArgs<TK> a = args[mem];
   if (a.method == 1)
     cg_body<DIM, DEG, TK, SubSync>(a, sg, smem_raw, false);

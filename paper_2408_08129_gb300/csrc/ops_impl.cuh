@@ -214,6 +214,9 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
     std::memcpy(hm, cta_member.data(), G * sizeof(int));
     std::memcpy(hm + G, cta_rank.data(), G * sizeof(int));
     std::memcpy(hm + 2 * G, ctas.data(), B * sizeof(int));
+    const int miss = ctx->batch_missing_cta_member - first;
+    // test hook: declare a CTA that never arrives (kept within the partial-sum buffers' bounds)
+    if (miss >= 0 && miss < B && ctas[miss] + 1 <= std::min(512, it[miss].npartial / 3)) hm[2 * G + miss] += 1;
     if (!ctx->arena) DG_CUDA(cudaMemcpyAsync(dev, host, b_args + b_map, cudaMemcpyHostToDevice, s));
     DG_CUDA(cudaMemsetAsync(dev + b_args + b_map, 0, b_bar, s));
     BatchMap map;
@@ -224,6 +227,7 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
     map.bar_count = (unsigned int*)(dev + b_args + b_map);
     map.bar_gen = map.bar_count + B;
     map.err = err;
+    map.timeout_ns = ctx->batch_timeout_ns;
     const GmresPArgs<TK>* dargs = (const GmresPArgs<TK>*)dev;
     count_launches(ctx, 1);
     void* kargs[] = {(void*)&dargs, (void*)&map};

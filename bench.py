@@ -38,8 +38,8 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 4 FP64 flop/clk/SM x 2.0
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel as it
-# stands (profiles/persistent_solve_hill2d.md: the persistent solve with the autotuned Chebyshev
-# body, FP64); set to None whenever that kernel changes
+# stands (the persistent solve with the autotuned Chebyshev body, FP64, on hill2d); set to None
+# whenever that kernel changes
 NCU_TRAFFIC_BYTES = {("hill2d", "chebyshev", "fp64"): 5.856768e6 + 0.147712e6}
 
 

@@ -132,6 +132,14 @@ int dg_math_selftest(int op, const double* x, double* y, int64_t n, void* stream
  * faults: the kernel only returns early); -1 turns this off.  Host-side
  * setting of the context, read when a batched launch is enqueued. */
 int dg_batch_barrier_test(dg_ctx* ctx, double barrier_limit_s, int missing_cta_member);
+/* Arithmetic-throughput probe (no counterpart in the paper; the ALU peaks the
+ * operator kernels are reported against): enqueue on `stream` one kernel of
+ * `blocks` CTAs x 256 threads, each thread running 16 independent fused
+ * multiply-add chains for `iters` steps in DG_FP64 or DG_FP32; `out` is a
+ * device array of blocks*256 elements of that type (receives the chains'
+ * sums).  *flops receives the floating-point operations the kernel performs
+ * (2 per FMA); the caller times the launch, e.g. with CUDA events. */
+int dg_peak_fma(int precision, int64_t iters, int blocks, void* out, void* stream, double* flops);
 /* Number of CUDA kernels the library has launched through this context so far. */
 int dg_launch_count(const dg_ctx* ctx, long long* out);
 
@@ -241,15 +249,19 @@ int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* mesh, const void* h, const voi
                       int precision, void* stream);
 /* The Helmholtz operator of dg_apply_implicit, for callers that cannot
  * allocate device memory (no cudaMalloc, no allocating library routine):
- * same arguments and result, but the two scratch buffers the operator needs
- * (face values and the h-scaled gradient) come from a fixed 4 MiB array
- * compiled into the library, held by every GPU that loads the library until
- * the process exits.  The paper has no counterpart; this is a deployment aid.
- *  - Meshes whose scratch, dim*(faces*face_nodes) + dim*n_nodes elements
- *    (8 bytes each for DG_FP64, 4 for DG_FP32), exceeds 4 MiB are rejected
- *    with DG_EINVAL and a message giving the bytes needed.
+ * same arguments and result, bit for bit, but the one scratch buffer the
+ * operator needs (the h-scaled gradient between its two launches) comes from
+ * a fixed 4 MiB array compiled into the library, held by every GPU that loads
+ * the library until the process exits.  The paper has no counterpart; this
+ * is a deployment aid.
+ *  - Meshes whose scratch, dim*n_nodes elements (8 bytes each for DG_FP64, 4
+ *    for DG_FP32), exceeds 4 MiB are rejected with DG_EINVAL and a message
+ *    giving the bytes needed.
  *  - The first call on a device looks up the array's device address with that
- *    device current; make that first call before any stream capture.
+ *    device current; make that first call before any stream capture.  Calls
+ *    outside a capture look the address up again (a device reset reloads the
+ *    library's module and moves the array); calls during a capture use the
+ *    address found before it.
  *  - Every call on a device shares the one array and leaves its contents
  *    behind; each call writes every scratch element before reading it, so no
  *    clearing is needed.  Calls whose executions overlap on the GPU (other

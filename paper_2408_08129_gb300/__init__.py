@@ -33,6 +33,7 @@ from .api import (  # noqa: F401
     dg_init_state,
     dg_launch_count,
     dg_math_selftest,
+    dg_peak_fma,
     dg_profile_enable,
     dg_profile_read,
     dg_profile_read_gmres_phases,

@@ -124,6 +124,7 @@ def _load():
         "dg_state_download": (c_int, [P, P]),
         "dg_math_selftest": (c_int, [c_int, P, P, ctypes.c_int64, P]),
         "dg_batch_barrier_test": (c_int, [P, c_double, c_int]),
+        "dg_peak_fma": (c_int, [c_int, ctypes.c_int64, c_int, P, P, P]),
         "dg_state_chebyshev_bound": (c_int, [P, P, P]),
         "imex_rk2_step": (c_int, [P, P, P, c_double, ctypes.POINTER(SolverOpts), ctypes.POINTER(StepStats), P]),
         "dg_batch_step": (c_int, [P, c_int, P, P, P, ctypes.POINTER(SolverOpts), P, P, P]),

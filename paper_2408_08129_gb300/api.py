@@ -209,6 +209,14 @@ def dg_batch_barrier_test(ctx, barrier_limit_s=2.0, missing_cta_member=-1):
           "dg_batch_barrier_test")
 
 
+def dg_peak_fma(precision, iters, blocks, out, stream=None):
+    """Enqueue the FMA-throughput probe; returns the floating-point operations it performs."""
+    fl = ctypes.c_double(0.0)
+    check(lib.dg_peak_fma(int(precision), int(iters), int(blocks), _ptr(out), _stream(stream), ctypes.byref(fl)),
+          "dg_peak_fma")
+    return float(fl.value)
+
+
 def dg_launch_count(ctx):
     n = ctypes.c_longlong(0)
     check(lib.dg_launch_count(ctx.handle, ctypes.byref(n)), "dg_launch_count")

@@ -1,8 +1,9 @@
 """Build the CUDA library in-tree with nvcc (sm_103a only).
 
-Every translation unit under ``csrc/`` is compiled in parallel into
-``_build/`` and linked into ``_lib/libdgatmo.so``.  Recompiles only sources
-newer than their object (headers count for every unit).
+Every translation unit under ``csrc/``, plus one generated unit per
+(dimension, degree, precision) of the operator kernels, is compiled in
+parallel into ``_build/`` and linked into ``_lib/libdgatmo.so``.  Recompiles
+only sources newer than their object (headers count for every unit).
 """
 
 import concurrent.futures
@@ -35,11 +36,36 @@ def _flags(src):
     return common + ["--expt-relaxed-constexpr"]
 
 
+# The operator kernels (ops_impl.cuh) are compiled once per (dimension, degree,
+# precision), each in a translation unit of its own, so that the slowest part
+# of the build spreads over all cores.
+DIMS, DEGREES, PRECISIONS = (2, 3), (1, 2, 3, 4, 5), (("f64", "double"), ("f32", "float"))
+
+
+def _generated_units():
+    gen = os.path.join(BUILD, "gen")
+    os.makedirs(gen, exist_ok=True)
+    units = []
+    for dim in DIMS:
+        for deg in DEGREES:
+            for tag, ctype in PRECISIONS:
+                path = os.path.join(gen, "ops_%dd_r%d_%s.cu" % (dim, deg, tag))
+                text = ('// generated by build.py: operator kernels for dim %d, degree %d, %s\n'
+                        '#include "%s"\n\nnamespace dg {\nDG_INSTANTIATE_DEGREE(%d, %d, %s)\n}  // namespace dg\n'
+                        % (dim, deg, ctype, os.path.join(CSRC, "ops_impl.cuh"), dim, deg, ctype))
+                if not os.path.exists(path) or open(path).read() != text:
+                    with open(path, "w") as f:
+                        f.write(text)
+                units.append(path)
+    return units
+
+
 def build(verbose=False, jobs=None):
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    sources += _generated_units()
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(
         os.path.join(HERE, "..", "include", "*.h"))
     newest_header = max((os.path.getmtime(h) for h in headers), default=0.0)
@@ -64,6 +90,8 @@ def build(verbose=False, jobs=None):
 
     if jobs_list:
         n = jobs or min(len(jobs_list), os.cpu_count() or 4)
+        # longest units first (the 3D operator kernels of high degree)
+        jobs_list.sort(key=lambda it: (("ops_3d" in it[0]) * 10 + ("_r5" in it[0]) + ("_r4" in it[0])), reverse=True)
         with concurrent.futures.ThreadPoolExecutor(max_workers=n) as ex:
             list(ex.map(compile_one, jobs_list))
     if jobs_list or not os.path.exists(LIB):

@@ -239,9 +239,9 @@ extern "C" int dg_apply_grad(dg_ctx* ctx, const dg_mesh* m, const void* p, const
   if (!ctx || !m || !p || !g) return fail(DG_EINVAL, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == DG_FP64)
-    return op_grad<double>(m, (const double*)p, (const double*)h, (double*)g, m->d_face_scratch64, s, nullptr);
+    return op_grad<double>(m, (const double*)p, (const double*)h, (double*)g, s, nullptr);
   if (precision == DG_FP32)
-    return op_grad<float>(m, (const float*)p, (const float*)h, (float*)g, (float*)m->d_face_scratch64, s, nullptr);
+    return op_grad<float>(m, (const float*)p, (const float*)h, (float*)g, s, nullptr);
   return fail(DG_EINVAL, "bad precision");
 }
 
@@ -249,9 +249,9 @@ extern "C" int dg_apply_div(dg_ctx* ctx, const dg_mesh* m, const void* f, void* 
   if (!ctx || !m || !f || !out) return fail(DG_EINVAL, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == DG_FP64)
-    return op_div<double>(m, (const double*)f, (double*)out, m->d_face_scratch64, s, nullptr);
+    return op_div<double>(m, (const double*)f, (double*)out, s, nullptr);
   if (precision == DG_FP32)
-    return op_div<float>(m, (const float*)f, (float*)out, (float*)m->d_face_scratch64, s, nullptr);
+    return op_div<float>(m, (const float*)f, (float*)out, s, nullptr);
   return fail(DG_EINVAL, "bad precision");
 }
 
@@ -260,11 +260,11 @@ extern "C" int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* m, const void* h, c
   if (!ctx || !m || !h || !p || !Ap) return fail(DG_EINVAL, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == DG_FP64)
-    return op_helmholtz<double>(m, (const double*)h, (const double*)p, (double*)Ap, alpha, m->d_face_scratch64,
-                                m->d_vec_scratch64, s, nullptr);
+    return op_helmholtz<double>(m, (const double*)h, (const double*)p, (double*)Ap, alpha, m->d_vec_scratch64, s,
+                                nullptr);
   if (precision == DG_FP32)
     return op_helmholtz<float>(m, (const float*)h, (const float*)p, (float*)Ap, (float)alpha,
-                               (float*)m->d_face_scratch64, (float*)m->d_vec_scratch64, s, nullptr);
+                               (float*)m->d_vec_scratch64, s, nullptr);
   return fail(DG_EINVAL, "bad precision");
 }
 

@@ -66,6 +66,16 @@ struct MeshView {
   const int* cell_cmask; // [n_cells] bit lf set if local face lf is the coarse side of a 2:1 face
   const T* tab;     // packed Tables1D of the mesh's degree
   T gravity;
+  // Geometry in compact form, for kernels that recompute the metric terms:
+  // every cell is affine in the horizontal coordinates (x = x0 + hb_a 2^-l
+  // (xi + 1), likewise y), so J d xi^a / d x_b and J follow from the nodal
+  // heights alone.  zdev is the height of a node above its computational
+  // height (z - zeta: the terrain-following displacement, small next to z,
+  // which keeps its derivatives accurate in FP32).
+  const T* zdev;          // [n_nodes]
+  const int* cell_level;  // [n_cells] refinement level
+  T hb[3];                // half width of a base cell per axis
+  int geo_z;              // 1 if every cell is affine in x (and y)
 };
 
 }  // namespace dg

@@ -309,6 +309,27 @@ int build_mesh(dg_mesh* m) {
       for (int q = 0; q < nc; ++q) m->X[((size_t)b * K + c) * nc + q] = (*src)[(size_t)b * nc + q];
   }
 
+  // height of every node above its computational height, and whether every
+  // cell is affine in the horizontal coordinates (then the metric terms
+  // follow from these heights)
+  std::vector<double> zdev(m->Nn);
+  bool geo_z = true;
+  for (int64_t c = 0; c < K; ++c) {
+    const int l = m->level[c];
+    for (int q = 0; q < nc; ++q) {
+      for (int a = 0; a < dim; ++a) {
+        const double h = hb[a] / (double)(1 << l);
+        const double comp = m->ijk[c * dim + a] * h + 0.5 * (tab.xi[mi[3 * q + a]] + 1.0) * h;
+        const double xv = m->X[((size_t)a * K + c) * nc + q];
+        if (a < dim - 1) {
+          if (std::fabs(xv - comp) > 1e-9 * d.extent[a]) geo_z = false;
+        } else {
+          zdev[(size_t)c * nc + q] = xv - comp;
+        }
+      }
+    }
+  }
+
   // metric terms at nodes
   std::vector<double> Ja((size_t)dim * dim * m->Nn), invJ(m->Nn), wJ(m->Nn), rhob(m->Nn), pb(m->Nn);
   for (int64_t c = 0; c < K; ++c) {
@@ -400,8 +421,8 @@ int build_mesh(dg_mesh* m) {
   for (int64_t c = 0; c < K; ++c)
     for (int lf = 0; lf < 2 * dim; ++lf)
       if ((cell_face[c * 2 * dim + lf] & 3) == 2) cell_cmask[c] |= 1 << lf;
-  const size_t n_int = (size_t)5 * nf + cell_face.size() + 2 * (size_t)nf * NF + (size_t)K;
-  const size_t n_real = (size_t)dim * dim * m->Nn + 4 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size();
+  const size_t n_int = (size_t)5 * nf + cell_face.size() + 2 * (size_t)nf * NF + 2 * (size_t)K;
+  const size_t n_real = (size_t)dim * dim * m->Nn + 5 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size();
   auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
   DG_CUDA(cudaSetDevice(m->ctx->device));
   DG_CUDA(cudaMalloc(&m->d_int, pad(n_int) * sizeof(int)));
@@ -426,6 +447,7 @@ int build_mesh(dg_mesh* m) {
   ibuf.insert(ibuf.end(), fnode_m.begin(), fnode_m.end());
   ibuf.insert(ibuf.end(), fnode_p.begin(), fnode_p.end());
   ibuf.insert(ibuf.end(), cell_cmask.begin(), cell_cmask.end());
+  for (int64_t c = 0; c < K; ++c) ibuf.push_back((int)m->level[c]);
   DG_CUDA(cudaMemcpy(m->d_int, ibuf.data(), ibuf.size() * sizeof(int), cudaMemcpyHostToDevice));
 
   std::vector<double> rbuf;
@@ -444,6 +466,8 @@ int build_mesh(dg_mesh* m) {
   rbuf.insert(rbuf.end(), fn.begin(), fn.end());
   size_t o_fsj = rbuf.size();
   rbuf.insert(rbuf.end(), fsj.begin(), fsj.end());
+  size_t o_zdev = rbuf.size();
+  rbuf.insert(rbuf.end(), zdev.begin(), zdev.end());
   size_t o_tab = rbuf.size();
   rbuf.insert(rbuf.end(), tabp.begin(), tabp.end());
   DG_CUDA(cudaMemcpy(m->d_f64, rbuf.data(), rbuf.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -476,6 +500,10 @@ int build_mesh(dg_mesh* m) {
     v.fnode_p = v.fnode_m + (size_t)nf * NF;
     v.cell_cmask = v.fnode_p + (size_t)nf * NF;
     v.gravity = (decltype(v.gravity))d.gravity;
+    v.zdev = base + o_zdev;
+    v.cell_level = v.cell_cmask + K;
+    for (int a = 0; a < 3; ++a) v.hb[a] = (decltype(v.gravity))(a < dim ? 0.5 * hb[a] : 0.0);
+    v.geo_z = geo_z ? 1 : 0;
   };
   fill(m->v64, (const double*)m->d_f64);
   fill(m->v32, (const float*)m->d_f32);

@@ -1,6 +1,8 @@
 // Operators of the implicit pressure stage (Sec. 2 IMEX split; Sec. 3.2
-// pressure loop), centred traces, in a one-pass cell form (persistent solves)
-// and a two-pass face + cell form (standalone launches):
+// pressure loop), centred traces, in a one-pass cell form: every cell pass
+// computes the face terms of its own nodes (no face pass, no face buffer).
+// The persistent solves run the passes between grid barriers; standalone
+// calls launch them one kernel per operator:
 //
 //  gradient (strong form):  g_b = [ sum_a Ja^a_b (D_a p) + Gh_b / w_end ] / J,
 //      face value Gh_b = 1/2 |N| n_b (p+ - p-), added with + on both sides
@@ -58,6 +60,54 @@ __device__ __forceinline__ T coarse_weight(const T* sIt, int s, int kt, int q) {
   constexpr int N = DEG + 1;
   if (DIM == 2) return sIt[s * N * N + kt * N + q];
   return sIt[(s & 1) * N * N + (kt % N) * N + (q % N)] * sIt[((s >> 1) & 1) * N * N + (kt / N) * N + (q / N)];
+}
+
+// Metric terms of node id of a cell whose x (and y) are affine, from the
+// heights above the computational coordinates in shared memory (sz: the
+// cell's NC values) and the cell's half widths (hb * 2^-level per axis):
+//   2D: Ja = [[z_z, 0], [-z_x, ax]],  J = ax z_z
+//   3D: Ja = [[ay z_z, 0, 0], [0, ax z_z, 0], [-ay z_x, -ax z_y, ax ay]],  J = ax ay z_z
+// with z_a = d z / d xi^a (the vertical one includes the computational half
+// width).  These equal the cofactors of the nodal-derivative Jacobian that the
+// stored metric terms hold.
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void metric_from_z(const MeshView<T>& mv, int64_t c, const T* sz, const int* id,
+                                              const T* sD, T (&Ja)[DIM][DIM], T& invJ) {
+  constexpr int N = DEG + 1;
+  const T scale = T(1) / T(1 << mv.cell_level[c]);
+  T zd[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+    const int node = id[0] + N * id[1] + (DIM == 3 ? N * N * id[2] : 0);
+    const T* zc = sz + node - id[a] * stride;
+    const T* D = sD + id[a] * N;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < N; ++k) s += D[k] * zc[k * stride];
+    zd[a] = s;
+  }
+  zd[DIM - 1] += mv.hb[DIM - 1] * scale;
+  const T ax = mv.hb[0] * scale;
+  if (DIM == 2) {
+    Ja[0][0] = zd[1];
+    Ja[0][1] = T(0);
+    Ja[1][0] = -zd[0];
+    Ja[1][1] = ax;
+    invJ = T(1) / (ax * zd[1]);
+  } else {
+    const T ay = mv.hb[1] * scale;
+    Ja[0][0] = ay * zd[DIM - 1];
+    Ja[0][1] = T(0);
+    Ja[0][DIM - 1] = T(0);
+    Ja[1][0] = T(0);
+    Ja[1][1] = ax * zd[DIM - 1];
+    Ja[1][DIM - 1] = T(0);
+    Ja[DIM - 1][0] = -ay * zd[0];
+    Ja[DIM - 1][1] = -ax * zd[1];
+    Ja[DIM - 1][DIM - 1] = ax * ay;
+    invJ = T(1) / (ax * ay * zd[DIM - 1]);
+  }
 }
 
 // ---------------------------------------------------------------- gradient
@@ -133,10 +183,13 @@ __device__ __forceinline__ void coarse_pass(const MeshView<T>& mv, bool active, 
   }
 }
 
-// sum over the node's conforming and fine-side faces of 1/2 |N| n_b (p+ - p-)
-template <int DIM, int DEG, typename T>
+// sum over the node's conforming and fine-side faces of 1/2 |N| n_b (p+ - p-);
+// GZ: the face normal |N| n is the node's own outward metric row +-Ja[a] (the
+// same face seen from either side; on a 2:1 face the fine side's)
+template <int DIM, int DEG, typename T, bool GZ = false>
 __device__ __forceinline__ void grad_face_terms(const MeshView<T>& mv, const T* __restrict__ p, const int* codes,
-                                                const int* id, T pv, const T* sI, T* facc) {
+                                                const int* id, T pv, const T* sI, T* facc,
+                                                const T (*Jl)[DIM] = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int NF = S::NF, NC = S::NC;
   const int64_t total = (int64_t)mv.nf * NF;
@@ -159,9 +212,15 @@ __device__ __forceinline__ void grad_face_terms(const MeshView<T>& mv, const T* 
       else
         coarse_interp<DIM, DEG, T, 1>(p, 0, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], kt, sI, &pp);
     }
-    const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
+    if (GZ) {
+      const T jmp = (id[a] == DEG ? T(0.5) : T(-0.5)) * (side == 1 ? pm - pp : pp - pm);
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) facc[b] += jmp * mv.fn[(int64_t)b * total + t];
+      for (int b = 0; b < DIM; ++b) facc[b] += jmp * Jl[a][b];
+    } else {
+      const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) facc[b] += jmp * mv.fn[(int64_t)b * total + t];
+    }
   }
 }
 
@@ -169,10 +228,11 @@ __device__ __forceinline__ void grad_face_terms(const MeshView<T>& mv, const T* 
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 // sII holds the interpolation tables I (2 N^2) followed by It (2 N^2); sJ is
 // the coarse-pass buffer (coarse_buffer<DIM, DEG, DIM>() elements).
-template <int DIM, int DEG, typename T>
+// GZ: metric terms from the heights (metric_from_z), staged in sz (CPB*NC).
+template <int DIM, int DEG, typename T, bool GZ = false>
 __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
                                                 const T* __restrict__ h, T* __restrict__ g, int64_t batch, T* sp,
-                                                T* sJ, const T* sD, const T* sII) {
+                                                T* sJ, const T* sD, const T* sII, T* sz = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
@@ -189,16 +249,26 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
     pv = p[idx];
     sp[lc * NC + i] = pv;
     load_face_codes<DIM, DEG, T>(mv, c, id, codes);
+    if (GZ) {
+      sz[lc * NC + i] = mv.zdev[idx];
+      scale = h ? h[idx] : T(1);
+    } else {
 #pragma unroll
-    for (int a = 0; a < DIM; ++a)
+      for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
-    scale = mv.invJ[idx] * (h ? h[idx] : T(1));
+        for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
+      scale = mv.invJ[idx] * (h ? h[idx] : T(1));
+    }
   }
   __syncthreads();
   T facc[DIM], dp[DIM];
 #pragma unroll
   for (int b = 0; b < DIM; ++b) facc[b] = dp[b] = T(0);
+  if (GZ && active) {
+    T ij;
+    metric_from_z<DIM, DEG, T>(mv, c, sz + lc * NC, id, sD, Jl, ij);
+    scale *= ij;
+  }
   if (active) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -210,7 +280,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
       for (int kk = 0; kk < N; ++kk) s += D[kk] * sp[i0 + kk * stride];
       dp[a] = s;
     }
-    grad_face_terms<DIM, DEG, T>(mv, p, codes, id, pv, sII, facc);
+    grad_face_terms<DIM, DEG, T, GZ>(mv, p, codes, id, pv, sII, facc, Jl);
   }
   // coarse sides: jump at each fine point from the fine value and the cell's own polynomial
   const int64_t total = (int64_t)mv.nf * NF;
@@ -242,9 +312,10 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
 
 // sum over the node's conforming and fine-side faces of +-|N| {f}.n (+ on the
 // minus side, - on the plus side)
-template <int DIM, int DEG, typename T>
+template <int DIM, int DEG, typename T, bool GZ = false>
 __device__ __forceinline__ void div_face_terms(const MeshView<T>& mv, const T* __restrict__ fld, const int* codes,
-                                               const int* id, const T* fv, const T* sI, T* facc) {
+                                               const int* id, const T* fv, const T* sI, T* facc,
+                                               const T (*Jl)[DIM] = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int NF = S::NF, NC = S::NC;
   const int64_t total = (int64_t)mv.nf * NF;
@@ -269,12 +340,19 @@ __device__ __forceinline__ void div_face_terms(const MeshView<T>& mv, const T* _
     } else {
       coarse_interp<DIM, DEG, T, DIM>(fld, Nn, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], kt, sI, fo);
     }
-    // (minus + plus) in that order on both sides
-    T s = T(0);
+    if (GZ) {  // own outward normal +-Ja[a]
+      T s = T(0);
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) s += (side == 1 ? fo[b] + fv[b] : fv[b] + fo[b]) * mv.fn[(int64_t)b * total + t];
-    const T dh = T(0.5) * mv.fsj[t] * s;
-    facc[0] += (side == 1) ? -dh : dh;
+      for (int b = 0; b < DIM; ++b) s += (side == 1 ? fo[b] + fv[b] : fv[b] + fo[b]) * Jl[a][b];
+      facc[0] += (id[a] == DEG ? T(0.5) : T(-0.5)) * s;
+    } else {
+      // (minus + plus) in that order on both sides
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) s += (side == 1 ? fo[b] + fv[b] : fv[b] + fo[b]) * mv.fn[(int64_t)b * total + t];
+      const T dh = T(0.5) * mv.fsj[t] * s;
+      facc[0] += (side == 1) ? -dh : dh;
+    }
   }
 }
 
@@ -282,10 +360,12 @@ __device__ __forceinline__ void div_face_terms(const MeshView<T>& mv, const T* _
 // at every node of the batch (the caller stores it, or fuses further pointwise work).
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 // sF: DIM * CPB * NC elements; sJ: coarse-pass buffer (coarse_buffer<DIM, DEG, 1>() elements).
-template <int DIM, int DEG, typename T, bool HELM, class Epi>
+// GZ: metric terms from the heights (metric_from_z with sD), staged in sz (CPB*NC).
+template <int DIM, int DEG, typename T, bool HELM, class Epi, bool GZ = false>
 __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
                                                const T* __restrict__ p, T alpha, T scale, T ident, Epi& epi,
-                                               int64_t batch, T* sF, T* sJ, const T* sDw, const T* sII) {
+                                               int64_t batch, T* sF, T* sJ, const T* sDw, const T* sII,
+                                               T* sz = nullptr, const T* sD = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
@@ -298,19 +378,37 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   T ft[DIM];  // Ja^a . f for each axis a
   T fv[DIM];
   T ij = T(0), pv = T(0);
+  T Jl[DIM][DIM];
   const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch);
   if (active) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fv[b] = fld[(int64_t)b * Nn + idx];
     load_face_codes<DIM, DEG, T>(mv, c, id, codes);
-    ij = mv.invJ[idx];
     if (HELM) pv = p[idx];
+    if (GZ) {
+      sz[lc * NC + i] = mv.zdev[idx];
+    } else {
+      ij = mv.invJ[idx];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      T s = T(0);
+      for (int a = 0; a < DIM; ++a) {
+        T s = T(0);
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * fv[b];
-      ft[a] = s;
+        for (int b = 0; b < DIM; ++b) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * fv[b];
+        ft[a] = s;
+      }
+    }
+  }
+  if (GZ) {
+    __syncthreads();
+    if (active) {
+      metric_from_z<DIM, DEG, T>(mv, c, sz + lc * NC, id, sD, Jl, ij);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) s += Jl[a][b] * fv[b];
+        ft[a] = s;
+      }
     }
   }
   // all DIM contravariant components staged at once (sF holds DIM * CPB * NC)
@@ -331,7 +429,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     }
   }
   T facc = T(0);
-  if (active) div_face_terms<DIM, DEG, T>(mv, fld, codes, id, fv, sII, &facc);
+  if (active) div_face_terms<DIM, DEG, T, GZ>(mv, fld, codes, id, fv, sII, &facc, Jl);
   // coarse sides: |N| {f}.n at each fine point from the fine value and the cell's own polynomial
   const int64_t total = (int64_t)mv.nf * NF;
   coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, bmask, sII + 2 * N * N, T(-1), sJ, &facc,
@@ -356,229 +454,65 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   __syncthreads();  // sF and sJ are rewritten by the next batch
 }
 
-// ---------------------------------------------------------------- two-pass form
+// ---------------------------------------------------------------- standalone one-pass kernels
 //
-// The standalone operators (dg_apply_grad / _div / _implicit and the
-// one-launch-per-kernel Krylov solve) run each operator as a face pass, which
-// evaluates every face value once into a face buffer, and a cell pass that
-// gathers them.  Launched on their own, these kernels keep more blocks
-// resident and shorter load chains than the one-pass cell form above, which
-// serves the persistent solves (where it saves two grid barriers per mat-vec).
+// dg_apply_grad / dg_apply_div / dg_apply_implicit: one CTA per cell batch,
+// the face terms computed by the cells themselves (no face buffer: the only
+// intermediate of the Helmholtz operator is the h-scaled gradient between
+// the two launches).  GZ: the metric terms are recomputed from the nodal
+// heights instead of loaded (used in FP32 on meshes affine in x and y, where
+// it cuts the geometry read per node from d^2 + 1 values to one).
 
-// face node t (< (nconf+nsub)*NF): Gh_b = 1/2 |N| n_b (p+ - p-)
-template <int DIM, int DEG, typename T>
-__device__ __forceinline__ void grad_face_item(const MeshView<T>& mv, const T* __restrict__ p, T* __restrict__ Gh,
-                                               int64_t t) {
-  using S = Shape<DIM, DEG>;
-  constexpr int NC = S::NC, NF = S::NF;
-  const int64_t total = (int64_t)mv.nf * NF;
-  const int f = (int)(t / NF), k = (int)(t % NF);
-  const T pm = p[mv.fnode_m[t]];
-  T pp;
-  if (f < mv.nconf)
-    pp = p[mv.fnode_p[t]];
-  else
-    coarse_interp<DIM, DEG, T, 1>(p, 0, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], k, mv.tab + S::T_I,
-                                  &pp);
-  const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) Gh[(int64_t)b * total + t] = jmp * mv.fn[(int64_t)b * total + t];
-}
+template <typename T>
+struct StoreOut {
+  T* out;
+  __device__ __forceinline__ void operator()(int64_t i, T v) const { out[i] = v; }
+};
 
-// Cells [batch*CPB, batch*CPB + CPB): g_b = h [sum_a Ja^a_b (D_a p) + Gh_b / w_end] / J.
-// Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
-// Every global load that does not depend on the face values is issued before
-// the barrier so that the loads' latencies overlap.
-template <int DIM, int DEG, typename T>
-__device__ __forceinline__ void grad_gather_batch(const MeshView<T>& mv, const T* __restrict__ p,
-                                                const T* __restrict__ h, const T* __restrict__ Gh,
-                                                T* __restrict__ g, int64_t batch, T* sp, const T* sD,
-                                                const T* sIt) {
-  using S = Shape<DIM, DEG>;
-  constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
-  const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int64_t c = batch * CPB + lc;
-  const bool active = (lc < CPB) && (c < mv.n_cells);
-  const int64_t Nn = mv.n_nodes;
-  const int64_t idx = c * NC + i;
-  int id[3] = {i % N, (i / N) % N, i / (N * N)};
-  int codes[DIM];
-  T Jl[DIM][DIM];
-  T scale = T(0);
-  if (active) {
-    sp[lc * NC + i] = p[idx];
-    load_face_codes<DIM, DEG, T>(mv, c, id, codes);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a)
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
-    scale = mv.invJ[idx] * (h ? h[idx] : T(1));
-  }
-  __syncthreads();
-  if (active) {
-    T dp[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
-      const int i0 = lc * NC + i - id[a] * stride;
-      const T* D = sD + id[a] * N;
-      T s = T(0);
-#pragma unroll
-      for (int kk = 0; kk < N; ++kk) s += D[kk] * sp[i0 + kk * stride];
-      dp[a] = s;
-    }
-    T facc[DIM];
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) facc[b] = T(0);
-    gather_faces_codes<DIM, DEG, T, DIM>(mv, Gh, codes, id, sIt, T(1), T(1), true, facc);
-    const T iwend = mv.tab[S::T_IWEND];
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) {
-      T s = facc[b] * iwend;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) s += Jl[a][b] * dp[a];
-      g[(int64_t)b * Nn + idx] = s * scale;
-    }
-  }
-  __syncthreads();
-}
-
-// face node t (< (nconf+nsub)*NF): Dh = |N| {f}.n
-template <int DIM, int DEG, typename T>
-__device__ __forceinline__ void div_face_item(const MeshView<T>& mv, const T* __restrict__ fld, T* __restrict__ Dh,
-                                              int64_t t) {
-  using S = Shape<DIM, DEG>;
-  constexpr int NC = S::NC, NF = S::NF;
-  const int64_t total = (int64_t)mv.nf * NF;
-  const int f = (int)(t / NF), k = (int)(t % NF);
-  const int64_t Nn = mv.n_nodes;
-  const int64_t im = mv.fnode_m[t];
-  T fp[DIM];
-  if (f < mv.nconf) {
-    const int64_t ip = mv.fnode_p[t];
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) fp[b] = fld[(int64_t)b * Nn + ip];
-  } else {
-    coarse_interp<DIM, DEG, T, DIM>(fld, Nn, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], k,
-                                    mv.tab + S::T_I, fp);
-  }
-  T s = T(0);
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) s += (fld[(int64_t)b * Nn + im] + fp[b]) * mv.fn[(int64_t)b * total + t];
-  Dh[t] = T(0.5) * mv.fsj[t] * s;
-}
-
-// Cells of one batch: out = HELM ? scale * (ident p/(gamma-1) - alpha div) : div.
-// Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
-template <int DIM, int DEG, typename T, bool HELM>
-__device__ __forceinline__ void div_gather_batch(const MeshView<T>& mv, const T* __restrict__ fld,
-                                               const T* __restrict__ Dh, const T* __restrict__ p, T alpha, T scale,
-                                               T ident, T* __restrict__ out, int64_t batch, T* sF, const T* sDw,
-                                               const T* sIt) {
-  using S = Shape<DIM, DEG>;
-  constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
-  const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int64_t c = batch * CPB + lc;
-  const bool active = (lc < CPB) && (c < mv.n_cells);
-  const int64_t Nn = mv.n_nodes;
-  const int64_t idx = c * NC + i;
-  int id[3] = {i % N, (i / N) % N, i / (N * N)};
-  int codes[DIM];
-  T ft[DIM];  // Ja^a . f for each axis a
-  T ij = T(0), pv = T(0);
-  if (active) {
-    T fv[DIM];
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) fv[b] = fld[(int64_t)b * Nn + idx];
-    load_face_codes<DIM, DEG, T>(mv, c, id, codes);
-    ij = mv.invJ[idx];
-    if (HELM) pv = p[idx];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      T s = T(0);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * fv[b];
-      ft[a] = s;
-    }
-  }
-  T acc = T(0);
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    if (active) sF[lc * NC + i] = ft[a];
-    __syncthreads();
-    if (active) {
-      const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
-      const int i0 = lc * NC + i - id[a] * stride;
-      const T* Dw = sDw + id[a] * N;
-#pragma unroll
-      for (int kk = 0; kk < N; ++kk) acc -= Dw[kk] * sF[i0 + kk * stride];
-    }
-    __syncthreads();
-  }
-  if (active) {
-    T facc = T(0);
-    gather_faces_codes<DIM, DEG, T, 1>(mv, Dh, codes, id, sIt, T(1), T(-1), true, &facc);
-    const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
-    if (HELM)
-      out[idx] = scale * (ident * pv * inv_gm1<T>() - alpha * dv);
-    else
-      out[idx] = dv;
-  }
-}
-
-
-template <int DIM, int DEG, typename T>
-__global__ void __launch_bounds__(256) grad_face_kernel(MeshView<T> mv, const T* __restrict__ p,
-                                                        T* __restrict__ Gh, const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)(mv.nconf + mv.nsub) * Shape<DIM, DEG>::NF) return;
-  grad_face_item<DIM, DEG, T>(mv, p, Gh, t);
-}
-
-template <int DIM, int DEG, typename T>
-__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_gather_kernel(MeshView<T> mv,
-                                                                             const T* __restrict__ p,
-                                                                             const T* __restrict__ h,
-                                                                             const T* __restrict__ Gh,
-                                                                             T* __restrict__ g,
-                                                                             const int* __restrict__ skip) {
+template <int DIM, int DEG, typename T, bool GZ>
+__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_cell_kernel(MeshView<T> mv,
+                                                                           const T* __restrict__ p,
+                                                                           const T* __restrict__ h,
+                                                                           T* __restrict__ g,
+                                                                           const int* __restrict__ skip) {
   if (skip && *skip) return;
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N;
   __shared__ T sp[S::CPB * S::NC];
+  __shared__ T sz[GZ ? S::CPB * S::NC : 1];
+  __shared__ T sJ[coarse_buffer<DIM, DEG, DIM>()];
   __shared__ T sD[N * N];
-  __shared__ T sIt[2 * N * N];
+  __shared__ T sII[4 * N * N];
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sD[q] = mv.tab[S::T_D + q];
-  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
-  grad_gather_batch<DIM, DEG, T>(mv, p, h, Gh, g, blockIdx.x, sp, sD, sIt);
+  for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
+  // the tables are read only after grad_cell_batch's first block barrier
+  grad_cell_batch<DIM, DEG, T, GZ>(mv, p, h, g, blockIdx.x, sp, sJ, sD, sII, sz);
 }
 
-template <int DIM, int DEG, typename T>
-__global__ void __launch_bounds__(256) div_face_kernel(MeshView<T> mv, const T* __restrict__ fld,
-                                                       T* __restrict__ Dh, const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)(mv.nconf + mv.nsub) * Shape<DIM, DEG>::NF) return;
-  div_face_item<DIM, DEG, T>(mv, fld, Dh, t);
-}
-
-template <int DIM, int DEG, typename T, bool HELM>
-__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_gather_kernel(MeshView<T> mv,
-                                                                            const T* __restrict__ fld,
-                                                                            const T* __restrict__ Dh,
-                                                                            const T* __restrict__ p, T alpha,
-                                                                            T* __restrict__ out,
-                                                                            const int* __restrict__ skip) {
+template <int DIM, int DEG, typename T, bool HELM, bool GZ>
+__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(MeshView<T> mv,
+                                                                          const T* __restrict__ f,
+                                                                          const T* __restrict__ p, T alpha,
+                                                                          T* __restrict__ out,
+                                                                          const int* __restrict__ skip) {
   if (skip && *skip) return;
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N;
-  __shared__ T sF[S::CPB * S::NC];
+  __shared__ T sF[DIM * S::CPB * S::NC];
+  __shared__ T sz[GZ ? S::CPB * S::NC : 1];
+  __shared__ T sJ[coarse_buffer<DIM, DEG, 1>()];
   __shared__ T sDw[N * N];
-  __shared__ T sIt[2 * N * N];
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sDw[q] = mv.tab[S::T_DW + q];
-  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
-  div_gather_batch<DIM, DEG, T, HELM>(mv, fld, Dh, p, alpha, T(1), T(1), out, blockIdx.x, sF, sDw, sIt);
+  __shared__ T sD[GZ ? N * N : 1];
+  __shared__ T sII[4 * N * N];
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
+    sDw[q] = mv.tab[S::T_DW + q];
+    if (GZ) sD[q] = mv.tab[S::T_D + q];
+  }
+  for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
+  // the tables are read only after div_cell_batch's first block barrier
+  StoreOut<T> epi{out};
+  div_cell_batch<DIM, DEG, T, HELM, StoreOut<T>, GZ>(mv, f, p, alpha, T(1), T(1), epi, blockIdx.x, sF, sJ, sDw,
+                                                     sII, sz, sD);
 }
 
 }  // namespace dg

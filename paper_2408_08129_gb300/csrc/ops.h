@@ -24,12 +24,13 @@ template <int DIM, typename T>
 int launch_explicit(const dg_mesh* m, const T* U, T* R, T* face_scratch, bool full, cudaStream_t s,
                     const int* skip);
 template <int DIM, typename T>
-int launch_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* face_scratch, cudaStream_t s, const int* skip);
+int launch_grad(const dg_mesh* m, const T* p, const T* h, T* g, cudaStream_t s, const int* skip);
 template <int DIM, typename T>
-int launch_div(const dg_mesh* m, const T* f, T* out, T* face_scratch, cudaStream_t s, const int* skip);
+int launch_div(const dg_mesh* m, const T* f, T* out, cudaStream_t s, const int* skip);
+// vec_scratch: the h-scaled gradient between the two launches, dim * n_nodes elements
 template <int DIM, typename T>
-int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* face_scratch, T* vec_scratch,
-                     cudaStream_t s, const int* skip);
+int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* vec_scratch, cudaStream_t s,
+                     const int* skip);
 
 // One cooperative launch solving A(h) x = b by restarted GMRES(restart) to
 // relative residual tol (k_gmres.cuh).  TK = double: FP64 GMRES; TK = float:
@@ -102,21 +103,21 @@ inline int op_explicit(const dg_mesh* m, const T* U, T* R, T* fs, bool full, cud
                      : launch_explicit<3, T>(m, U, R, fs, full, s, skip);
 }
 template <typename T>
-inline int op_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* fs, cudaStream_t s, const int* skip) {
+inline int op_grad(const dg_mesh* m, const T* p, const T* h, T* g, cudaStream_t s, const int* skip) {
   ProfScope ps(m->ctx, DG_PROF_GRAD, s);
-  return m->dim == 2 ? launch_grad<2, T>(m, p, h, g, fs, s, skip) : launch_grad<3, T>(m, p, h, g, fs, s, skip);
+  return m->dim == 2 ? launch_grad<2, T>(m, p, h, g, s, skip) : launch_grad<3, T>(m, p, h, g, s, skip);
 }
 template <typename T>
-inline int op_div(const dg_mesh* m, const T* f, T* out, T* fs, cudaStream_t s, const int* skip) {
+inline int op_div(const dg_mesh* m, const T* f, T* out, cudaStream_t s, const int* skip) {
   ProfScope ps(m->ctx, DG_PROF_DIV, s);
-  return m->dim == 2 ? launch_div<2, T>(m, f, out, fs, s, skip) : launch_div<3, T>(m, f, out, fs, s, skip);
+  return m->dim == 2 ? launch_div<2, T>(m, f, out, s, skip) : launch_div<3, T>(m, f, out, s, skip);
 }
 template <typename T>
-inline int op_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* fs, T* vs, cudaStream_t s,
+inline int op_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* vs, cudaStream_t s,
                         const int* skip) {
   ProfScope ps(m->ctx, DG_PROF_HELMHOLTZ, s);
-  return m->dim == 2 ? launch_helmholtz<2, T>(m, h, p, Ap, alpha, fs, vs, s, skip)
-                     : launch_helmholtz<3, T>(m, h, p, Ap, alpha, fs, vs, s, skip);
+  return m->dim == 2 ? launch_helmholtz<2, T>(m, h, p, Ap, alpha, vs, s, skip)
+                     : launch_helmholtz<3, T>(m, h, p, Ap, alpha, vs, s, skip);
 }
 
 }  // namespace dg

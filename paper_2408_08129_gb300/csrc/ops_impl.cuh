@@ -1,4 +1,8 @@
-// Launcher bodies; included once per (dimension, precision) translation unit.
+// Launcher bodies of the operator kernels, one function per (dimension,
+// degree, precision).  The build compiles this header once per combination,
+// in translation units of its own (generated by build.py) that instantiate
+// them with DG_INSTANTIATE_DEGREE; ops_dispatch.cu picks among them at run
+// time by the mesh's degree.
 #pragma once
 
 #include <algorithm>
@@ -23,6 +27,8 @@ inline int check_launch(const char* what) {
 
 inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
+}  // namespace
+
 template <int DIM, int DEG, typename T>
 int run_explicit(const dg_mesh* m, const T* U, T* R, T* Fh, bool full, cudaStream_t s, const int* skip) {
   using S = Shape<DIM, DEG>;
@@ -41,26 +47,32 @@ int run_explicit(const dg_mesh* m, const T* U, T* R, T* Fh, bool full, cudaStrea
   return check_launch("explicit operator launch");
 }
 
+// Gradient and divergence, one launch each, face terms computed by the cells
+// (k_implicit.cuh, standalone one-pass kernels); FP32 on meshes affine in x
+// and y recomputes the metric terms from the nodal heights.
 template <int DIM, int DEG, typename T>
-int run_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* Gh, cudaStream_t s, const int* skip) {
+int run_grad(const dg_mesh* m, const T* p, const T* h, T* g, cudaStream_t s, const int* skip) {
   using S = Shape<DIM, DEG>;
   const MeshView<T>& mv = view<T>(m);
-  const int64_t tf = (int64_t)(mv.nconf + mv.nsub) * S::NF;
-  count_launches(m->ctx, tf ? 2 : 1);
-  if (tf) grad_face_kernel<DIM, DEG, T><<<blocks_for(tf, 256), 256, 0, s>>>(mv, p, Gh, skip);
-  grad_gather_kernel<DIM, DEG, T><<<blocks_for(mv.n_cells, S::CPB), S::THREADS, 0, s>>>(mv, p, h, Gh, g, skip);
+  const unsigned nb = blocks_for(mv.n_cells, S::CPB);
+  count_launches(m->ctx, 1);
+  if (std::is_same<T, float>::value && mv.geo_z)
+    grad_cell_kernel<DIM, DEG, T, true><<<nb, S::THREADS, 0, s>>>(mv, p, h, g, skip);
+  else
+    grad_cell_kernel<DIM, DEG, T, false><<<nb, S::THREADS, 0, s>>>(mv, p, h, g, skip);
   return check_launch("gradient launch");
 }
 
 template <int DIM, int DEG, typename T, bool HELM>
-int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, T* Dh, cudaStream_t s, const int* skip) {
+int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, cudaStream_t s, const int* skip) {
   using S = Shape<DIM, DEG>;
   const MeshView<T>& mv = view<T>(m);
-  const int64_t tf = (int64_t)(mv.nconf + mv.nsub) * S::NF;
-  count_launches(m->ctx, tf ? 2 : 1);
-  if (tf) div_face_kernel<DIM, DEG, T><<<blocks_for(tf, 256), 256, 0, s>>>(mv, f, Dh, skip);
-  div_gather_kernel<DIM, DEG, T, HELM><<<blocks_for(mv.n_cells, S::CPB), S::THREADS, 0, s>>>(mv, f, Dh, p, alpha,
-                                                                                             out, skip);
+  const unsigned nb = blocks_for(mv.n_cells, S::CPB);
+  count_launches(m->ctx, 1);
+  if (std::is_same<T, float>::value && mv.geo_z)
+    div_cell_kernel<DIM, DEG, T, HELM, true><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
+  else
+    div_cell_kernel<DIM, DEG, T, HELM, false><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
   return check_launch("divergence launch");
 }
 
@@ -239,69 +251,15 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
   return DG_OK;
 }
 
-}  // namespace
 
-#define DG_DEGREE_SWITCH(deg, ...)                         \
-  switch (deg) {                                           \
-    case 1: { constexpr int DEG = 1; __VA_ARGS__; }        \
-    case 2: { constexpr int DEG = 2; __VA_ARGS__; }        \
-    case 3: { constexpr int DEG = 3; __VA_ARGS__; }        \
-    case 4: { constexpr int DEG = 4; __VA_ARGS__; }        \
-    case 5: { constexpr int DEG = 5; __VA_ARGS__; }        \
-    default: return fail(DG_EINVAL, "unsupported degree"); \
-  }
-
-template <int DIM, typename T>
-int launch_explicit(const dg_mesh* m, const T* U, T* R, T* fs, bool full, cudaStream_t s, const int* skip) {
-  DG_DEGREE_SWITCH(m->degree, return (run_explicit<DIM, DEG, T>(m, U, R, fs, full, s, skip)))
-}
-
-template <int DIM, typename T>
-int launch_grad(const dg_mesh* m, const T* p, const T* h, T* g, T* fs, cudaStream_t s, const int* skip) {
-  DG_DEGREE_SWITCH(m->degree, return (run_grad<DIM, DEG, T>(m, p, h, g, fs, s, skip)))
-}
-
-template <int DIM, typename T>
-int launch_div(const dg_mesh* m, const T* f, T* out, T* fs, cudaStream_t s, const int* skip) {
-  DG_DEGREE_SWITCH(m->degree, return (run_div<DIM, DEG, T, false>(m, f, nullptr, T(0), out, fs, s, skip)))
-}
-
-template <int DIM, typename T>
-int launch_helmholtz(const dg_mesh* m, const T* h, const T* p, T* Ap, T alpha, T* fs, T* vs, cudaStream_t s,
-                     const int* skip) {
-  DG_DEGREE_SWITCH(m->degree, {
-    int st = run_grad<DIM, DEG, T>(m, p, h, vs, fs, s, skip);
-    if (st != DG_OK) return st;
-    return (run_div<DIM, DEG, T, true>(m, vs, p, alpha, Ap, fs, s, skip));
-  })
-}
-
-template <int DIM, typename TK>
-int launch_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b, double* x, double alpha,
-                 double tol, double inner_tol, int restart, int max_iters, int method, TK* Q, TK* w, double* w64,
-                 double* partial, int npartial, double* out, double* lmax, unsigned long long* phase,
-                 cudaStream_t s) {
-  DG_DEGREE_SWITCH(m->degree, return (run_gmres<DIM, DEG, TK>(m, h64, hk, b, x, alpha, tol, inner_tol, restart,
-                                                               max_iters, method, Q, w, w64, partial, npartial, out,
-                                                               lmax, phase, s)))
-}
-
-template <int DIM, typename TK>
-int launch_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int restart, int* err,
-                         cudaStream_t s) {
-  if (n_items <= 0) return DG_OK;
-  DG_DEGREE_SWITCH(items[0].m->degree, return (run_gmres_batched<DIM, DEG, TK>(ctx, items, n_items, restart, err, s)))
-}
-
-#define DG_INSTANTIATE_OPS(DIM, T)                                                                              \
-  template int launch_explicit<DIM, T>(const dg_mesh*, const T*, T*, T*, bool, cudaStream_t, const int*);      \
-  template int launch_grad<DIM, T>(const dg_mesh*, const T*, const T*, T*, T*, cudaStream_t, const int*);      \
-  template int launch_div<DIM, T>(const dg_mesh*, const T*, T*, T*, cudaStream_t, const int*);                 \
-  template int launch_helmholtz<DIM, T>(const dg_mesh*, const T*, const T*, T*, T, T*, T*, cudaStream_t,       \
-                                        const int*);                                                            \
-  template int launch_gmres<DIM, T>(const dg_mesh*, const double*, const T*, const double*, double*, double,     \
-                                    double, double, int, int, int, T*, T*, double*, double*, int, double*,       \
-                                    double*, unsigned long long*, cudaStream_t);                                \
-  template int launch_gmres_batched<DIM, T>(dg_ctx*, const GmresItem<T>*, int, int, int*, cudaStream_t);
+#define DG_INSTANTIATE_DEGREE(DIM, DEG, T)                                                                       \
+  template int run_explicit<DIM, DEG, T>(const dg_mesh*, const T*, T*, T*, bool, cudaStream_t, const int*);     \
+  template int run_grad<DIM, DEG, T>(const dg_mesh*, const T*, const T*, T*, cudaStream_t, const int*);         \
+  template int run_div<DIM, DEG, T, false>(const dg_mesh*, const T*, const T*, T, T*, cudaStream_t, const int*); \
+  template int run_div<DIM, DEG, T, true>(const dg_mesh*, const T*, const T*, T, T*, cudaStream_t, const int*);  \
+  template int run_gmres<DIM, DEG, T>(const dg_mesh*, const double*, const T*, const double*, double*, double,    \
+                                      double, double, int, int, int, T*, T*, double*, double*, int, double*,      \
+                                      double*, unsigned long long*, cudaStream_t);                               \
+  template int run_gmres_batched<DIM, DEG, T>(dg_ctx*, const GmresItem<T>*, int, int, int*, cudaStream_t);
 
 }  // namespace dg

@@ -248,7 +248,7 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
   const int64_t Nn = S->Nn;
   const int restart = std::min(o->restart, S->restart);
   auto A64 = [&](const double* x, double* y, const int* skip) {
-    return op_helmholtz<double>(m, S->h, x, y, alpha, m->d_face_scratch64, m->d_vec_scratch64, s, skip);
+    return op_helmholtz<double>(m, S->h, x, y, alpha, m->d_vec_scratch64, s, skip);
   };
   GmresResult res;
   int rc;
@@ -279,8 +279,7 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
   to_f32_kernel<<<gridn(Nn), 256, 0, s>>>(S->h, h32, Nn);
   count_launches(S->ctx, 1);
   auto A32 = [&](const float* x, float* y, const int* skip) {
-    return op_helmholtz<float>(m, h32, x, y, (float)alpha, (float*)m->d_face_scratch64,
-                               (float*)m->d_vec_scratch64, s, skip);
+    return op_helmholtz<float>(m, h32, x, y, (float)alpha, (float*)m->d_vec_scratch64, s, skip);
   };
   double bn2 = 0.0, rn2 = 0.0;
   double* scal = S->gm64.d.scal;  // reuse: [6] = ||b||^2, [7] = ||r||^2
@@ -332,10 +331,10 @@ int step_explicit(dg_state* S, const double* U, double* E, cudaStream_t s) {
   return check("sponge layer");
 }
 int step_grad(dg_state* S, const double* p, double* g, cudaStream_t s) {
-  return op_grad<double>(S->mesh, p, nullptr, g, S->mesh->d_face_scratch64, s, nullptr);
+  return op_grad<double>(S->mesh, p, nullptr, g, s, nullptr);
 }
 int step_div(dg_state* S, const double* f, double* out, cudaStream_t s) {
-  return op_div<double>(S->mesh, f, out, S->mesh->d_face_scratch64, s, nullptr);
+  return op_div<double>(S->mesh, f, out, s, nullptr);
 }
 
 }  // namespace

@@ -117,6 +117,35 @@ def test_implicit_operators_fp64(dg, ctx, name, dim, r):
     assert _rel(Ap.cpu().numpy(), ref.helmholtz(p0, h0, alpha)) < 1e-12
 
 
+@pytest.mark.parametrize("name,dim,r", CASES)
+def test_implicit_operators_fp32(dg, ctx, name, dim, r):
+    """FP32 gradient, divergence and Helmholtz operator (one launch per operator; on these
+    meshes, affine in x and y, the metric terms are recomputed from the nodal heights) against
+    the FP64 oracle, to FP32 accuracy."""
+    case = _case(name, dim, r)
+    ref = DG(case)
+    mesh = dg.Mesh(ctx, case)
+    rng = np.random.default_rng(12)
+    shp = (ref.mesh.K, ref.mesh.nc)
+    p0 = 100.0 * rng.standard_normal(shp)
+    h0 = 3.5e5 * (1.0 + 0.05 * rng.random(shp))
+    f0 = rng.standard_normal((dim,) + shp)
+    p, h, f = (torch.from_numpy(a).float().cuda() for a in (p0, h0, f0))
+    p0, h0, f0 = (a.astype(np.float32).astype(np.float64) for a in (p0, h0, f0))  # the same inputs
+    g = torch.empty((dim,) + shp, dtype=torch.float32, device="cuda")
+    dv = torch.empty(shp, dtype=torch.float32, device="cuda")
+    Ap = torch.empty(shp, dtype=torch.float32, device="cuda")
+    dg.dg_apply_grad(ctx, mesh, p, g, h=h, precision=dg.DG_FP32)
+    dg.dg_apply_div(ctx, mesh, f, dv, precision=dg.DG_FP32)
+    alpha = (0.3 * case.dt) ** 2
+    dg.dg_apply_implicit(ctx, mesh, h, p, Ap, alpha, precision=dg.DG_FP32)
+    torch.cuda.synchronize()
+    e = [_per_var_rel(g.double().cpu().numpy(), h0[None] * ref.grad(p0)),
+         _rel(dv.double().cpu().numpy(), ref.div(f0)),
+         _rel(Ap.double().cpu().numpy(), ref.helmholtz(p0, h0, alpha))]
+    assert max(e) < 2e-5, e
+
+
 @pytest.mark.parametrize("name,dim,r", [("tiny", 2, 3), ("tiny", 3, 2), ("hill2d", 2, 4)])
 def test_conservation_sums(dg, ctx, name, dim, r):
     case = _case(name, dim, r)
@@ -179,9 +208,9 @@ def test_fp32_explicit_apply_accuracy(dg, ctx):
 @pytest.mark.parametrize("name,dim,r", CASES)
 @pytest.mark.parametrize("terms", ["full", "imex"])
 def test_fp32_explicit_apply_all_meshes(dg, ctx, name, dim, r, terms):
-    """FP32 explicit apply (one pass, metric terms from z, where the mesh allows) against the FP64
-    oracle on every parity mesh and both term sets, and its mass balance: the face fluxes are the
-    same bits on both sides, so sum w J R_rho vanishes to FP32 rounding."""
+    """FP32 explicit apply (perturbation state, FP64 background added inside) against the FP64
+    oracle on every parity mesh and both term sets, and its mass balance: each face flux is
+    computed once and taken by both sides, so sum w J R_rho vanishes to FP32 rounding."""
     case = _case(name, dim, r)
     ref = DG(case)
     mesh = dg.Mesh(ctx, case)

@@ -34,8 +34,10 @@ sys.path.insert(0, ROOT)
 #   Helmholtz apply: bytes/node = 3 s;       flops/node = 2 (2dn + 2d^2) + 10
 P_VOL = {2: 25, 3: 45}
 P_FACE = {2: 70, 3: 90}
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz (nominal 1.25 TF)
-FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz
+# ALU peaks: measured at start-up by the library's FMA-throughput probe (measure_alu_peaks); these
+# nominal figures (SM count x FMA lanes x 2 x maximum clock) stand in only if the probe fails
+ALU_PEAK_TFLOPS = {"fp64": 152 * 4 * 2.07e9 / 1e12, "fp32": 152 * 256 * 2.07e9 / 1e12}
+ALU_PEAK_SOURCE = "nominal"
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel as it
 # stands (the persistent solve with the autotuned Chebyshev body, FP64, on hill2d); set to None
@@ -76,6 +78,45 @@ def measured_peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def measure_alu_peaks(dg, torch, reps=5):
+    """FP64 and FP32 FMA throughput of the whole GPU: the library's probe (16 independent FMA chains
+    per thread, 8 CTAs of 256 threads per SM), best of `reps` launches timed with CUDA events, with
+    the SM clock sampled meanwhile.  Sets ALU_PEAK_TFLOPS to the measured values."""
+    global ALU_PEAK_SOURCE
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = 8 * sms
+    stream = torch.cuda.current_stream()
+    out = {}
+    clk = Clocks(os.path.join(tempfile.gettempdir(), "dg_bench_peak_clocks.csv"))
+    with clk:
+        for name, prec, dtype, iters in (("fp64", dg.DG_FP64, torch.float64, 4096),
+                                         ("fp32", dg.DG_FP32, torch.float32, 262144)):
+            buf = torch.empty(blocks * 256, dtype=dtype, device="cuda")
+            dg.dg_peak_fma(prec, 64, blocks, buf)
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fl = dg.dg_peak_fma(prec, iters, blocks, buf)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = fl / (best / 1e3) / 1e12
+            if not math.isfinite(float(buf.sum())):
+                raise RuntimeError("FMA probe produced non-finite values")
+    c = clk.summary(torch.cuda.current_device())
+    for k in ("fp64", "fp32"):
+        ALU_PEAK_TFLOPS[k] = out[k]
+    ALU_PEAK_SOURCE = "measured"
+    return {"fp64_tflops": out["fp64"], "fp32_tflops": out["fp32"], "sm_mhz": c.get("sm_mhz"),
+            "sm_max_mhz": c.get("sm_max_mhz"), "reasons": c.get("reasons"),
+            "how": "dg_peak_fma: 16 independent FMA chains per thread, %d CTAs x 256 threads, best of %d "
+                   "launches timed with CUDA events" % (blocks, reps)}
 
 
 class Clocks:
@@ -253,7 +294,8 @@ def apply_sweep(dg, torch, case_name, reps=10):
         return statistics.median(ms)
 
     n = mesh.n_nodes
-    for prec, name, s_b, peak in ((dg.DG_FP64, "fp64", 8, FP64_PEAK_TFLOPS), (dg.DG_FP32, "fp32", 4, FP32_PEAK_TFLOPS)):
+    for prec, name, s_b in ((dg.DG_FP64, "fp64", 8), (dg.DG_FP32, "fp32", 4)):
+        peak = ALU_PEAK_TFLOPS[name]
         Uin = U if prec == dg.DG_FP64 else Up32
         R = torch.empty_like(Uin)
         t = timeit(lambda: dg.dg_apply_explicit(ctx, mesh, Uin, R, prec, dg.DG_TERMS_FULL))
@@ -271,8 +313,8 @@ def apply_sweep(dg, torch, case_name, reps=10):
     out["workload"] = "%s: %d cells, degree %d, %d DoF (vectors larger than L2)" % (
         case_name, mesh.n_cells, case.degree, mesh.n_dof)
     out["hbm_peak_gbs"] = hbm
-    out["peaks"] = "HBM %s; FP64 %.3f and FP32 %.1f TFLOP/s derived from SM count and clock" % (
-        src, FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS)
+    out["peaks"] = "HBM %s (%.0f GB/s); FP64 %.3f and FP32 %.1f TFLOP/s %s (FMA-throughput probe)" % (
+        src, hbm, ALU_PEAK_TFLOPS["fp64"], ALU_PEAK_TFLOPS["fp32"], ALU_PEAK_SOURCE)
     mesh.close()
     ctx.close()
     return out
@@ -433,8 +475,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    try:
+        peaks = measure_alu_peaks(dg, torch)
+    except Exception as e:  # the nominal figures stay, and the line says so
+        peaks = {"error": str(e)[:200]}
     if args.sweep_only:
-        print(json.dumps({"applies": apply_sweep(dg, torch, args.sweep_workload)}))
+        print(json.dumps({"alu_peaks": peaks, "applies": apply_sweep(dg, torch, args.sweep_workload)}))
         return
     if world > 1:
         import torch.distributed as dist
@@ -617,9 +663,10 @@ def main():
         flops = helm_flops
         name = dom
     achieved = flops / (avg_ms / 1e3) / 1e12
-    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_source": "derived FP64 rate: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+    pk = ALU_PEAK_TFLOPS[args.precision]
+    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk,
+            "peak_source": "%s %s FMA throughput (dg_peak_fma probe at start-up)" % (ALU_PEAK_SOURCE, args.precision),
             "traffic": NCU_TRAFFIC_BYTES.get(traffic_key), "traffic_unit": "bytes per launch",
             "avg_launch_us": avg_ms * 1e3, "launches": cats[dom]["count"],
             "hbm_peak_gbs": hbm, "hbm_peak_source": peak_src}
@@ -637,7 +684,7 @@ def main():
         "autotuned_solver": tuned,
         "fp32_refined": fp32,
         "other_krylov_forms": cg,
-        "e2e": e2e, "gpu_launches": launches,
+        "e2e": e2e, "gpu_launches": launches, "alu_peaks": peaks,
         "clocks": clk.summary(local),
     }
     if rank == 0 and not args.no_sweep:

@@ -181,6 +181,31 @@ typedef struct {
   double sponge_depth;    /* (m), 0..H                                          */
   double sponge_rate;     /* tau at the top (1/s), >= 0                         */
   double sponge_u0;       /* reference x-velocity (m/s)                         */
+  /* Optional caller-built geometry and topology (for meshes generated
+   * elsewhere, as the paper's are).  Each may be NULL / 0: then it is built
+   * from the tree and the terrain map above.  Host arrays, read during the
+   * call only, in the layouts dg_mesh_get_coords / dg_mesh_get_faces export:
+   *  - node_xyz [dim][n_cells][nodes_per_cell]: the nodal physical
+   *    coordinates (GLL nodes of each cell, node index as above).  Checked:
+   *    J > 0 at every node (DG_EINVAL), and watertight faces -- the two sides
+   *    of a conforming face, and a fine face against its coarse face's
+   *    polynomial, agree to 1e-9 of the domain size (DG_EUNBALANCED).
+   *  - the three face tables, given together (all or none): conforming
+   *    [n_conforming*4] (minus cell, minus local face, plus cell, plus local
+   *    face), subfaces [n_subfaces*4] (fine cell, fine local face, coarse
+   *    cell, subface position), walls [n_walls*2] (cell, local face).
+   *    Checked against level/ijk (DG_EUNBALANCED): every cell face listed
+   *    exactly once, opposite local faces, neighbours adjacent (periodic axes
+   *    wrap) at the same level on conforming faces and one level apart on 2:1
+   *    faces (position s matching), walls on non-periodic domain boundaries,
+   *    the 2^(dim-1) subfaces of each coarse face complete. */
+  const double* node_xyz;
+  int64_t n_conforming;
+  const int32_t* conforming;
+  int64_t n_subfaces;
+  const int32_t* subfaces;
+  int64_t n_walls;
+  const int32_t* walls;
 } dg_mesh_desc;
 
 typedef struct {

@@ -6,6 +6,7 @@ step of the computation runs in the library's CUDA kernels.
 """
 
 import ctypes
+from ctypes import c_double
 
 import numpy as np
 import torch
@@ -61,8 +62,12 @@ class Context:
             pass
 
 
-def mesh_desc(case, gravity=None):
-    """dg_mesh_desc of a workload description; returns (desc, arrays to keep alive)."""
+def mesh_desc(case, gravity=None, node_xyz=None, faces=None):
+    """dg_mesh_desc of a workload description; returns (desc, arrays to keep alive).
+
+    node_xyz (dim x cells x nodes, float64) and faces ((conforming, subfaces, walls) int32 tables in
+    the layout Mesh.faces() returns) optionally replace the geometry and connectivity the library
+    would build from the tree and the terrain map."""
     d = B.MeshDesc()
     d.dim = case.dim
     d.degree = case.degree
@@ -91,7 +96,22 @@ def mesh_desc(case, gravity=None):
     d.sponge_depth = sp.get("depth", 0.0)
     d.sponge_rate = sp.get("rate", 0.0)
     d.sponge_u0 = sp.get("u0", 0.0)
-    return d, (level, ijk)
+    keep = [level, ijk]
+    if node_xyz is not None:
+        X = np.ascontiguousarray(node_xyz, dtype=np.float64)
+        if X.shape != (case.dim, case.n_cells, case.nodes_per_cell):
+            raise ValueError("node_xyz must have shape (dim, cells, nodes per cell)")
+        d.node_xyz = X.ctypes.data_as(ctypes.POINTER(c_double))
+        keep.append(X)
+    if faces is not None:
+        conf, subs, walls = (np.ascontiguousarray(t, dtype=np.int32) for t in faces)
+        for name, t, w in (("conforming", conf, 4), ("subfaces", subs, 4), ("walls", walls, 2)):
+            if t.ndim != 2 or t.shape[1] != w:
+                raise ValueError("%s table must have shape (n, %d)" % (name, w))
+            setattr(d, "n_" + name, t.shape[0])
+            setattr(d, name, t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+            keep.append(t)
+    return d, tuple(keep)
 
 
 def init_params(case):
@@ -110,8 +130,8 @@ def init_params(case):
 class Mesh:
     """dg_mesh built from a workload description (see workloads.Case)."""
 
-    def __init__(self, ctx, case, gravity=None):
-        d, self._keep = mesh_desc(case, gravity)
+    def __init__(self, ctx, case, gravity=None, node_xyz=None, faces=None):
+        d, self._keep = mesh_desc(case, gravity, node_xyz, faces)
         h = ctypes.c_void_p()
         check(lib.dg_mesh_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "dg_mesh_create")
         self.handle = h

@@ -64,6 +64,10 @@ struct MeshView {
   const int* fnode_m;    // [nf*NF] node index of each face node on the minus side
   const int* fnode_p;    // [nf*NF] node index on the plus side (conforming faces; -1 otherwise)
   const int* cell_cmask; // [n_cells] bit lf set if local face lf is the coarse side of a 2:1 face
+  // [n_cells*2*dim] per cell face: (neighbour cell << 4) | (s << 2) | kind, read as unsigned;
+  // kind 0 conforming (the neighbour), 1 fine side of a 2:1 face (the coarse cell, s = the
+  // subface position), 2 coarse side, 3 wall
+  const int* cell_link;
   const T* tab;     // packed Tables1D of the mesh's degree
   T gravity;
   // Geometry in compact form, for kernels that recompute the metric terms:

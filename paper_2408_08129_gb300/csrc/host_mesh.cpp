@@ -90,6 +90,111 @@ int host_face_node(int dim, int n, int lf, int k) {
   return idx[0] + n * idx[1] + n * n * idx[2];
 }
 
+// Caller-given conforming faces and walls, checked against the cells' levels
+// and integer coordinates (the subfaces are checked here too and copied by the
+// caller of this function).
+int caller_topology(dg_mesh* m, std::vector<int32_t>& conf, std::vector<int32_t>& walls) {
+  const dg_mesh_desc& d = m->desc;
+  const int dim = d.dim;
+  const int64_t K = d.n_cells;
+  if (!d.conforming || !d.subfaces || !d.walls)
+    if (!((d.conforming || d.n_conforming == 0) && (d.subfaces || d.n_subfaces == 0) && (d.walls || d.n_walls == 0)))
+      return fail(DG_EINVAL, "face table pointer missing for a non-zero count");
+  if (d.n_conforming < 0 || d.n_subfaces < 0 || d.n_walls < 0) return fail(DG_EINVAL, "negative face count");
+  if (d.n_conforming + d.n_subfaces + d.n_walls > ((int64_t)1 << 29)) return fail(DG_EINVAL, "too many faces");
+  auto cell_ok = [&](int64_t c) { return c >= 0 && c < K; };
+  auto lf_ok = [&](int lf) { return lf >= 0 && lf < 2 * dim; };
+  // same-level neighbour coordinate of cell c across local face lf; false at a wall
+  auto neighbour = [&](int64_t c, int lf, int* nb) {
+    const int l = m->level[c], a = lf >> 1;
+    for (int b = 0; b < 3; ++b) nb[b] = b < dim ? m->ijk[c * dim + b] : 0;
+    nb[a] += (lf & 1) ? 1 : -1;
+    const int nmax = d.base[a] << l;
+    if (nb[a] < 0 || nb[a] >= nmax) {
+      if (!d.periodic[a]) return false;
+      nb[a] = (nb[a] + nmax) % nmax;
+    }
+    return true;
+  };
+  for (int64_t j = 0; j < d.n_conforming; ++j) {
+    const int32_t* e = d.conforming + 4 * j;
+    if (!cell_ok(e[0]) || !cell_ok(e[2]) || !lf_ok(e[1]) || e[3] != (e[1] ^ 1))
+      return fail(DG_EUNBALANCED, "bad conforming face entry");
+    int nb[3];
+    if (m->level[e[0]] != m->level[e[2]] || !neighbour(e[0], e[1], nb))
+      return fail(DG_EUNBALANCED, "conforming face between cells that are not same-level neighbours");
+    for (int b = 0; b < dim; ++b)
+      if (nb[b] != m->ijk[(int64_t)e[2] * dim + b])
+        return fail(DG_EUNBALANCED, "conforming face between cells that are not same-level neighbours");
+    conf.insert(conf.end(), e, e + 4);
+  }
+  for (int64_t j = 0; j < d.n_subfaces; ++j) {
+    const int32_t* e = d.subfaces + 4 * j;
+    if (!cell_ok(e[0]) || !cell_ok(e[2]) || !lf_ok(e[1]) || e[3] < 0 || e[3] >= (1 << (dim - 1)))
+      return fail(DG_EUNBALANCED, "bad subface entry");
+    int nb[3];
+    if (m->level[e[0]] != m->level[e[2]] + 1 || !neighbour(e[0], e[1], nb))
+      return fail(DG_EUNBALANCED, "2:1 face between cells that are not one level apart and adjacent");
+    int s = 0, t = 0;
+    for (int b = 0; b < dim; ++b) {
+      if (nb[b] >> 1 != m->ijk[(int64_t)e[2] * dim + b])
+        return fail(DG_EUNBALANCED, "2:1 face between cells that are not one level apart and adjacent");
+      if (b == (e[1] >> 1)) continue;
+      s |= (m->ijk[(int64_t)e[0] * dim + b] & 1) << t;
+      ++t;
+    }
+    if (s != e[3]) return fail(DG_EUNBALANCED, "subface position does not match the cell coordinates");
+  }
+  for (int64_t j = 0; j < d.n_walls; ++j) {
+    const int32_t* e = d.walls + 2 * j;
+    int nb[3];
+    if (!cell_ok(e[0]) || !lf_ok(e[1]) || neighbour(e[0], e[1], nb))
+      return fail(DG_EUNBALANCED, "wall entry not on a non-periodic domain boundary");
+    walls.insert(walls.end(), e, e + 2);
+  }
+  return DG_OK;
+}
+
+// Caller-given node coordinates must close every face: both sides of a
+// conforming face at the same points, and each fine face on its coarse face's
+// polynomial (evaluated at the fine points with the subinterval
+// interpolation), to 1e-9 of the domain size.
+int check_watertight(const dg_mesh* m, const Tables1D& tab, const std::vector<int>& face_m,
+                     const std::vector<int>& face_lfm, const std::vector<int>& face_p,
+                     const std::vector<int>& face_lfp, const std::vector<int>& face_s) {
+  const int dim = m->dim, n = m->n, nc = m->nc, NF = m->nf_nodes;
+  const int64_t K = m->K;
+  double ext = 0.0;
+  for (int a = 0; a < dim; ++a) ext = std::max(ext, m->desc.extent[a]);
+  const double tol = 1e-9 * ext;
+  auto X = [&](int b, int64_t c, int q) { return m->X[((size_t)b * K + c) * nc + q]; };
+  for (int f = 0; f < m->nconf + m->nsub; ++f) {
+    const bool sub = f >= m->nconf;
+    for (int k = 0; k < NF; ++k) {
+      const int qm = host_face_node(dim, n, face_lfm[f], k);
+      for (int b = 0; b < dim; ++b) {
+        double xo;
+        if (!sub) {
+          xo = X(b, face_p[f], host_face_node(dim, n, face_lfp[f], k));
+        } else {
+          // coarse face polynomial at fine face node k of subface position s
+          const int s = face_s[f], k1 = k % n, k2 = k / n;
+          xo = 0.0;
+          for (int j2 = 0; j2 < (dim == 3 ? n : 1); ++j2)
+            for (int j1 = 0; j1 < n; ++j1) {
+              double w = tab.I[(size_t)(s & 1) * n * n + (size_t)k1 * n + j1];
+              if (dim == 3) w *= tab.I[(size_t)((s >> 1) & 1) * n * n + (size_t)k2 * n + j2];
+              xo += w * X(b, face_p[f], host_face_node(dim, n, face_lfp[f], j1 + n * j2));
+            }
+        }
+        if (!(std::fabs(X(b, face_m[f], qm) - xo) <= tol))
+          return fail(DG_EUNBALANCED, "node coordinates are not watertight across a face");
+      }
+    }
+  }
+  return DG_OK;
+}
+
 int build_mesh(dg_mesh* m) {
   const dg_mesh_desc& d = m->desc;
   const int dim = d.dim, r = d.degree, n = r + 1;
@@ -131,7 +236,16 @@ int build_mesh(dg_mesh* m) {
     int fine, lff, coarse, lfc, s;
   };
   std::vector<Sub> subs;
-  for (int64_t c = 0; c < K; ++c) {
+  const bool caller_faces = d.conforming || d.subfaces || d.walls;
+  if (caller_faces) {
+    int rc = caller_topology(m, conf, walls);
+    if (rc != DG_OK) return rc;
+    for (int64_t j = 0; j < d.n_subfaces; ++j) {
+      const int32_t* e = d.subfaces + 4 * j;
+      subs.push_back({e[0], e[1], e[2], e[1] ^ 1, e[3]});
+    }
+  }
+  for (int64_t c = 0; c < (caller_faces ? 0 : K); ++c) {
     const int l = m->level[c];
     int ijk[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) ijk[a] = m->ijk[c * dim + a];
@@ -206,13 +320,20 @@ int build_mesh(dg_mesh* m) {
   const int nf = m->nf;
   std::vector<int> face_m(nf), face_lfm(nf), face_p(nf), face_lfp(nf), face_s(nf, 0);
   std::vector<int> cell_face(K * 2 * dim, -1);
+  // every cell face takes exactly one entry (caller tables may list one twice)
+  auto claim = [&](int c, int lf, int code) {
+    int& slot = cell_face[(size_t)c * 2 * dim + lf];
+    if (slot >= 0) return false;
+    slot = code;
+    return true;
+  };
   for (int f = 0; f < m->nconf; ++f) {
     face_m[f] = conf[4 * f];
     face_lfm[f] = conf[4 * f + 1];
     face_p[f] = conf[4 * f + 2];
     face_lfp[f] = conf[4 * f + 3];
-    cell_face[face_m[f] * 2 * dim + face_lfm[f]] = (f << 2) | 0;
-    cell_face[face_p[f] * 2 * dim + face_lfp[f]] = (f << 2) | 1;
+    if (!claim(face_m[f], face_lfm[f], (f << 2) | 0) || !claim(face_p[f], face_lfp[f], (f << 2) | 1))
+      return fail(DG_EUNBALANCED, "a cell face is listed twice");
   }
   const int nsubface = 1 << (dim - 1);
   for (int j = 0; j < m->nsub; ++j) {
@@ -223,14 +344,16 @@ int build_mesh(dg_mesh* m) {
     face_p[f] = s.coarse;
     face_lfp[f] = s.lfc;
     face_s[f] = s.s;
-    cell_face[s.fine * 2 * dim + s.lff] = (f << 2) | 0;
+    if (!claim(s.fine, s.lff, (f << 2) | 0)) return fail(DG_EUNBALANCED, "a cell face is listed twice");
     if (s.s == 0) {
       // the coarse face's subfaces must be the next 2^(d-1) entries, s = 0, 1, ...
       for (int q = 0; q < nsubface; ++q) {
         if (j + q >= m->nsub || subs[j + q].coarse != s.coarse || subs[j + q].lfc != s.lfc || subs[j + q].s != q)
           return fail(DG_EUNBALANCED, "incomplete set of subfaces on a 2:1 face");
       }
-      cell_face[s.coarse * 2 * dim + s.lfc] = (f << 2) | 2;
+      if (!claim(s.coarse, s.lfc, (f << 2) | 2)) return fail(DG_EUNBALANCED, "a cell face is listed twice");
+    } else if (j == 0 || subs[j - 1].coarse != s.coarse || subs[j - 1].lfc != s.lfc) {
+      return fail(DG_EUNBALANCED, "incomplete set of subfaces on a 2:1 face");
     }
   }
   for (int j = 0; j < m->nwall; ++j) {
@@ -239,7 +362,7 @@ int build_mesh(dg_mesh* m) {
     face_lfm[f] = walls[2 * j + 1];
     face_p[f] = -1;
     face_lfp[f] = -1;
-    cell_face[face_m[f] * 2 * dim + face_lfm[f]] = (f << 2) | 3;
+    if (!claim(face_m[f], face_lfm[f], (f << 2) | 3)) return fail(DG_EUNBALANCED, "a cell face is listed twice");
   }
   for (size_t i = 0; i < cell_face.size(); ++i)
     if (cell_face[i] < 0) return fail(DG_EUNBALANCED, "mesh is not watertight");
@@ -261,7 +384,8 @@ int build_mesh(dg_mesh* m) {
     mi[3 * q + 1] = (q / n) % n;
     mi[3 * q + 2] = q / (n * n);
   }
-  for (int64_t c = 0; c < K; ++c) {
+  if (d.node_xyz) m->X.assign(d.node_xyz, d.node_xyz + (size_t)dim * K * nc);
+  for (int64_t c = 0; c < (d.node_xyz ? 0 : K); ++c) {
     const int l = m->level[c];
     int ijk[3] = {0, 0, 0}, bijk[3] = {0, 0, 0}, off[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) {
@@ -307,6 +431,13 @@ int build_mesh(dg_mesh* m) {
     }
     for (int b = 0; b < dim; ++b)
       for (int q = 0; q < nc; ++q) m->X[((size_t)b * K + c) * nc + q] = (*src)[(size_t)b * nc + q];
+  }
+
+  if (d.node_xyz) {
+    for (double v : m->X)
+      if (!std::isfinite(v)) return fail(DG_EINVAL, "non-finite node coordinate");
+    int rc = check_watertight(m, tab, face_m, face_lfm, face_p, face_lfp, face_s);
+    if (rc != DG_OK) return rc;
   }
 
   // height of every node above its computational height, and whether every
@@ -417,11 +548,20 @@ int build_mesh(dg_mesh* m) {
 
   // ---------------------------------------------------------------- upload
   const std::vector<double> tabp = tab.packed();
+  std::vector<int> cell_link((size_t)K * 2 * dim, 3);
+  for (int f = 0; f < nf; ++f) {
+    const int kind = f < m->nconf ? 0 : (f < m->nconf + m->nsub ? 1 : 3);
+    if (kind == 3) continue;
+    cell_link[(size_t)face_m[f] * 2 * dim + face_lfm[f]] =
+        (int)(((uint32_t)face_p[f] << 4) | ((uint32_t)face_s[f] << 2) | (uint32_t)kind);
+    if (kind == 0) cell_link[(size_t)face_p[f] * 2 * dim + face_lfp[f]] = (int)(((uint32_t)face_m[f] << 4) | 0u);
+    else cell_link[(size_t)face_p[f] * 2 * dim + face_lfp[f]] = 2;
+  }
   std::vector<int> cell_cmask(K, 0);
   for (int64_t c = 0; c < K; ++c)
     for (int lf = 0; lf < 2 * dim; ++lf)
       if ((cell_face[c * 2 * dim + lf] & 3) == 2) cell_cmask[c] |= 1 << lf;
-  const size_t n_int = (size_t)5 * nf + cell_face.size() + 2 * (size_t)nf * NF + 2 * (size_t)K;
+  const size_t n_int = (size_t)5 * nf + 2 * cell_face.size() + 2 * (size_t)nf * NF + 2 * (size_t)K;
   const size_t n_real = (size_t)dim * dim * m->Nn + 5 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size();
   auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
   DG_CUDA(cudaSetDevice(m->ctx->device));
@@ -448,6 +588,7 @@ int build_mesh(dg_mesh* m) {
   ibuf.insert(ibuf.end(), fnode_p.begin(), fnode_p.end());
   ibuf.insert(ibuf.end(), cell_cmask.begin(), cell_cmask.end());
   for (int64_t c = 0; c < K; ++c) ibuf.push_back((int)m->level[c]);
+  ibuf.insert(ibuf.end(), cell_link.begin(), cell_link.end());
   DG_CUDA(cudaMemcpy(m->d_int, ibuf.data(), ibuf.size() * sizeof(int), cudaMemcpyHostToDevice));
 
   std::vector<double> rbuf;
@@ -502,6 +643,7 @@ int build_mesh(dg_mesh* m) {
     v.gravity = (decltype(v.gravity))d.gravity;
     v.zdev = base + o_zdev;
     v.cell_level = v.cell_cmask + K;
+    v.cell_link = v.cell_level + K;
     for (int a = 0; a < 3; ++a) v.hb[a] = (decltype(v.gravity))(a < dim ? 0.5 * hb[a] : 0.0);
     v.geo_z = geo_z ? 1 : 0;
   };
@@ -537,6 +679,7 @@ extern "C" int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* desc, dg_mesh** o
   m->desc = *desc;
   m->desc.level = nullptr;
   m->desc.ijk = nullptr;
+  // the optional caller geometry and face tables are read by build_mesh during this call only
   m->level.assign(desc->level, desc->level + desc->n_cells);
   m->ijk.assign(desc->ijk, desc->ijk + desc->n_cells * desc->dim);
   for (uint8_t l : m->level)
@@ -550,6 +693,8 @@ extern "C" int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* desc, dg_mesh** o
   } catch (const std::exception& e) {
     st = fail(DG_EINVAL, e.what());
   }
+  m->desc.node_xyz = nullptr;
+  m->desc.conforming = m->desc.subfaces = m->desc.walls = nullptr;
   if (st != DG_OK) {
     dg_mesh_destroy(m);
     return st;

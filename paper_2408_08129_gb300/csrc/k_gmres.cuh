@@ -1146,6 +1146,13 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
 constexpr int kPowerIters = 24;
 constexpr double kLmaxMargin = 1.05;
 
+// The GMRES fallback of the Chebyshev solve, kept out of line: inlined, its
+// register needs would be imposed on the Chebyshev loop as well.
+template <int DIM, int DEG, typename TK, class Sync>
+__device__ __noinline__ void gmres_fallback(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw, bool record) {
+  gmres_body<DIM, DEG, TK, Sync>(a, sg, smem_raw, record);
+}
+
 template <int DIM, int DEG, typename TK, class Sync>
 __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw, bool record) {
   using S = Shape<DIM, DEG>;
@@ -1417,7 +1424,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
   if (diverged) {
     if (sg.rank == 0 && threadIdx.x == 0) a.lmax[0] = 0.0;  // re-estimate on the next solve
     sg.sync();
-    gmres_body<DIM, DEG, TK, Sync>(a, sg, smem_raw, record);
+    gmres_fallback<DIM, DEG, TK, Sync>(a, sg, smem_raw, record);
     if (sg.rank == 0 && threadIdx.x == 0) a.out[0] += total;
     return;
   }
@@ -1430,15 +1437,17 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
   }
 }
 
-template <int DIM, int DEG, typename TK>
+// One kernel per method (each allocates registers for its own body only; the
+// Chebyshev one holds the GMRES body too, its fallback).
+template <int DIM, int DEG, typename TK, int METHOD>
 __global__ void __launch_bounds__(256, 2) gmres_persistent_kernel(GmresPArgs<TK> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GridSync sg;
-  if (a.method == 1)
+  if (METHOD == 1)
     cg_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
-  else if (a.method == 2)
+  else if (METHOD == 2)
     gmres_cgs2_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
-  else if (a.method == 3)
+  else if (METHOD == 3)
     cheb_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
   else
     gmres_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);

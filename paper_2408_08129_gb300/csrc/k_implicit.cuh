@@ -183,45 +183,45 @@ __device__ __forceinline__ void coarse_pass(const MeshView<T>& mv, bool active, 
   }
 }
 
-// sum over the node's conforming and fine-side faces of 1/2 |N| n_b (p+ - p-);
-// GZ: the face normal |N| n is the node's own outward metric row +-Ja[a] (the
-// same face seen from either side; on a 2:1 face the fine side's)
-template <int DIM, int DEG, typename T, bool GZ = false>
-__device__ __forceinline__ void grad_face_terms(const MeshView<T>& mv, const T* __restrict__ p, const int* codes,
-                                                const int* id, T pv, const T* sI, T* facc,
-                                                const T (*Jl)[DIM] = nullptr) {
-  using S = Shape<DIM, DEG>;
-  constexpr int NF = S::NF, NC = S::NC;
-  const int64_t total = (int64_t)mv.nf * NF;
+// Face links of node id of cell c, one per axis: the link of the cell face the
+// node lies on along that axis (MeshView::cell_link), or kind 3 (no face
+// term) where the node is interior along the axis.  Loaded early so that
+// their latency overlaps other work.
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void load_face_links(const MeshView<T>& mv, int64_t c, const int* id, int* links) {
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    const int code = codes[a];
-    if (code < 0) continue;
-    const int f = code >> 2, side = code & 3;
-    if (side >= 2) continue;  // coarse side: coarse_pass; wall: p^ = p-, no jump
-    const int kt = tangential_index<DIM, DEG>(a, id);
-    const int64_t t = (int64_t)f * NF + kt;
-    T pm, pp;
-    if (side == 1) {
-      pp = pv;
-      pm = p[mv.fnode_m[t]];
-    } else {
-      pm = pv;
-      if (f < mv.nconf)
-        pp = p[mv.fnode_p[t]];
-      else
-        coarse_interp<DIM, DEG, T, 1>(p, 0, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], kt, sI, &pp);
-    }
-    if (GZ) {
-      const T jmp = (id[a] == DEG ? T(0.5) : T(-0.5)) * (side == 1 ? pm - pp : pp - pm);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) facc[b] += jmp * Jl[a][b];
-    } else {
-      const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) facc[b] += jmp * mv.fn[(int64_t)b * total + t];
-    }
+    links[a] = 3;
+    if (id[a] == 0 || id[a] == DEG) links[a] = mv.cell_link[c * 2 * DIM + 2 * a + (id[a] == DEG ? 1 : 0)];
   }
+}
+
+// The other side's NV values at the face node of node id on its face along
+// axis a (X[v * vstride + node]): on a conforming face the neighbour's node,
+// on the fine side of a 2:1 face the coarse cell's polynomial at this point.
+// link kind must be 0 or 1.
+template <int DIM, int DEG, typename T, int NV>
+__device__ __forceinline__ void other_trace(const T* __restrict__ X, int64_t vstride, int link, int a, const int* id,
+                                            const T* sI, T* out) {
+  constexpr int NC = Shape<DIM, DEG>::NC;
+  const int64_t nb = (int64_t)((unsigned)link >> 4);
+  const int lfo = 2 * a + (id[a] == DEG ? 0 : 1);  // the neighbour's face is the opposite one
+  const int kt = tangential_index<DIM, DEG>(a, id);
+  if ((link & 3) == 0) {
+    const int64_t o = nb * NC + face_node<DIM, DEG>(lfo, kt);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = X[(int64_t)v * vstride + o];
+  } else {
+    coarse_interp<DIM, DEG, T, NV>(X, vstride, nb * NC, lfo, (link >> 2) & 3, kt, sI, out);
+  }
+}
+
+// Outward face normal |N| n of node id on its face along axis a, times 1/2:
+// the node's own metric row +-Ja[a] / 2 (the same face seen from either side
+// of a conforming face; on a 2:1 face the fine side's).
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ T half_sign(int a, const int* id) {
+  return id[a] == DEG ? T(0.5) : T(-0.5);
 }
 
 // Cells [batch*CPB, batch*CPB + CPB): g_b = h [sum_a Ja^a_b (D_a p) + face_b / w_end] / J.
@@ -241,14 +241,15 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   const int64_t Nn = mv.n_nodes;
   const int64_t idx = c * NC + i;
   int id[3] = {i % N, (i / N) % N, i / (N * N)};
-  int codes[DIM];
+  int links[DIM];
   T Jl[DIM][DIM];
+  T po[DIM];  // the other side's value at this node's faces
   T scale = T(0), pv = T(0);
   const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch);
   if (active) {
     pv = p[idx];
     sp[lc * NC + i] = pv;
-    load_face_codes<DIM, DEG, T>(mv, c, id, codes);
+    load_face_links<DIM, DEG, T>(mv, c, id, links);
     if (GZ) {
       sz[lc * NC + i] = mv.zdev[idx];
       scale = h ? h[idx] : T(1);
@@ -259,6 +260,10 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
         for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
       scale = mv.invJ[idx] * (h ? h[idx] : T(1));
     }
+    // neighbour traces: issued before the barrier, their latency overlaps it
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+      if ((links[a] & 3) < 2) other_trace<DIM, DEG, T, 1>(p, 0, links[a], a, id, sII, &po[a]);
   }
   __syncthreads();
   T facc[DIM], dp[DIM];
@@ -280,7 +285,15 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
       for (int kk = 0; kk < N; ++kk) s += D[kk] * sp[i0 + kk * stride];
       dp[a] = s;
     }
-    grad_face_terms<DIM, DEG, T, GZ>(mv, p, codes, id, pv, sII, facc, Jl);
+    // face terms: 1/2 (p_other - p_own) |N| n on conforming and fine-side faces (zero jump on
+    // walls, p^ = p-; coarse sides in the coarse pass)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if ((links[a] & 3) >= 2) continue;
+      const T jmp = half_sign<DIM, DEG, T>(a, id) * (po[a] - pv);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) facc[b] += jmp * Jl[a][b];
+    }
   }
   // coarse sides: jump at each fine point from the fine value and the cell's own polynomial
   const int64_t total = (int64_t)mv.nf * NF;
@@ -310,52 +323,6 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
 
 // ---------------------------------------------------------------- divergence
 
-// sum over the node's conforming and fine-side faces of +-|N| {f}.n (+ on the
-// minus side, - on the plus side)
-template <int DIM, int DEG, typename T, bool GZ = false>
-__device__ __forceinline__ void div_face_terms(const MeshView<T>& mv, const T* __restrict__ fld, const int* codes,
-                                               const int* id, const T* fv, const T* sI, T* facc,
-                                               const T (*Jl)[DIM] = nullptr) {
-  using S = Shape<DIM, DEG>;
-  constexpr int NF = S::NF, NC = S::NC;
-  const int64_t total = (int64_t)mv.nf * NF;
-  const int64_t Nn = mv.n_nodes;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const int code = codes[a];
-    if (code < 0) continue;
-    const int f = code >> 2, side = code & 3;
-    if (side >= 2) continue;  // coarse side: coarse_pass; wall: zero normal flux
-    const int kt = tangential_index<DIM, DEG>(a, id);
-    const int64_t t = (int64_t)f * NF + kt;
-    T fo[DIM];  // the other side's values
-    if (side == 1) {
-      const int64_t im = mv.fnode_m[t];
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) fo[b] = fld[(int64_t)b * Nn + im];
-    } else if (f < mv.nconf) {
-      const int64_t ip = mv.fnode_p[t];
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) fo[b] = fld[(int64_t)b * Nn + ip];
-    } else {
-      coarse_interp<DIM, DEG, T, DIM>(fld, Nn, (int64_t)mv.face_p[f] * NC, mv.face_lfp[f], mv.face_s[f], kt, sI, fo);
-    }
-    if (GZ) {  // own outward normal +-Ja[a]
-      T s = T(0);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) s += (side == 1 ? fo[b] + fv[b] : fv[b] + fo[b]) * Jl[a][b];
-      facc[0] += (id[a] == DEG ? T(0.5) : T(-0.5)) * s;
-    } else {
-      // (minus + plus) in that order on both sides
-      T s = T(0);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) s += (side == 1 ? fo[b] + fv[b] : fv[b] + fo[b]) * mv.fn[(int64_t)b * total + t];
-      const T dh = T(0.5) * mv.fsj[t] * s;
-      facc[0] += (side == 1) ? -dh : dh;
-    }
-  }
-}
-
 // Cells of one batch: epi(idx, v) receives v = HELM ? scale * (ident p/(gamma-1) - alpha div) : div
 // at every node of the batch (the caller stores it, or fuses further pointwise work).
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
@@ -374,7 +341,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   const int64_t Nn = mv.n_nodes;
   const int64_t idx = c * NC + i;
   int id[3] = {i % N, (i / N) % N, i / (N * N)};
-  int codes[DIM];
+  int links[DIM];
   T ft[DIM];  // Ja^a . f for each axis a
   T fv[DIM];
   T ij = T(0), pv = T(0);
@@ -383,17 +350,21 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   if (active) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fv[b] = fld[(int64_t)b * Nn + idx];
-    load_face_codes<DIM, DEG, T>(mv, c, id, codes);
+    load_face_links<DIM, DEG, T>(mv, c, id, links);
     if (HELM) pv = p[idx];
     if (GZ) {
       sz[lc * NC + i] = mv.zdev[idx];
     } else {
       ij = mv.invJ[idx];
 #pragma unroll
+      for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
+#pragma unroll
       for (int a = 0; a < DIM; ++a) {
         T s = T(0);
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) s += mv.Ja[(int64_t)(a * DIM + b) * Nn + idx] * fv[b];
+        for (int b = 0; b < DIM; ++b) s += Jl[a][b] * fv[b];
         ft[a] = s;
       }
     }
@@ -429,7 +400,20 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     }
   }
   T facc = T(0);
-  if (active) div_face_terms<DIM, DEG, T, GZ>(mv, fld, codes, id, fv, sII, &facc, Jl);
+  // face terms: 1/2 (f_own + f_other).|N| n on conforming and fine-side faces (zero normal
+  // flux on walls; coarse sides in the coarse pass)
+  if (active) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if ((links[a] & 3) >= 2) continue;
+      T fo[DIM];
+      other_trace<DIM, DEG, T, DIM>(fld, Nn, links[a], a, id, sII, fo);
+      T sum = T(0);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) sum += (fv[b] + fo[b]) * Jl[a][b];
+      facc += half_sign<DIM, DEG, T>(a, id) * sum;
+    }
+  }
   // coarse sides: |N| {f}.n at each fine point from the fine value and the cell's own polynomial
   const int64_t total = (int64_t)mv.nf * NF;
   coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, bmask, sII + 2 * N * N, T(-1), sJ, &facc,

@@ -269,6 +269,8 @@ extern "C" int dg_serve_submit(dg_server* sv, const dg_request* req, uint64_t* i
   const dg_mesh_desc& d = req->mesh;
   if ((d.dim != 2 && d.dim != 3) || d.degree < 1 || d.degree > kMaxDegree || d.n_cells <= 0 || !d.level || !d.ijk)
     return fail(DG_EINVAL, "malformed request: bad mesh description");
+  if (d.node_xyz || d.conforming || d.subfaces || d.walls)
+    return fail(DG_EINVAL, "malformed request: serving builds meshes from the tree (no caller geometry or face tables)");
   if (!(req->dt > 0.0) || req->steps < 1) return fail(DG_EINVAL, "malformed request: dt and steps must be positive");
   if (req->init_kind < DG_INIT_REST || req->init_kind > DG_INIT_INFLOW || req->n_init_params < 0 ||
       req->n_init_params > 8)

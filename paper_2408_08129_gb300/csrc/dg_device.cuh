@@ -24,7 +24,7 @@ struct Shape {
   static constexpr int THREADS = ((CPB * NC + 31) / 32) * 32;
   // table offsets (see Tables1D)
   static constexpr int T_D = 0, T_DW = N * N, T_I = 2 * N * N, T_IT = 4 * N * N, T_W = 6 * N * N,
-                       T_IWEND = 6 * N * N + N, T_SIZE = 6 * N * N + N + 1;
+                       T_IWEND = 6 * N * N + N, T_XI = 6 * N * N + N + 1, T_SIZE = 6 * N * N + 2 * N + 1;
 };
 
 // node index inside the cell of face node k on local face lf = 2*axis + side
@@ -66,6 +66,23 @@ __device__ __forceinline__ double rsqrt64(double x) {
 #pragma unroll
   for (int i = 0; i < 2; ++i) y = y * fma(-hx, y * y, 1.5);
   return y;
+}
+
+// Hydrostatic background (rho_bar, p_bar) at height z from the mesh's cubic
+// Hermite table (heights outside the table clamp to its ends)
+template <typename T>
+__device__ __forceinline__ void background_at(const MeshView<T>& mv, T z, T& rb, T& pb) {
+  T s = (z - mv.bg_z0) * mv.bg_idz;
+  s = s < T(0) ? T(0) : (s > T(mv.bg_m) ? T(mv.bg_m) : s);
+  int k = (int)s;
+  if (k >= mv.bg_m) k = mv.bg_m - 1;
+  s -= T(k);
+  const T s2 = s * s, s3 = s2 * s;
+  const T h00 = T(2) * s3 - T(3) * s2 + T(1), h10 = s3 - T(2) * s2 + s, h01 = T(3) * s2 - T(2) * s3,
+          h11 = s3 - s2;
+  const T* e = mv.bg_tab + 4 * k;
+  pb = h00 * e[0] + h10 * e[1] + h01 * e[4] + h11 * e[5];
+  rb = h00 * e[2] + h10 * e[3] + h01 * e[6] + h11 * e[7];
 }
 
 // 1/(gamma-1) = 2.5 exactly: a multiplication instead of a division sequence

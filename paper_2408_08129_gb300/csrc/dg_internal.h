@@ -31,14 +31,14 @@ int cuda_fail(cudaError_t e, const char* what);
 //   Dw [n*n]  Dw[i*n+k] = w_k l_i'(xi_k) / w_i          (weak derivative / w_i)
 //   I  [2*n*n] I[s*n*n + f*n + j] = l_j((xi_f + 2s - 1)/2)  (coarse -> half s)
 //   It [2*n*n] It[s*n*n + i*n + f] = (w_f / w_i) I[s][f][i]  (its weighted transpose)
-//   w  [n], then 1/w_end (w_end = w_0 = w_r)
+//   w  [n], then 1/w_end (w_end = w_0 = w_r), then the nodes xi [n]
 struct Tables1D {
   int degree = 0;
   std::vector<double> xi, w, D, Dw, I, It;
   std::vector<double> packed() const;  // D|Dw|I|It|w|1/w_end
 };
 Tables1D make_tables(int degree);
-inline int table_size(int n) { return 6 * n * n + n + 1; }
+inline int table_size(int n) { return 6 * n * n + 2 * n + 1; }
 // Lagrange basis on `nodes` at point x: out[j] = l_j(x)
 void lagrange_eval(const std::vector<double>& nodes, double x, double* out);
 
@@ -80,6 +80,13 @@ struct MeshView {
   const int* cell_level;  // [n_cells] refinement level
   T hb[3];                // half width of a base cell per axis
   int geo_z;              // 1 if every cell is affine in x (and y)
+  const T* cell_zeta0;    // [n_cells] computational height of the cell's lower face
+  // Hydrostatic background as a function of height: cubic Hermite data at
+  // bg_m + 1 equally spaced heights from bg_z0 (spacing 1/bg_idz), four values
+  // per height: p_bar, dz dp_bar/dz, rho_bar, dz drho_bar/dz (dz = the spacing)
+  const T* bg_tab;
+  T bg_z0, bg_idz;
+  int bg_m;
 };
 
 }  // namespace dg

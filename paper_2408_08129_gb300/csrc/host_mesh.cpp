@@ -546,6 +546,36 @@ int build_mesh(dg_mesh* m) {
     }
   }
 
+  // the background as a function of height (cubic Hermite data every ~25 m;
+  // interpolation error ~ (dz / scale height)^4 / 384, far below FP32 rounding)
+  double zlo = 1e300, zhi = -1e300;
+  for (int64_t i = 0; i < m->Nn; ++i) {
+    const double z = m->X[(size_t)(dim - 1) * K * nc + (size_t)i];
+    zlo = std::min(zlo, z);
+    zhi = std::max(zhi, z);
+  }
+  zlo -= 1.0;
+  zhi += 1.0;
+  const int bg_m = (int)std::min(4096.0, std::max(16.0, std::ceil((zhi - zlo) / 25.0)));
+  const double bg_dz = (zhi - zlo) / bg_m;
+  std::vector<double> bgtab((size_t)4 * (bg_m + 1));
+  for (int k = 0; k <= bg_m; ++k) {
+    double rho, p;
+    const double z = zlo + k * bg_dz;
+    background(d, z, &rho, &p);
+    const double g = 9.81;
+    double drho = 0.0;
+    if (d.atm_kind == DG_ATM_ISOTHERMAL) drho = -rho * g / (kRgas * d.atm_T);
+    if (d.atm_kind == DG_ATM_STRATIFIED) drho = rho * (-rho * g / (kGamma * p) - d.atm_N * d.atm_N / g);
+    bgtab[4 * k] = p;
+    bgtab[4 * k + 1] = -rho * g * bg_dz;  // hydrostatic: dp/dz = -rho g
+    bgtab[4 * k + 2] = rho;
+    bgtab[4 * k + 3] = drho * bg_dz;
+  }
+  std::vector<double> zeta0(K);
+  for (int64_t c = 0; c < K; ++c)
+    zeta0[c] = m->ijk[c * dim + dim - 1] * (hb[dim - 1] / (double)(1 << m->level[c]));
+
   // ---------------------------------------------------------------- upload
   const std::vector<double> tabp = tab.packed();
   std::vector<int> cell_link((size_t)K * 2 * dim, 3);
@@ -562,7 +592,8 @@ int build_mesh(dg_mesh* m) {
     for (int lf = 0; lf < 2 * dim; ++lf)
       if ((cell_face[c * 2 * dim + lf] & 3) == 2) cell_cmask[c] |= 1 << lf;
   const size_t n_int = (size_t)5 * nf + 2 * cell_face.size() + 2 * (size_t)nf * NF + 2 * (size_t)K;
-  const size_t n_real = (size_t)dim * dim * m->Nn + 5 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size();
+  const size_t n_real = (size_t)dim * dim * m->Nn + 5 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size() +
+                        (size_t)K + bgtab.size();
   auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
   DG_CUDA(cudaSetDevice(m->ctx->device));
   DG_CUDA(cudaMalloc(&m->d_int, pad(n_int) * sizeof(int)));
@@ -611,6 +642,10 @@ int build_mesh(dg_mesh* m) {
   rbuf.insert(rbuf.end(), zdev.begin(), zdev.end());
   size_t o_tab = rbuf.size();
   rbuf.insert(rbuf.end(), tabp.begin(), tabp.end());
+  size_t o_zeta0 = rbuf.size();
+  rbuf.insert(rbuf.end(), zeta0.begin(), zeta0.end());
+  size_t o_bg = rbuf.size();
+  rbuf.insert(rbuf.end(), bgtab.begin(), bgtab.end());
   DG_CUDA(cudaMemcpy(m->d_f64, rbuf.data(), rbuf.size() * sizeof(double), cudaMemcpyHostToDevice));
   std::vector<float> fbuf(rbuf.begin(), rbuf.end());
   DG_CUDA(cudaMemcpy(m->d_f32, fbuf.data(), fbuf.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -646,6 +681,11 @@ int build_mesh(dg_mesh* m) {
     v.cell_link = v.cell_level + K;
     for (int a = 0; a < 3; ++a) v.hb[a] = (decltype(v.gravity))(a < dim ? 0.5 * hb[a] : 0.0);
     v.geo_z = geo_z ? 1 : 0;
+    v.cell_zeta0 = base + o_zeta0;
+    v.bg_tab = base + o_bg;
+    v.bg_z0 = (decltype(v.gravity))zlo;
+    v.bg_idz = (decltype(v.gravity))(1.0 / bg_dz);
+    v.bg_m = bg_m;
   };
   fill(m->v64, (const double*)m->d_f64);
   fill(m->v32, (const float*)m->d_f32);

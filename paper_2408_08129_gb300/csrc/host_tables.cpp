@@ -120,6 +120,7 @@ std::vector<double> Tables1D::packed() const {
   out.insert(out.end(), It.begin(), It.end());
   out.insert(out.end(), w.begin(), w.end());
   out.push_back(1.0 / w[0]);
+  out.insert(out.end(), xi.begin(), xi.end());
   return out;
 }
 

@@ -163,9 +163,7 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline_sample(case_name, seconds):
-    """Time the CPU oracle on a bounded number of steps in a single-threaded subprocess."""
-    code = r"""
+_ORACLE_STEPS = r"""
 import json, os, sys, time
 sys.path.insert(0, %r)
 from workloads import make_case
@@ -184,14 +182,67 @@ while True:
         break
 el = time.perf_counter() - t0
 print(json.dumps({"steps": n, "seconds": el, "dof": case.n_dof}))
-""" % (ROOT, case_name, seconds)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["dof"] * d["steps"] / d["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
-            "sample": "%d IMEX-RK2 step(s) of %s on 1 host thread (%.1f s)" % (d["steps"], case_name, d["seconds"])}
+"""
+
+
+def _one_thread_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def cpu_baseline_sample(case_name, seconds, replicas=None):
+    """Time the CPU oracle (as it stands) on whole IMEX-RK2 steps of the workload, on the host cores:
+    `replicas` independent single-threaded oracle processes (default: one per host core) stepping
+    the same case for about `seconds` each, and one of them alone.  Returns the all-cores figure
+    with the one-thread figure beside it."""
+    ncores = os.cpu_count() or 1
+    replicas = replicas or ncores
+    code = _ORACLE_STEPS % (ROOT, case_name, seconds)
+
+    def run(n):
+        procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                  text=True, env=_one_thread_env()) for _ in range(n)]
+        outs = []
+        for p in procs:
+            o, e = p.communicate(timeout=900)
+            if p.returncode != 0:
+                raise RuntimeError(e[-2000:])
+            outs.append(json.loads(o.strip().splitlines()[-1]))
+        return outs
+
+    one = run(1)[0]
+    many = run(replicas)
+    v1 = one["dof"] * one["steps"] / one["seconds"]
+    vall = sum(d["dof"] * d["steps"] / d["seconds"] for d in many)
+    return {"value": vall, "unit": "DoF/s", "cores": replicas, "kind": "oracle",
+            "sample": "%d independent single-threaded oracle processes on %d host cores, each %d-%d IMEX-RK2 "
+                      "steps of %s (about %.0f s each); whole-job DoF-steps/s" % (
+                          replicas, ncores, min(d["steps"] for d in many), max(d["steps"] for d in many),
+                          case_name, seconds),
+            "one_thread": {"value": v1, "unit": "DoF/s", "cores": 1,
+                           "sample": "%d step(s) of %s on 1 host thread (%.1f s)" % (one["steps"], case_name,
+                                                                                   one["seconds"])}}
+
+
+def start_oracle_step(case_name, path, threads):
+    """One oracle IMEX-RK2 step of a workload from its initial state, in a background process that
+    writes the result to `path` (.npy); returns the process."""
+    code = r"""
+import sys
+import numpy as np
+sys.path.insert(0, %r)
+from workloads import make_case
+from oracle.dg import DG
+from oracle.imex import Stepper
+case = make_case(%r, 0)
+dg = DG(case)
+U1 = Stepper(dg, tol=1e-12).step(dg.state(), case.dt)
+np.save(%r, U1)
+np.save(%r, dg.Ubg)
+""" % (ROOT, case_name, path, path + ".bg.npy")
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.DEVNULL, stderr=subprocess.PIPE,
+                            text=True, env=env)
 
 
 def run_reference(args):
@@ -199,7 +250,7 @@ def run_reference(args):
     if rank != 0:
         return
     per_step = max(3.0, 60.0 / max(1, args.steps + args.warmup))
-    cb = cpu_baseline_sample(args.workload, per_step * max(1, args.steps))
+    cb = cpu_baseline_sample(args.workload, min(20.0, per_step * max(1, args.steps)))
     line = {
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "DoF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
@@ -213,7 +264,8 @@ def run_reference(args):
 
 def precision_forms_3d(dg, torch, case_name="hill3d", steps=2, inner_tol=1e-6):
     """The 3D workload stepped in FP64 and in the FP32-refined form from the same start (autotuned
-    solver each): time per step and the FP32 form's deviation from the FP64 result."""
+    solver each): time per step, the FP32 form's deviation from the FP64 result, and each form's
+    state after one step (returned under "_one_step" for the comparison with the oracle)."""
     import numpy as np
     from workloads import make_case
 
@@ -228,7 +280,7 @@ def precision_forms_3d(dg, torch, case_name="hill3d", steps=2, inner_tol=1e-6):
     dg.dg_background(ctx, mesh, bg)
     bg = bg.cpu().numpy()
     stream = torch.cuda.current_stream()
-    out, res = {}, {}
+    out, res, one_step = {}, {}, {}
     for name, prec in (("fp64", dg.DG_FP64), ("fp32_refined", dg.DG_FP32)):
         o = dg.solver_opts(tol=1e-12, precision=prec, inner_tol=inner_tol)
         st.upload(U0)
@@ -244,6 +296,9 @@ def precision_forms_3d(dg, torch, case_name="hill3d", steps=2, inner_tol=1e-6):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         res[name] = st.download()
+        st.upload(U0)
+        dg.imex_rk2_step(ctx, mesh, st, case.dt, o)
+        one_step[name] = st.download()
         out[name] = {"ms_per_step": ms, "dof_steps_per_s": mesh.n_dof / (ms / 1e3),
                      "solver": mesh.autotuned()[name[:4]]["form"]}
     dev = max(np.linalg.norm(res["fp32_refined"][v] - res["fp64"][v])
@@ -255,7 +310,30 @@ def precision_forms_3d(dg, torch, case_name="hill3d", steps=2, inner_tol=1e-6):
     st.close()
     mesh.close()
     ctx.close()
+    out["_one_step"] = one_step
     return out
+
+
+def oracle_errors(forms, proc, path):
+    """Relative L2 error (largest over the variables, of the deviation from the background) of each
+    form's one-step state against the oracle's step, once the background oracle process is done."""
+    import numpy as np
+
+    one = forms.pop("_one_step")
+    try:
+        _, err = proc.communicate(timeout=1800)
+        if proc.returncode != 0:
+            raise RuntimeError(err[-500:])
+        U1 = np.load(path)
+        bg = np.load(path + ".bg.npy")
+    except Exception as e:  # reported, not hidden
+        forms["oracle"] = {"error": str(e)[:300]}
+        return forms
+    for name, U in one.items():
+        forms[name]["rel_err_vs_oracle_one_step"] = max(
+            float(np.linalg.norm(U[v] - U1[v]) / np.linalg.norm(U1[v] - bg[v])) for v in range(U.shape[0]))
+    forms["oracle"] = "one oracle IMEX-RK2 step from the same initial state (FP64, CPU), same dt and tolerances"
+    return forms
 
 
 def apply_sweep(dg, torch, case_name, reps=10):
@@ -383,11 +461,13 @@ def ensemble_bench(dg, torch, n_members=64, steps=10, inner_tol=1e-6):
     return out
 
 
-def serving_bench(dg, torch, n_requests=40, rate=20.0, dof_hi=3e5, steps_hi=40, budget=160e9, inner_tol=1e-6):
-    """Config-5 shape, bounded sample: Poisson arrivals, 2D/3D, degree 2-5, FP64 or FP32-refined."""
+def serving_bench(dg, torch, n_requests=24, rate=20.0, dof_hi=5e6, steps_lo=10, steps_hi=500, budget=160e9,
+                  inner_tol=1e-6):
+    """The serving stream: Poisson arrivals, 2D/3D, degree 2-5, DoF 1e4-5e6 log-uniform, 10-500 steps,
+    FP64 or FP32-refined; the first n_requests requests of the seeded trace."""
     from workloads.cases import serving_trace
 
-    trace = serving_trace(7, n_requests, rate, 1e4, dof_hi, 5, steps_hi)
+    trace = serving_trace(7, n_requests, rate, 1e4, dof_hi, steps_lo, steps_hi)
     ctx = dg.Context(torch.cuda.current_device())
     sv = dg.Server(ctx, int(budget))
     t0 = time.perf_counter()
@@ -415,9 +495,11 @@ def serving_bench(dg, torch, n_requests=40, rate=20.0, dof_hi=3e5, steps_hi=40, 
     def pct(q):
         return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] if lat else None
 
-    return {"workload": "%d requests, Poisson %.0f/s, 2D/3D, degree 2-5, DoF 1e4-%.0e, %d-%d steps, "
-                        "FP64 or FP32-refined 50/50, %.0f GB budget (bounded sample of the serving stream)"
-                        % (n_requests, rate, dof_hi, 5, steps_hi, budget / 1e9),
+    return {"workload": "%d requests, Poisson %.0f/s, 2D/3D, degree 2-5, DoF 1e4-%.0e log-uniform, %d-%d steps, "
+                        "FP64 or FP32-refined 50/50, %.0f GB budget (the first %d requests of the seeded stream; "
+                        "the full ranges of DoF and steps, fewer requests to keep the bench within minutes)"
+                        % (n_requests, rate, dof_hi, steps_lo, steps_hi, budget / 1e9, n_requests),
+            "dof_steps_total": dof_steps,
             "completed": len(ok), "p50_s": pct(0.5), "p99_s": pct(0.99), "makespan_s": span,
             "member_steps_per_s": steps_total / span, "dof_steps_per_s": dof_steps / span,
             "ticks": stats["ticks"]}
@@ -629,6 +711,12 @@ def main():
     e2e = {"value": world * dof * args.steps / e2e_s, "unit": "DoF/s",
            "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes)}
 
+    # the oracle's hill3d step for the precision forms, in the background while the GPU sections run
+    oracle_proc, oracle_path = None, None
+    if rank == 0 and not args.no_sweep:
+        oracle_path = os.path.join(tempfile.gettempdir(), "dg_bench_oracle_hill3d_%d.npy" % os.getpid())
+        oracle_proc = start_oracle_step("hill3d", oracle_path, max(1, (os.cpu_count() or 2) // 2))
+
     # roofline of the dominant operator class inside the timed region
     cats = {k: v for k, v in prof.items()
             if k in ("explicit", "helmholtz", "grad", "div", "krylov", "gmres") and v["count"]}
@@ -687,14 +775,17 @@ def main():
         "e2e": e2e, "gpu_launches": launches, "alu_peaks": peaks,
         "clocks": clk.summary(local),
     }
+    forms3d = None
     if rank == 0 and not args.no_sweep:
         line["applies"] = apply_sweep(dg, torch, args.sweep_workload)
-        line["precision_forms_3d"] = precision_forms_3d(dg, torch, inner_tol=args.inner_tol)
+        forms3d = precision_forms_3d(dg, torch, inner_tol=args.inner_tol)
     if rank == 0 and not args.no_ensemble:
         line["ensemble"] = ensemble_bench(dg, torch, inner_tol=args.inner_tol)
         line["serving"] = serving_bench(dg, torch, inner_tol=args.inner_tol)
+    if forms3d is not None:
+        line["precision_forms_3d"] = oracle_errors(forms3d, oracle_proc, oracle_path)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(args.workload, 12.0)
+        line["cpu_baseline"] = cpu_baseline_sample(args.workload, 10.0)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -1328,8 +1328,12 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         const double ib = 1.0 / beta, fr = floor * ib;
         sc[3] = beta;
         // steps the Chebyshev bound 2 q^k needs to reach the floor; well past that, the
-        // residual has stalled or grows slowly (a bound a little low)
-        sc[4] = fmin(2.0 * ceil(log(0.5 * fr) / logq) + 20.0, 1e9);
+        // residual has stalled or grows slowly (a bound a little low).  The stop test starts
+        // after 3/4 of those steps: the residual norms before that are not needed (a bound
+        // far too low makes that count small, so growth is still caught early)
+        const double kpred = ceil(log(0.5 * fr) / logq);
+        sc[4] = fmin(2.0 * kpred + 20.0, 1e9);
+        sc[7] = fmin(fmax(trunc(0.75 * kpred) - 1.0, 0.0), 1e9);
         sc[5] = ib;
         sc[6] = fr * fr;
         rel = beta / bn;  // reported by thread 0
@@ -1343,6 +1347,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     }
     if (total >= a.max_iters) break;
     const int cycle_cap = (int)sc[4];
+    const int kskip = (int)sc[7];
     int cycle_its = 0;
     const float ibeta = (float)sc[5];
     // the stop test compares (||r|| / beta)^2 with squared limits (no square root per step);
@@ -1380,9 +1385,13 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
           break;
         }
         if (rn2 <= floor2 || total >= a.max_iters || sg.failed()) break;  // same decision in every CTA
+      } else if (total >= a.max_iters || sg.failed()) {
+        break;
       }
       sg.sync();
       pc.mark(PH_GRAD_CELL);
+      // whether the next step tests this step's residual (the same in every CTA)
+      const bool want = cycle_its + 1 >= kskip;
       // divergence pass with the update: x += d, r -= A d, d = c1 d + c2 r
       const double rho1 = sc[0];
       const TK c1 = (TK)sc[1], c2 = (TK)sc[2];
@@ -1396,13 +1405,15 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         else
           a.x[i] += (double)di;
         d[i] = c1 * di + c2 * ri;
-        const float rs = (float)ri * ibeta;  // FP32: no FP64 instruction for the stop test
-        racc += rs * rs;
+        if (want) {
+          const float rs = (float)ri * ibeta;  // FP32: no FP64 instruction for the stop test
+          racc += rs * rs;
+        }
       };
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         div_cell_batch<DIM, DEG, TK, true>(a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi, bt, scellk, sJk, sDwk,
                                            sIIk);
-      {
+      if (want) {
         const float t = block_sum_f(racc, sred);
         if (threadIdx.x == 0) ((float*)a.partial)[sg.rank] = t;  // FP32 partials for the stop test
       }
@@ -1411,7 +1422,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       rho = rho1;
       ++total;
       ++cycle_its;
-      have_prev = true;
+      have_prev = want;
     }
     if (fold)
       for (int64_t i = tid; i < n; i += gstride) a.x[i] += (double)dx[i];

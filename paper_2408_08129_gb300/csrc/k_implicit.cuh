@@ -122,61 +122,82 @@ __device__ __forceinline__ void metric_from_z(const MeshView<T>& mv, int64_t c, 
 // (coarse_pass below), and each coarse face node then sums them through It.
 
 // Number of fine points behind one coarse face, and the shared-memory buffer
-// (elements) the coarse pass needs per cell batch for NV values per point.
+// (elements) the coarse pass needs per cell batch for NV values per point:
+// kCoarseSlots coarse faces per cell are handled in one round.
+constexpr int kCoarseSlots = 2;
 template <int DIM, int DEG>
 __host__ __device__ constexpr int coarse_points() {
   return Shape<DIM, DEG>::NSUB * Shape<DIM, DEG>::NF;
 }
 template <int DIM, int DEG, int NV>
 __host__ __device__ constexpr int coarse_buffer() {
-  return Shape<DIM, DEG>::CPB * NV * coarse_points<DIM, DEG>();
+  return Shape<DIM, DEG>::CPB * NV * coarse_points<DIM, DEG>() * kCoarseSlots;
 }
 
-// OR over the cells of batch `batch` of their coarse-side face masks, formed by
-// every warp on its own (lanes load one or two cells' masks and reduce), so
-// that the whole block agrees without a barrier
+// OR over the cells of batch `batch` of their coarse-side face masks, and the
+// largest number of coarse faces of one cell (in *nmax), formed by every warp
+// on its own (lanes load one or two cells' masks and reduce), so that the
+// whole block agrees without a barrier
 template <int DIM, int DEG, typename T>
-__device__ __forceinline__ unsigned batch_coarse_mask(const MeshView<T>& mv, int64_t batch) {
+__device__ __forceinline__ unsigned batch_coarse_mask(const MeshView<T>& mv, int64_t batch, int* nmax = nullptr) {
   constexpr int CPB = Shape<DIM, DEG>::CPB;
   const int lane = threadIdx.x & 31;
-  unsigned m = 0u;
+  unsigned m = 0u, k = 0u;
   for (int j = lane; j < CPB; j += 32) {
     const int64_t c = batch * CPB + j;
-    if (c < mv.n_cells) m |= (unsigned)mv.cell_cmask[c];
+    if (c < mv.n_cells) {
+      const unsigned cm = (unsigned)mv.cell_cmask[c];
+      m |= cm;
+      k = max(k, (unsigned)__popc(cm));
+    }
   }
+  if (nmax) *nmax = (int)__reduce_max_sync(0xffffffffu, k);
   return __reduce_or_sync(0xffffffffu, m);
 }
 
-// Coarse sides of the batch's 2:1 faces, one local face at a time.  For every
-// cell whose face lf is a coarse side, point(f, lf, s, q, j) writes the NV
-// face values of fine point q of subface s (face f + s) to the buffer at
-// sJ[(lc * NV + v) * NP + j], j = s * NF + q; then each node of that face adds
-// sum_s sum_q weight * value to acc[0..NV) with weight = sign * It.  Called by
-// the whole block with the batch's mask bmask (the same in every thread);
-// contains __syncthreads only for the faces some cell of the batch has.
+// Coarse sides of the batch's 2:1 faces.  For every cell, each of its coarse
+// faces (local face lf, first subface f) takes a slot; in rounds of
+// kCoarseSlots slots, point(f, lf, s, q, j, buf) writes the NV face values of
+// fine point q of subface s (face f + s) to buf[(lc * NV + v) * NP + j],
+// j = s * NF + q, buf being the slot's part of sJ; after one block barrier,
+// each node on those faces adds sum_s sum_q weight * value to acc[0..NV) with
+// weight = sign * It.  Called by the whole block with the batch's mask bmask
+// and largest slot count nmax (the same in every thread); contains
+// __syncthreads only when some cell of the batch has a coarse face.
 template <int DIM, int DEG, typename T, int NV, class Point>
 __device__ __forceinline__ void coarse_pass(const MeshView<T>& mv, bool active, int64_t c, int lc, int i,
-                                            const int* id, unsigned bmask, const T* sIt, T sign, T* sJ, T* acc,
-                                            Point&& point) {
+                                            const int* id, unsigned bmask, int nmax, const T* sIt, T sign, T* sJ,
+                                            T* acc, Point&& point) {
   using S = Shape<DIM, DEG>;
   constexpr int NF = S::NF, NC = S::NC, NP = coarse_points<DIM, DEG>();
+  constexpr int SLOT = S::CPB * NV * NP;
   if (bmask == 0u) return;
   const unsigned cmask = active ? (unsigned)mv.cell_cmask[c] : 0u;
-  for (int lf = 0; lf < 2 * DIM; ++lf) {
-    if (!((bmask >> lf) & 1u)) continue;
-    const bool mine = (cmask >> lf) & 1u;
-    const int a = lf >> 1;
-    const int f = mine ? (mv.cell_face[c * 2 * DIM + lf] >> 2) : 0;
-    if (mine)
-      for (int j = i; j < NP; j += NC) point(f, lf, j / NF, j % NF, j);
+  for (int r0 = 0; r0 < nmax; r0 += kCoarseSlots) {
+    int slot = 0;
+#pragma unroll
+    for (int lf = 0; lf < 2 * DIM; ++lf) {
+      if (!((cmask >> lf) & 1u)) continue;
+      const int sl = slot++ - r0;
+      if (sl < 0 || sl >= kCoarseSlots) continue;
+      const int f = mv.cell_face[c * 2 * DIM + lf] >> 2;
+      for (int j = i; j < NP; j += NC) point(f, lf, j / NF, j % NF, j, sJ + sl * SLOT);
+    }
     __syncthreads();
-    if (mine && id[a] == ((lf & 1) ? DEG : 0)) {
+    slot = 0;
+#pragma unroll
+    for (int lf = 0; lf < 2 * DIM; ++lf) {
+      if (!((cmask >> lf) & 1u)) continue;
+      const int sl = slot++ - r0;
+      const int a = lf >> 1;
+      if (sl < 0 || sl >= kCoarseSlots || id[a] != ((lf & 1) ? DEG : 0)) continue;
       const int kt = tangential_index<DIM, DEG>(a, id);
+      const T* buf = sJ + sl * SLOT;
       for (int s = 0; s < S::NSUB; ++s)
         for (int q = 0; q < NF; ++q) {
           const T wgt = sign * coarse_weight<DIM, DEG, T>(sIt, s, kt, q);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) acc[v] += wgt * sJ[(lc * NV + v) * NP + s * NF + q];
+          for (int v = 0; v < NV; ++v) acc[v] += wgt * buf[(lc * NV + v) * NP + s * NF + q];
         }
     }
     __syncthreads();
@@ -245,7 +266,8 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   T Jl[DIM][DIM];
   T po[DIM];  // the other side's value at this node's faces
   T scale = T(0), pv = T(0);
-  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch);
+  int nmax = 0;
+  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch, &nmax);
   if (active) {
     pv = p[idx];
     sp[lc * NC + i] = pv;
@@ -297,8 +319,8 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   }
   // coarse sides: jump at each fine point from the fine value and the cell's own polynomial
   const int64_t total = (int64_t)mv.nf * NF;
-  coarse_pass<DIM, DEG, T, DIM>(mv, active, c, lc, i, id, bmask, sII + 2 * N * N, T(1), sJ, facc,
-                                [&](int f, int lf, int s, int q, int j) {
+  coarse_pass<DIM, DEG, T, DIM>(mv, active, c, lc, i, id, bmask, nmax, sII + 2 * N * N, T(1), sJ, facc,
+                                [&](int f, int lf, int s, int q, int j, T* buf) {
                                   const int64_t t = (int64_t)(f + s) * NF + q;
                                   const T pm = p[mv.fnode_m[t]];
                                   T pp;
@@ -306,7 +328,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
                                   const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
 #pragma unroll
                                   for (int b = 0; b < DIM; ++b)
-                                    sJ[(lc * DIM + b) * NP + j] = jmp * mv.fn[(int64_t)b * total + t];
+                                    buf[(lc * DIM + b) * NP + j] = jmp * mv.fn[(int64_t)b * total + t];
                                 });
   if (active) {
     const T iwend = mv.tab[S::T_IWEND];
@@ -346,7 +368,8 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   T fv[DIM];
   T ij = T(0), pv = T(0);
   T Jl[DIM][DIM];
-  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch);
+  int nmax = 0;
+  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch, &nmax);
   if (active) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fv[b] = fld[(int64_t)b * Nn + idx];
@@ -416,8 +439,8 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   }
   // coarse sides: |N| {f}.n at each fine point from the fine value and the cell's own polynomial
   const int64_t total = (int64_t)mv.nf * NF;
-  coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, bmask, sII + 2 * N * N, T(-1), sJ, &facc,
-                              [&](int f, int lf, int s, int q, int j) {
+  coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, bmask, nmax, sII + 2 * N * N, T(-1), sJ, &facc,
+                              [&](int f, int lf, int s, int q, int j, T* buf) {
                                 const int64_t t = (int64_t)(f + s) * NF + q;
                                 const int64_t im = mv.fnode_m[t];
                                 T fc[DIM];
@@ -426,7 +449,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
 #pragma unroll
                                 for (int b = 0; b < DIM; ++b)
                                   sum += (fld[(int64_t)b * Nn + im] + fc[b]) * mv.fn[(int64_t)b * total + t];
-                                sJ[lc * NP + j] = T(0.5) * mv.fsj[t] * sum;
+                                buf[lc * NP + j] = T(0.5) * mv.fsj[t] * sum;
                               });
   if (active) {
     const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
@@ -524,7 +547,7 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_onepass_ker
   __shared__ T sF[V][CPB * NC];  // contravariant flux along one axis
   __shared__ T sz[CPB * NC];     // heights above the computational ones
   __shared__ T szabs[CPB * NC];  // absolute heights (coarse pass)
-  __shared__ T sJ[CPB * V * NP]; // coarse-pass fluxes
+  __shared__ T sJ[coarse_buffer<DIM, DEG, V>()];  // coarse-pass fluxes
   __shared__ T sD[N * N], sDw[N * N], sII[4 * N * N], sxi[N];
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
     sD[q] = mv.tab[S::T_D + q];
@@ -541,7 +564,8 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_onepass_ker
   int id[3] = {i % N, (i / N) % N, i / (N * N)};
   int links[DIM];
   T u[V], zd = T(0);
-  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch);
+  int nmax = 0;
+  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch, &nmax);
   if (active) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -636,8 +660,8 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_onepass_ker
     __syncthreads();
   }
   const int64_t total = (int64_t)mv.nf * NF;
-  coarse_pass<DIM, DEG, T, V>(mv, active, c, lc, i, id, bmask, sII + 2 * N * N, T(1), sJ, facc,
-                              [&](int f, int lf, int s, int q, int j) {
+  coarse_pass<DIM, DEG, T, V>(mv, active, c, lc, i, id, bmask, nmax, sII + 2 * N * N, T(1), sJ, facc,
+                              [&](int f, int lf, int s, int q, int j, T* buf) {
                                 const int64_t t = (int64_t)(f + s) * NF + q;
                                 const int64_t im = mv.fnode_m[t];
                                 T uf[V], uc[V], zq, rq, pq, n[DIM];
@@ -655,7 +679,7 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_onepass_ker
                                 const T sj = mv.fsj[t];
 #pragma unroll
                                 for (int v = 0; v < V; ++v)
-                                  sJ[(lc * V + v) * NP + j] =
+                                  buf[(lc * V + v) * NP + j] =
                                       sj * (T(0.5) * (Ff[v] + Fc[v]) - T(0.5) * lam * (uc[v] - uf[v]));
                               });
   // volume term, one axis at a time through shared memory

@@ -300,7 +300,7 @@ def precision_forms_3d(dg, torch, case_name="hill3d", steps=2, inner_tol=1e-6):
         dg.imex_rk2_step(ctx, mesh, st, case.dt, o)
         one_step[name] = st.download()
         out[name] = {"ms_per_step": ms, "dof_steps_per_s": mesh.n_dof / (ms / 1e3),
-                     "solver": mesh.autotuned()[name[:4]]["form"]}
+                     "solver": mesh.autotuned()[name[:4]]["form"], "helmholtz_kappa": spectrum_of(st)}
     dev = max(np.linalg.norm(res["fp32_refined"][v] - res["fp64"][v])
               / max(np.linalg.norm(res["fp64"][v] - bg[v]), 1e-300) for v in range(mesh.n_vars))
     out["fp32_refined"]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32_refined"]["ms_per_step"]
@@ -311,6 +311,56 @@ def precision_forms_3d(dg, torch, case_name="hill3d", steps=2, inner_tol=1e-6):
     mesh.close()
     ctx.close()
     out["_one_step"] = one_step
+    return out
+
+
+def spectrum_of(state):
+    """Condition number of the state's last Helmholtz operator: the power-iteration upper bound the
+    Chebyshev solves keep (less its 5% margin) over the lower bound 1/(gamma-1) = 2.5 (0 if the
+    state has not run a Chebyshev solve)."""
+    lmax, _ = state.chebyshev_bound()
+    return lmax / 1.05 / 2.5 if lmax > 0 else 0.0
+
+
+def paper_pair(dg, torch, steps=3):
+    """Sec. 3.1/3.2's comparison: the bell-shaped hill on the uniform 60x40x16 mesh and on the
+    non-conforming mesh of the same finest resolution, FP64 IMEX-RK2 steps of dt = 2 s (autotuned
+    Helmholtz solver), timed with CUDA events after one warm-up step; the wall clock of T_f = 1 h
+    (1800 steps) extrapolated from the step time, beside the paper's figures (context only)."""
+    from workloads import make_case
+
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name in ("bell3d_nc", "bell3d_uniform"):
+        case = make_case(name, 0)
+        ctx = dg.Context(torch.cuda.current_device())
+        mesh = dg.Mesh(ctx, case)
+        o = dg.solver_opts(tol=1e-12)
+        st = dg.State(ctx, mesh, o)
+        kind, params = dg.api.init_params(case)
+        dg.dg_init_state(ctx, mesh, kind, params, st.U)
+        dg.imex_rk2_step(ctx, mesh, st, case.dt, o)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = 0
+        for _ in range(steps):
+            its += dg.imex_rk2_step(ctx, mesh, st, case.dt, o)["gmres_iters"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"cells": mesh.n_cells, "dof": mesh.n_dof, "ms_per_step": ms,
+                     "dof_steps_per_s": mesh.n_dof / (ms / 1e3), "iters_per_step": its / steps,
+                     "wall_clock_1h_s": 1800 * ms / 1e3, "solver": mesh.autotuned()["fp64"]["form"],
+                     "helmholtz_kappa": spectrum_of(st)}
+        st.close()
+        mesh.close()
+        ctx.close()
+    nc, un = out["bell3d_nc"], out["bell3d_uniform"]
+    out["saving_vs_uniform"] = 1.0 - nc["ms_per_step"] / un["ms_per_step"]
+    out["paper"] = ("Sec. 3.2, context only: 2560 s (1958-cell non-conforming mesh) vs 36500 s (uniform "
+                    "60x40x16) wall clock, a ~93% saving, on MeluXina CPU nodes (core count not stated)")
     return out
 
 
@@ -444,12 +494,17 @@ def ensemble_bench(dg, torch, n_members=64, steps=10, inner_tol=1e-6):
     gms = g0.elapsed_time(g1)
     kernels_per_step = (dg.dg_launch_count(ctx) - n0) / steps
     plan.close()
+    kap = {}
+    for c, st in zip(cases, states):
+        kap.setdefault("r%d" % c.degree, []).append(spectrum_of(st))
+    kappa_by_degree = {k: {"min": min(v), "max": max(v), "members": len(v)} for k, v in sorted(kap.items())}
     dof = sum(m.n_dof for m in meshes)
     out = {"workload": "%d 2D members (base 16x8..128x64, 0-2 levels, degree 2-5), %d DoF in all, "
                        "FP32 Krylov + FP64 residual, one CUDA-graph replay per ensemble step" % (n_members, dof),
            "member_steps_per_s": n_members * steps / (gms / 1e3), "dof_steps_per_s": dof * steps / (gms / 1e3),
            "ms_per_ensemble_step": gms / steps, "gmres_iters_per_member_step": giters / (n_members * steps),
            "graph_capture_ms": capture_ms, "kernels_per_ensemble_step": kernels_per_step,
+           "helmholtz_kappa_by_degree": kappa_by_degree,
            "without_graph": {"ms_per_ensemble_step": ms / steps,
                              "member_steps_per_s": n_members * steps / (ms / 1e3),
                              "gmres_iters_per_member_step": iters / (n_members * steps)}}
@@ -482,6 +537,10 @@ def serving_bench(dg, torch, n_requests=24, rate=20.0, dof_hi=5e6, steps_lo=10, 
         sv.wait(rid, 900)
     infos = [sv.poll(rid) for rid, _, _ in ids]
     ok = [i for i in infos if i["state"] == "done"]
+    from paper_2408_08129_gb300._binding import DG_STATUS
+    failed = [{"status": DG_STATUS.get(i["status"], i["status"]), "dim": c.dim, "degree": c.degree, "dof": c.n_dof,
+               "steps": s, "precision": p, "steps_done": i["steps_done"], "init": c.init["kind"]}
+              for i, (_, c, s), (_, _, _, p) in zip(infos, ids, trace) if i["state"] != "done"]
     lat = sorted(i["t_finish"] - i["t_submit"] for i in ok)
     t_first = min(i["t_submit"] for i in infos)
     t_last = max(i["t_finish"] for i in infos)
@@ -500,7 +559,7 @@ def serving_bench(dg, torch, n_requests=24, rate=20.0, dof_hi=5e6, steps_lo=10, 
                         "the full ranges of DoF and steps, fewer requests to keep the bench within minutes)"
                         % (n_requests, rate, dof_hi, steps_lo, steps_hi, budget / 1e9, n_requests),
             "dof_steps_total": dof_steps,
-            "completed": len(ok), "p50_s": pct(0.5), "p99_s": pct(0.99), "makespan_s": span,
+            "completed": len(ok), "failed": failed, "p50_s": pct(0.5), "p99_s": pct(0.99), "makespan_s": span,
             "member_steps_per_s": steps_total / span, "dof_steps_per_s": dof_steps / span,
             "ticks": stats["ticks"]}
 
@@ -620,6 +679,7 @@ def main():
     value = whole_job_value(world, dof, args.steps, total_ms)
 
     U64 = state.download()
+    kappa = spectrum_of(state)
 
     Ubg = torch.empty(mesh.shape(), dtype=torch.float64, device="cuda")
     dg.dg_background(ctx, mesh, Ubg)
@@ -769,6 +829,7 @@ def main():
         "gmres_phase_us_per_iteration": {k: 1e3 * v / max(1, phases["iterations"]) for k, v in phases.items()
                                          if k not in ("iterations", "second_passes")},
         "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in stats),
+        "helmholtz_kappa": kappa,
         "autotuned_solver": tuned,
         "fp32_refined": fp32,
         "other_krylov_forms": cg,
@@ -779,6 +840,7 @@ def main():
     if rank == 0 and not args.no_sweep:
         line["applies"] = apply_sweep(dg, torch, args.sweep_workload)
         forms3d = precision_forms_3d(dg, torch, inner_tol=args.inner_tol)
+        line["paper_pair"] = paper_pair(dg, torch)
     if rank == 0 and not args.no_ensemble:
         line["ensemble"] = ensemble_bench(dg, torch, inner_tol=args.inner_tol)
         line["serving"] = serving_bench(dg, torch, inner_tol=args.inner_tol)

@@ -181,6 +181,14 @@ typedef struct {
   double sponge_depth;    /* (m), 0..H                                          */
   double sponge_rate;     /* tau at the top (1/s), >= 0                         */
   double sponge_u0;       /* reference x-velocity (m/s)                         */
+  /* Lateral absorbing layers (the lateral boundaries of the paper's runs are
+   * non-reflecting too; this is the same reading as the top layer): within
+   * sponge_lateral_width metres of a lateral domain boundary (x = 0, x = Lx,
+   * and in 3D y = 0, y = Ly), tau_lat = sponge_lateral_rate sin^2(pi/2 (w - d)/w),
+   * d the distance to the nearest of them, w the width; a node is damped at
+   * max(tau_top, tau_lat) towards the same U_ref.  Width 0 turns it off. */
+  double sponge_lateral_width; /* (m), 0 .. half the smallest lateral extent    */
+  double sponge_lateral_rate;  /* tau at the lateral boundaries (1/s), >= 0     */
   /* Optional caller-built geometry and topology (for meshes generated
    * elsewhere, as the paper's are).  Each may be NULL / 0: then it is built
    * from the tree and the terrain map above.  Host arrays, read during the

@@ -50,22 +50,40 @@ class DG:
 
     # ------------------------------------------------------------------ damping layer
     def _sponge(self, sp, z):
-        """Rayleigh damping layer below the top boundary.
+        """Rayleigh damping layers below the top boundary and along the lateral boundaries.
 
-        The paper's runs use non-reflecting boundaries whose method it defers
-        to earlier work; this reading relaxes the state towards a reference
-        state in the top ``depth`` metres of physical height, with the rate
-        rising as sin^2 from 0 at z_d = H - depth to ``rate`` at the top
-        (the usual profile of upper absorbing layers).  The reference state is
-        the hydrostatic background carrying the uniform x-velocity ``u0``.
+        The paper's runs use non-reflecting top and lateral boundaries whose
+        method it defers to earlier work; this reading relaxes the state towards
+        a reference state in the top ``depth`` metres of physical height, with
+        the rate rising as sin^2 from 0 at z_d = H - depth to ``rate`` at the top
+        (the usual profile of upper absorbing layers), and likewise within
+        ``lateral_width`` metres of the lateral domain boundaries (distance to
+        the nearest one, rising to ``lateral_rate`` at the boundary); where both
+        act, the larger rate applies.  The reference state is the hydrostatic
+        background carrying the uniform x-velocity ``u0``.
         """
         self.tau = None
-        if not sp or not (sp.get("depth", 0.0) > 0.0) or not (sp.get("rate", 0.0) > 0.0):
+        sp = sp or {}
+        top = sp.get("depth", 0.0) > 0.0 and sp.get("rate", 0.0) > 0.0
+        lat = sp.get("lateral_width", 0.0) > 0.0 and sp.get("lateral_rate", 0.0) > 0.0
+        if not (top or lat):
             return
-        depth, rate, u0 = sp["depth"], sp["rate"], sp.get("u0", 0.0)
-        top = self.case.extent[self.d - 1]
-        frac = np.clip((z - (top - depth)) / depth, 0.0, 1.0)
-        self.tau = rate * np.sin(0.5 * np.pi * frac) ** 2
+        tau = np.zeros_like(z)
+        if top:
+            depth, rate = sp["depth"], sp["rate"]
+            H = self.case.extent[self.d - 1]
+            frac = np.clip((z - (H - depth)) / depth, 0.0, 1.0)
+            tau = rate * np.sin(0.5 * np.pi * frac) ** 2
+        if lat:
+            w, rate_l = sp["lateral_width"], sp["lateral_rate"]
+            X = self.mesh.X
+            dist = np.full_like(z, np.inf)
+            for a in range(self.d - 1):
+                dist = np.minimum(dist, np.minimum(X[a], self.case.extent[a] - X[a]))
+            frac = np.clip((w - np.maximum(dist, 0.0)) / w, 0.0, 1.0)
+            tau = np.maximum(tau, rate_l * np.sin(0.5 * np.pi * frac) ** 2)
+        self.tau = tau
+        u0 = sp.get("u0", 0.0)
         self.Uref = self.Ubg.copy()
         self.Uref[1] = self.rhobar * u0
         self.Uref[self.V - 1] = self.pbar / (ph.GAMMA - 1.0) + 0.5 * self.rhobar * u0 * u0

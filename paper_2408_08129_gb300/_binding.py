@@ -36,6 +36,7 @@ class MeshDesc(ctypes.Structure):
         ("atm_kind", c_int), ("atm_T", c_double), ("atm_N", c_double), ("atm_p_ref", c_double),
         ("gravity", c_double),
         ("sponge_depth", c_double), ("sponge_rate", c_double), ("sponge_u0", c_double),
+        ("sponge_lateral_width", c_double), ("sponge_lateral_rate", c_double),
         ("node_xyz", ctypes.POINTER(c_double)),
         ("n_conforming", c_int64), ("conforming", ctypes.POINTER(ctypes.c_int32)),
         ("n_subfaces", c_int64), ("subfaces", ctypes.POINTER(ctypes.c_int32)),

@@ -96,6 +96,8 @@ def mesh_desc(case, gravity=None, node_xyz=None, faces=None):
     d.sponge_depth = sp.get("depth", 0.0)
     d.sponge_rate = sp.get("rate", 0.0)
     d.sponge_u0 = sp.get("u0", 0.0)
+    d.sponge_lateral_width = sp.get("lateral_width", 0.0)
+    d.sponge_lateral_rate = sp.get("lateral_rate", 0.0)
     keep = [level, ijk]
     if node_xyz is not None:
         X = np.ascontiguousarray(node_xyz, dtype=np.float64)

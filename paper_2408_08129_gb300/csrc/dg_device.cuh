@@ -68,6 +68,54 @@ __device__ __forceinline__ double rsqrt64(double x) {
   return y;
 }
 
+// Metric terms of node id of a cell whose x (and y) are affine, from the
+// heights above the computational coordinates in shared memory (sz: the
+// cell's NC values) and the cell's half widths (hb * 2^-level per axis):
+//   2D: Ja = [[z_z, 0], [-z_x, ax]],  J = ax z_z
+//   3D: Ja = [[ay z_z, 0, 0], [0, ax z_z, 0], [-ay z_x, -ax z_y, ax ay]],  J = ax ay z_z
+// with z_a = d z / d xi^a (the vertical one includes the computational half
+// width).  These equal the cofactors of the nodal-derivative Jacobian that the
+// stored metric terms hold.
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void metric_from_z(const MeshView<T>& mv, int64_t c, const T* sz, const int* id,
+                                              const T* sD, T (&Ja)[DIM][DIM], T& invJ) {
+  constexpr int N = DEG + 1;
+  const T scale = T(1) / T(1 << mv.cell_level[c]);
+  T zd[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+    const int node = id[0] + N * id[1] + (DIM == 3 ? N * N * id[2] : 0);
+    const T* zc = sz + node - id[a] * stride;
+    const T* D = sD + id[a] * N;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < N; ++k) s += D[k] * zc[k * stride];
+    zd[a] = s;
+  }
+  zd[DIM - 1] += mv.hb[DIM - 1] * scale;
+  const T ax = mv.hb[0] * scale;
+  if (DIM == 2) {
+    Ja[0][0] = zd[1];
+    Ja[0][1] = T(0);
+    Ja[1][0] = -zd[0];
+    Ja[1][1] = ax;
+    invJ = T(1) / (ax * zd[1]);
+  } else {
+    const T ay = mv.hb[1] * scale;
+    Ja[0][0] = ay * zd[DIM - 1];
+    Ja[0][1] = T(0);
+    Ja[0][DIM - 1] = T(0);
+    Ja[1][0] = T(0);
+    Ja[1][1] = ax * zd[DIM - 1];
+    Ja[1][DIM - 1] = T(0);
+    Ja[DIM - 1][0] = -ay * zd[0];
+    Ja[DIM - 1][1] = -ax * zd[1];
+    Ja[DIM - 1][DIM - 1] = ax * ay;
+    invJ = T(1) / (ax * ay * zd[DIM - 1]);
+  }
+}
+
 // Hydrostatic background (rho_bar, p_bar) at height z from the mesh's cubic
 // Hermite table (heights outside the table clamp to its ends)
 template <typename T>

@@ -532,19 +532,35 @@ int build_mesh(dg_mesh* m) {
       if (f < m->nconf) fnode_p[(size_t)f * NF + k] = face_p[f] * nc + host_face_node(dim, n, face_lfp[f], k);
     }
 
-  // Rayleigh damping rate per node: sin^2 profile over the top sponge_depth of physical height
+  // Rayleigh damping rate per node: sin^2 profile over the top sponge_depth of physical height,
+  // and over sponge_lateral_width from the lateral boundaries; the larger of the two
   std::vector<double> tau;
-  if (d.sponge_depth > 0.0 && d.sponge_rate > 0.0) {
+  const bool top_layer = d.sponge_depth > 0.0 && d.sponge_rate > 0.0;
+  const bool lat_layer = d.sponge_lateral_width > 0.0 && d.sponge_lateral_rate > 0.0;
+  if (top_layer || lat_layer) {
     const double H = d.extent[dim - 1], zd = H - d.sponge_depth;
     const double half_pi = 0.5 * 3.14159265358979323846;
     tau.assign(m->Nn, 0.0);
     for (int64_t i = 0; i < m->Nn; ++i) {
       const int64_t c = i / nc, q = i % nc;
+      double t = 0.0;
       const double z = m->X[((size_t)(dim - 1) * K + c) * nc + q];
-      if (z > zd) {
-        const double s = std::sin(half_pi * std::min(1.0, (z - zd) / d.sponge_depth));
-        tau[i] = d.sponge_rate * s * s;
+      if (top_layer && z > zd) {
+        const double sv = std::sin(half_pi * std::min(1.0, (z - zd) / d.sponge_depth));
+        t = d.sponge_rate * sv * sv;
       }
+      if (lat_layer) {
+        double dist = 1e300;
+        for (int a = 0; a < dim - 1; ++a) {
+          const double x = m->X[((size_t)a * K + c) * nc + q];
+          dist = std::min(dist, std::min(x, d.extent[a] - x));
+        }
+        if (dist < d.sponge_lateral_width) {
+          const double sv = std::sin(half_pi * (d.sponge_lateral_width - std::max(dist, 0.0)) / d.sponge_lateral_width);
+          t = std::max(t, d.sponge_lateral_rate * sv * sv);
+        }
+      }
+      tau[i] = t;
     }
   }
 
@@ -715,6 +731,10 @@ extern "C" int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* desc, dg_mesh** o
   if (!(desc->sponge_depth >= 0.0) || !(desc->sponge_rate >= 0.0) ||
       desc->sponge_depth > desc->extent[desc->dim - 1] || !std::isfinite(desc->sponge_u0))
     return fail(DG_EINVAL, "bad sponge layer parameters");
+  for (int a = 0; a < desc->dim - 1; ++a)
+    if (!(desc->sponge_lateral_width >= 0.0) || desc->sponge_lateral_width > 0.5 * desc->extent[a] ||
+        !(desc->sponge_lateral_rate >= 0.0))
+      return fail(DG_EINVAL, "bad lateral sponge layer parameters");
   dg_mesh* m = new (std::nothrow) dg_mesh();
   if (!m) return fail(DG_ENOMEM, "host allocation failed");
   m->ctx = ctx;

@@ -62,54 +62,6 @@ __device__ __forceinline__ T coarse_weight(const T* sIt, int s, int kt, int q) {
   return sIt[(s & 1) * N * N + (kt % N) * N + (q % N)] * sIt[((s >> 1) & 1) * N * N + (kt / N) * N + (q / N)];
 }
 
-// Metric terms of node id of a cell whose x (and y) are affine, from the
-// heights above the computational coordinates in shared memory (sz: the
-// cell's NC values) and the cell's half widths (hb * 2^-level per axis):
-//   2D: Ja = [[z_z, 0], [-z_x, ax]],  J = ax z_z
-//   3D: Ja = [[ay z_z, 0, 0], [0, ax z_z, 0], [-ay z_x, -ax z_y, ax ay]],  J = ax ay z_z
-// with z_a = d z / d xi^a (the vertical one includes the computational half
-// width).  These equal the cofactors of the nodal-derivative Jacobian that the
-// stored metric terms hold.
-template <int DIM, int DEG, typename T>
-__device__ __forceinline__ void metric_from_z(const MeshView<T>& mv, int64_t c, const T* sz, const int* id,
-                                              const T* sD, T (&Ja)[DIM][DIM], T& invJ) {
-  constexpr int N = DEG + 1;
-  const T scale = T(1) / T(1 << mv.cell_level[c]);
-  T zd[DIM];
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
-    const int node = id[0] + N * id[1] + (DIM == 3 ? N * N * id[2] : 0);
-    const T* zc = sz + node - id[a] * stride;
-    const T* D = sD + id[a] * N;
-    T s = T(0);
-#pragma unroll
-    for (int k = 0; k < N; ++k) s += D[k] * zc[k * stride];
-    zd[a] = s;
-  }
-  zd[DIM - 1] += mv.hb[DIM - 1] * scale;
-  const T ax = mv.hb[0] * scale;
-  if (DIM == 2) {
-    Ja[0][0] = zd[1];
-    Ja[0][1] = T(0);
-    Ja[1][0] = -zd[0];
-    Ja[1][1] = ax;
-    invJ = T(1) / (ax * zd[1]);
-  } else {
-    const T ay = mv.hb[1] * scale;
-    Ja[0][0] = ay * zd[DIM - 1];
-    Ja[0][1] = T(0);
-    Ja[0][DIM - 1] = T(0);
-    Ja[1][0] = T(0);
-    Ja[1][1] = ax * zd[DIM - 1];
-    Ja[1][DIM - 1] = T(0);
-    Ja[DIM - 1][0] = -ay * zd[0];
-    Ja[DIM - 1][1] = -ax * zd[1];
-    Ja[DIM - 1][DIM - 1] = ax * ay;
-    invJ = T(1) / (ax * ay * zd[DIM - 1]);
-  }
-}
-
 // ---------------------------------------------------------------- gradient
 //
 // Face terms are computed by the cells themselves (no face pass, no face
@@ -520,201 +472,6 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(Mesh
   StoreOut<T> epi{out};
   div_cell_batch<DIM, DEG, T, HELM, StoreOut<T>, GZ>(mv, f, p, alpha, T(1), T(1), epi, blockIdx.x, sF, sJ, sDw,
                                                      sII, sz, sD);
-}
-
-// ---------------------------------------------------------------- explicit operator, one-pass FP32 form
-//
-// The explicit operator (Eq. (1), Sec. 2; the same weak form as the two-pass
-// kernels of k_explicit.cuh) for FP32 perturbation states on meshes affine in
-// x and y, in one pass over the cells: every cell evaluates the Rusanov flux
-// at its own face nodes against the neighbour's trace (both sides of a face
-// evaluate the same flux, each with its own outward normal), the metric terms
-// from the nodal heights and the background from the height table, so that
-// per node the kernel reads the state and one height and writes the tendency.
-// The coarse side of a 2:1 face evaluates the fluxes at the fine points of
-// its subfaces cooperatively (with the fine side's normal) and takes them
-// through the weighted transposed interpolation.
-template <int DIM, int DEG, bool FULL>
-__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_onepass_kernel(MeshView<float> mv,
-                                                                                  const float* __restrict__ U,
-                                                                                  float* __restrict__ R,
-                                                                                  const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  using T = float;
-  using S = Shape<DIM, DEG>;
-  constexpr int N = S::N, NC = S::NC, V = S::V, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
-  __shared__ T sU[V][CPB * NC];  // the batch's state (coarse traces)
-  __shared__ T sF[V][CPB * NC];  // contravariant flux along one axis
-  __shared__ T sz[CPB * NC];     // heights above the computational ones
-  __shared__ T szabs[CPB * NC];  // absolute heights (coarse pass)
-  __shared__ T sJ[coarse_buffer<DIM, DEG, V>()];  // coarse-pass fluxes
-  __shared__ T sD[N * N], sDw[N * N], sII[4 * N * N], sxi[N];
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
-    sD[q] = mv.tab[S::T_D + q];
-    sDw[q] = mv.tab[S::T_DW + q];
-  }
-  for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
-  for (int q = threadIdx.x; q < N; q += blockDim.x) sxi[q] = mv.tab[S::T_XI + q];
-  const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int64_t batch = blockIdx.x;
-  const int64_t c = batch * CPB + lc;
-  const bool active = (lc < CPB) && (c < mv.n_cells);
-  const int64_t Nn = mv.n_nodes;
-  const int64_t idx = c * NC + i;
-  int id[3] = {i % N, (i / N) % N, i / (N * N)};
-  int links[DIM];
-  T u[V], zd = T(0);
-  int nmax = 0;
-  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch, &nmax);
-  if (active) {
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      u[v] = U[(int64_t)v * Nn + idx];
-      sU[v][lc * NC + i] = u[v];
-    }
-    zd = mv.zdev[idx];
-    sz[lc * NC + i] = zd;
-    load_face_links<DIM, DEG, T>(mv, c, id, links);
-  }
-  __syncthreads();
-  T Jl[DIM][DIM], ij = T(0), rb = T(0), pb = T(0), zabs = T(0);
-  T F[V][DIM], src[V], facc[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) facc[v] = src[v] = T(0);
-  if (active) {
-    metric_from_z<DIM, DEG, T>(mv, c, sz + lc * NC, id, sD, Jl, ij);
-    const T hz = mv.hb[DIM - 1] / T(1 << mv.cell_level[c]);
-    zabs = mv.cell_zeta0[c] + hz * (sxi[id[DIM - 1]] + T(1)) + zd;
-    background_at<T>(mv, zabs, rb, pb);
-    // pointwise flux tensor and gravity source of the perturbation state (as explicit_cell_kernel)
-    const T rho = rb + u[0];
-    const T irho = T(1) / rho;
-    T m2 = T(0);
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) m2 += u[1 + b] * u[1 + b];
-    const T pp = gm1<T>() * (u[V - 1] - T(0.5) * m2 * irho);
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) {
-      const T ub = u[1 + b] * irho;
-      F[0][b] = u[1 + b];
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) F[1 + a][b] = u[1 + a] * ub;
-      if (FULL) {
-        F[1 + b][b] += pp;
-        F[V - 1][b] = (u[V - 1] + pp + pb * (T(1.4) / gm1<T>())) * ub;
-      } else {
-        F[V - 1][b] = T(0.5) * m2 * irho * irho * u[1 + b];
-      }
-    }
-    if (FULL) src[DIM] = -u[0] * mv.gravity;
-    src[V - 1] = -mv.gravity * u[DIM];
-    // own face nodes: -|N| F*(u, u_other; n) with the outward normal +-Ja[a]
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      const int kind = links[a] & 3;
-      if (id[a] != 0 && id[a] != DEG) continue;  // interior along this axis
-      if (kind == 2) continue;                   // coarse side: coarse pass below
-      const T sg = half_sign<DIM, DEG, T>(a, id) * T(2);
-      T n[DIM], n2 = T(0);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        n[b] = sg * Jl[a][b];
-        n2 += n[b] * n[b];
-      }
-      const T sj = sqrtf(n2), isj = T(1) / sj;
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) n[b] *= isj;
-      T out[V];
-      if (kind == 3) {
-        // slip wall: Rusanov flux against the mirror state, in closed form
-        T mn = T(0);
-#pragma unroll
-        for (int b = 0; b < DIM; ++b) mn += u[1 + b] * n[b];
-        const T un = mn * irho;
-        T lam = fabsf(un);
-        if (FULL) lam += sqrtf(T(1.4) * (pb + pp) * irho);
-        const T mom = mn * un + (FULL ? pp : T(0)) + lam * mn;
-        out[0] = T(0);
-#pragma unroll
-        for (int b = 0; b < DIM; ++b) out[1 + b] = mom * n[b];
-        out[V - 1] = T(0);
-      } else {
-        T uo[V];
-        other_trace<DIM, DEG, T, V>(U, Nn, links[a], a, id, sII, uo);
-        T Fo[V], Fn[V], lo, lw;
-        normal_flux<DIM, T, FULL>(u, rb, pb, n, Fn, lw);
-        normal_flux<DIM, T, FULL>(uo, rb, pb, n, Fo, lo);
-        const T lam = lw > lo ? lw : lo;
-#pragma unroll
-        for (int v = 0; v < V; ++v) out[v] = T(0.5) * (Fn[v] + Fo[v]) - T(0.5) * lam * (uo[v] - u[v]);
-      }
-#pragma unroll
-      for (int v = 0; v < V; ++v) facc[v] -= sj * out[v];
-    }
-  }
-  // coarse sides of 2:1 faces: the flux at every fine point of the subfaces, from the fine
-  // node's state and this cell's polynomial there, with the fine side's normal; this cell is
-  // the plus side and takes +|N| F* through It
-  if (bmask != 0u) {
-    if (active) szabs[lc * NC + i] = zabs;  // absolute heights for the fine points' background
-    __syncthreads();
-  }
-  const int64_t total = (int64_t)mv.nf * NF;
-  coarse_pass<DIM, DEG, T, V>(mv, active, c, lc, i, id, bmask, nmax, sII + 2 * N * N, T(1), sJ, facc,
-                              [&](int f, int lf, int s, int q, int j, T* buf) {
-                                const int64_t t = (int64_t)(f + s) * NF + q;
-                                const int64_t im = mv.fnode_m[t];
-                                T uf[V], uc[V], zq, rq, pq, n[DIM];
-#pragma unroll
-                                for (int v = 0; v < V; ++v) uf[v] = U[(int64_t)v * Nn + im];
-                                coarse_interp<DIM, DEG, T, V>(&sU[0][0], CPB * NC, lc * NC, lf, s, q, sII, uc);
-                                coarse_interp<DIM, DEG, T, 1>(szabs, 0, lc * NC, lf, s, q, sII, &zq);
-                                background_at<T>(mv, zq, rq, pq);
-#pragma unroll
-                                for (int b = 0; b < DIM; ++b) n[b] = mv.fn[(int64_t)b * total + t];
-                                T Ff[V], Fc[V], lf_, lc_;
-                                normal_flux<DIM, T, FULL>(uf, rq, pq, n, Ff, lf_);
-                                normal_flux<DIM, T, FULL>(uc, rq, pq, n, Fc, lc_);
-                                const T lam = lf_ > lc_ ? lf_ : lc_;
-                                const T sj = mv.fsj[t];
-#pragma unroll
-                                for (int v = 0; v < V; ++v)
-                                  buf[(lc * V + v) * NP + j] =
-                                      sj * (T(0.5) * (Ff[v] + Fc[v]) - T(0.5) * lam * (uc[v] - uf[v]));
-                              });
-  // volume term, one axis at a time through shared memory
-  T acc[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) acc[v] = T(0);
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    if (active) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        T ft = T(0);
-#pragma unroll
-        for (int b = 0; b < DIM; ++b) ft += Jl[a][b] * F[v][b];
-        sF[v][lc * NC + i] = ft;
-      }
-    }
-    __syncthreads();
-    if (active) {
-      const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
-      const int i0 = lc * NC + i - id[a] * stride;
-      const T* Dw = sDw + id[a] * N;
-#pragma unroll
-      for (int kk = 0; kk < N; ++kk) {
-        const T dw = Dw[kk];
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] += dw * sF[v][i0 + kk * stride];
-      }
-    }
-    __syncthreads();
-  }
-  if (!active) return;
-  const T iwend = mv.tab[S::T_IWEND];
-#pragma unroll
-  for (int v = 0; v < V; ++v) R[(int64_t)v * Nn + idx] = (acc[v] + facc[v] * iwend) * ij + src[v];
 }
 
 }  // namespace dg

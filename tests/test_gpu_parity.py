@@ -378,10 +378,12 @@ def test_chebyshev_bound_estimate_and_repair(dg, ctx):
 @pytest.mark.parametrize("name,nsteps,sponge", [
     ("bubble2d", 10, dict(depth=4e3, rate=0.2, u0=0.0)),
     ("hill2d", 2, dict(depth=8e3, rate=0.5, u0=10.0)),
+    ("hill2d", 2, dict(depth=8e3, rate=0.5, u0=10.0, lateral_width=6e3, lateral_rate=0.3)),
     ("hill3d", 1, dict(depth=5e3, rate=0.3, u0=10.0)),
 ])
 def test_imex_steps_with_damping_layer(dg, ctx, name, nsteps, sponge):
-    """Rayleigh damping layer below the top: the GPU step matches the oracle's."""
+    """Rayleigh damping layers below the top (and along the lateral boundaries): the GPU step
+    matches the oracle's."""
     import dataclasses
 
     case = dataclasses.replace(make_case(name, 0), sponge=sponge)
@@ -392,11 +394,21 @@ def test_imex_steps_with_damping_layer(dg, ctx, name, nsteps, sponge):
     assert _per_var_rel(U - ref.Ubg, Ur - ref.Ubg) < 1e-9
 
 
+def test_bell_hill_nonconforming_step_matches_oracle(dg, ctx):
+    """Sec. 3.1's bell-shaped hill on the non-conforming mesh (1972 cells, degree 4, two 2:1 levels,
+    top and lateral absorbing layers, dt = 2 s): one FP64 step against the oracle."""
+    case = make_case("bell3d_nc", 0)
+    U, Ur, ref = _run_steps(dg, ctx, case, 1, dg.solver_opts(tol=1e-12))
+    assert ref.tau is not None and ref.tau.max() > 0
+    assert _per_var_rel(U - ref.Ubg, Ur - ref.Ubg) < 1e-10
+
+
 def test_damping_layer_parameters_validated(dg, ctx):
     import dataclasses
 
     case = make_case("bubble2d", 0)
-    for bad in (dict(depth=2e4, rate=0.1), dict(depth=1e3, rate=-1.0)):
+    for bad in (dict(depth=2e4, rate=0.1), dict(depth=1e3, rate=-1.0), dict(lateral_width=2e4, lateral_rate=0.1),
+                dict(lateral_width=1e3, lateral_rate=-0.1)):
         with pytest.raises(dg.DGError, match="sponge"):
             dg.Mesh(ctx, dataclasses.replace(case, sponge=bad))
 

@@ -86,3 +86,32 @@ def test_no_layer_no_change():
     assert DG(case).tau is None
     off = dataclasses.replace(case, sponge=dict(depth=0.0, rate=1.0))
     assert DG(off).tau is None
+
+
+def test_lateral_layer_damps_by_distance_to_the_lateral_boundaries():
+    """Lateral layers alone (no top layer), flat ground, g = 0, the background at rest plus a density
+    perturbation: each node's perturbation is multiplied per step by R(-tau dt), tau = the rate on
+    the lateral boundaries, half of it at half the width in from them, and nothing beyond the width
+    (2D: x only; 3D: the nearer of the x and y boundaries)."""
+    for dim in (2, 3):
+        base = (4, 3) if dim == 2 else (4, 4, 2)
+        ext = (4e3, 3e3) if dim == 2 else (4e3, 4e3, 2e3)
+        case = tiny_case(dim, 2, base=base, extent=ext, refine=[], atmosphere=STRAT,
+                         periodic=(True,) * (dim - 1) + (False,))
+        rate, dt, w = 0.05, 2.0, 1e3
+        case = dataclasses.replace(case, sponge=dict(lateral_width=w, lateral_rate=rate))
+        dg = DG(case, gravity=0.0)
+        U0 = dg.Ubg.copy()
+        drho = 1e-3 * dg.rhobar
+        U0[0] += drho
+        U1 = Stepper(dg, tol=1e-13).step(U0, dt)
+        ratio = (U1[0] - dg.rhobar) / drho
+        X = dg.mesh.X
+        dist = np.min([np.minimum(X[a], ext[a] - X[a]) for a in range(dim - 1)], axis=0)
+        edge = np.abs(dist) < 1e-6
+        half = np.abs(dist - 0.5 * w) < 1e-6
+        inner = dist >= w - 1e-6
+        assert edge.any() and half.any() and inner.any()
+        assert np.abs(ratio[edge] - _stability(-rate * dt)).max() < 1e-12
+        assert np.abs(ratio[half] - _stability(-0.5 * rate * dt)).max() < 1e-12
+        assert np.abs(ratio[inner] - 1.0).max() < 1e-12

@@ -346,6 +346,45 @@ def hill3d_big(seed: int = 0, degree: int = 3) -> Case:
     return hill3d(seed, degree, base=(64, 64, 32), name="hill3d_big")
 
 
+def bell3d(seed: int = 0, degree: int = 4, refined: bool = True) -> Case:
+    """Sec. 3.1's 3D medium-steep bell-shaped hill: 60 x 40 x 16 km, h = hc / (1 + r^2/a^2)^(3/2)
+    with hc = 400 m, a = 1 km, crest at (30, 20) km; constant-N atmosphere (N = 0.01 1/s,
+    T_ref = 293.15 K), 10 m/s inflow, degree 4, dt = 2 s.  The paper's non-reflecting top and
+    lateral boundaries are read as absorbing layers (top 6 km; 10 km along the lateral boundaries,
+    which are periodic).
+
+    refined=False: the uniform 60 x 40 x 16 mesh of 1 km cells (250 m effective resolution at
+    degree 4).  refined=True: 15 x 10 x 4 base cells of 4 km, refined to 2 km within 14 km of the
+    crest below 8 km and to 1 km within 9 km of it below 4 km (2:1 balanced), 1972 cells whose
+    finest resolution is the uniform mesh's (the paper's non-conforming mesh has 1958 cells)."""
+    extent = (60e3, 40e3, 16e3)
+    xc, yc = 30e3, 20e3
+    if refined:
+        base = (15, 10, 4)
+
+        def rule(level, centre):
+            r = math.hypot(centre[0] - xc, centre[1] - yc)
+            if level == 0:
+                return r < 14e3 and centre[2] < 8e3
+            if level == 1:
+                return r < 9e3 and centre[2] < 4e3
+            return False
+
+        leaves = build_tree(3, base, extent, (True, True, False), rule, 2)
+    else:
+        base = (60, 40, 16)
+        leaves = build_tree(3, base, extent, (True, True, False), None, 0)
+    case = _finish(
+        "bell3d_nc" if refined else "bell3d_uniform", 3, degree, base, extent, (True, True, False), leaves,
+        dict(kind="bell", hc=400.0, half_width=1e3, xc=xc, yc=yc),
+        dict(kind="stratified", N=0.01, T_ref=293.15, p_ref=1e5),
+        dict(kind="inflow", u0=10.0), 1.0, 1800, seed,
+    )
+    case.dt = 2.0  # Sec. 3.1
+    case.sponge = dict(depth=6e3, rate=1.0 / 100.0, u0=10.0, lateral_width=10e3, lateral_rate=1.0 / 100.0)
+    return case
+
+
 def member2d(seed: int) -> Case:
     """One uneven ensemble member: base 16x8..128x64, 0-2 levels, degree 2-5."""
     rng = np.random.default_rng(seed)
@@ -467,6 +506,8 @@ CONFIGS = {
     "hill2d": hill2d,
     "hill3d": hill3d,
     "hill3d_big": hill3d_big,
+    "bell3d_nc": lambda seed=0, **kw: bell3d(seed, refined=True, **kw),
+    "bell3d_uniform": lambda seed=0, **kw: bell3d(seed, refined=False, **kw),
 }
 
 

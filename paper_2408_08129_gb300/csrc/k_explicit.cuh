@@ -179,10 +179,7 @@ __device__ __forceinline__ void gather_faces(const MeshView<T>& mv, const T* __r
   gather_faces_codes<DIM, DEG, T, NV>(mv, Fh, codes, idx, sIt, sign_minus, sign_plus, skip_walls, acc);
 }
 
-// GZ (FP32 perturbation states on meshes affine in x and y): the metric terms
-// are recomputed from the nodal heights (metric_from_z, dg_device.cuh) and the
-// background from the height table, instead of loaded per node.
-template <int DIM, int DEG, typename T, bool FULL, bool PERT, bool GZ = false>
+template <int DIM, int DEG, typename T, bool FULL, bool PERT>
 __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_cell_kernel(MeshView<T> mv,
                                                                                  const T* __restrict__ U,
                                                                                  const T* __restrict__ Fh,
@@ -193,16 +190,8 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_cell_kernel
   __shared__ T sF[V][CPB * NC];
   __shared__ T sDw[N * N];
   __shared__ T sIt[2 * N * N];
-  __shared__ T sz[GZ ? CPB * NC : 1];
-  __shared__ T sD[GZ ? N * N : 1];
-  __shared__ T sxi[GZ ? N : 1];
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
-    sDw[q] = mv.tab[S::T_DW + q];
-    if (GZ) sD[q] = mv.tab[S::T_D + q];
-  }
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sDw[q] = mv.tab[S::T_DW + q];
   for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
-  if (GZ)
-    for (int q = threadIdx.x; q < N; q += blockDim.x) sxi[q] = mv.tab[S::T_XI + q];
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
   const int64_t c = (int64_t)blockIdx.x * CPB + lc;
   const bool active = (lc < CPB) && (c < mv.n_cells);
@@ -214,31 +203,15 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_cell_kernel
   T Ja[DIM][DIM];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = T(0);
-  T zd = T(0);
   if (active) {
+    rb = mv.rhob[idx];
+    pb = mv.pb[idx];
+    ij = mv.invJ[idx];
     load_pert<V, T, PERT>(U, Nn, idx, mv.rhob, mv.pb, u);
-    if (GZ) {
-      zd = mv.zdev[idx];
-      sz[lc * NC + i] = zd;
-    } else {
-      rb = mv.rhob[idx];
-      pb = mv.pb[idx];
-      ij = mv.invJ[idx];
 #pragma unroll
-      for (int a = 0; a < DIM; ++a)
+    for (int a = 0; a < DIM; ++a)
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) Ja[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
-    }
-  }
-  if (GZ) {
-    __syncthreads();
-    if (active) {
-      metric_from_z<DIM, DEG, T>(mv, c, sz + lc * NC, id, sD, Ja, ij);
-      const T hz = mv.hb[DIM - 1] / T(1 << mv.cell_level[c]);
-      background_at<T>(mv, mv.cell_zeta0[c] + hz * (sxi[id[DIM - 1]] + T(1)) + zd, rb, pb);
-    }
-  }
-  if (active) {
+      for (int b = 0; b < DIM; ++b) Ja[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
     const T rho = rb + u[0];
     const T irho = T(1) / rho;
     T m2 = T(0);

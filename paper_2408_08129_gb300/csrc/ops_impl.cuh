@@ -36,21 +36,13 @@ int run_explicit(const dg_mesh* m, const T* U, T* R, T* Fh, bool full, cudaStrea
   const MeshView<T>& mv = view<T>(m);
   const int64_t tf = (int64_t)mv.nf * S::NF;
   const unsigned cb = blocks_for(mv.n_cells, S::CPB);
-  // FP32 on meshes affine in x and y: the cell pass recomputes the metric terms and the background
-  const bool gz = PERT && mv.geo_z;
   count_launches(m->ctx, tf ? 2 : 1);
   if (full) {
     if (tf) explicit_face_kernel<DIM, DEG, T, true, PERT><<<blocks_for(tf, 256), 256, 0, s>>>(mv, U, Fh, skip);
-    if (gz)
-      explicit_cell_kernel<DIM, DEG, T, true, PERT, PERT><<<cb, S::THREADS, 0, s>>>(mv, U, Fh, R, skip);
-    else
-      explicit_cell_kernel<DIM, DEG, T, true, PERT, false><<<cb, S::THREADS, 0, s>>>(mv, U, Fh, R, skip);
+    explicit_cell_kernel<DIM, DEG, T, true, PERT><<<cb, S::THREADS, 0, s>>>(mv, U, Fh, R, skip);
   } else {
     if (tf) explicit_face_kernel<DIM, DEG, T, false, PERT><<<blocks_for(tf, 256), 256, 0, s>>>(mv, U, Fh, skip);
-    if (gz)
-      explicit_cell_kernel<DIM, DEG, T, false, PERT, PERT><<<cb, S::THREADS, 0, s>>>(mv, U, Fh, R, skip);
-    else
-      explicit_cell_kernel<DIM, DEG, T, false, PERT, false><<<cb, S::THREADS, 0, s>>>(mv, U, Fh, R, skip);
+    explicit_cell_kernel<DIM, DEG, T, false, PERT><<<cb, S::THREADS, 0, s>>>(mv, U, Fh, R, skip);
   }
   return check_launch("explicit operator launch");
 }

@@ -452,9 +452,14 @@ def tiny_case(
 def request_case(seed: int, dof_lo: float = 1e4, dof_hi: float = 5e6) -> Case:
     """One serving request: 2D or 3D (50/50), degree 2-5, DoF log-uniform in [dof_lo, dof_hi].
 
-    The base grid is sized to the drawn DoF (x by y by z/2 cells), with a
-    seeded hill of up to 1 km and a bubble or an inflow, 0 or 1 refinement
-    level near the ground.
+    The base grid is sized to the drawn DoF (x by y by z/2 cells) at a fixed
+    resolution of 1 km per base cell, so the domain grows with the request and
+    every request stays resolved (coarse cells of several km at low degree,
+    run for hundreds of steps, go unstable in the collocated discretisation:
+    the aliasing of the nonlinear fluxes is not damped).  A seeded hill of up
+    to a fifth of the domain height (at most 1 km) and half-width a tenth of
+    the domain length, a bubble (radius a fifth of the height) or an inflow,
+    0 or 1 refinement level near the ground.
     """
     rng = np.random.default_rng(seed)
     dim = int(rng.choice([2, 3]))
@@ -462,12 +467,14 @@ def request_case(seed: int, dof_lo: float = 1e4, dof_hi: float = 5e6) -> Case:
     dof = float(np.exp(rng.uniform(np.log(dof_lo), np.log(dof_hi))))
     V = dim + 2
     cells = dof / (V * (degree + 1) ** dim)
+    h = 1e3
     if dim == 2:
         nx = max(4, 2 * int(round(math.sqrt(2.0 * cells) / 2)))
-        base, extent, periodic = (nx, nx // 2), (40e3, 20e3), (True, False)
+        base, periodic = (nx, nx // 2), (True, False)
     else:
         nx = max(4, 2 * int(round((2.0 * cells) ** (1.0 / 3.0) / 2)))
-        base, extent, periodic = (nx, nx, nx // 2), (40e3, 40e3, 20e3), (True, True, False)
+        base, periodic = (nx, nx, nx // 2), (True, True, False)
+    extent = tuple(b * h for b in base)
     refine = bool(rng.uniform() < 0.5)
     dz = extent[-1] / base[-1]
 
@@ -475,9 +482,12 @@ def request_case(seed: int, dof_lo: float = 1e4, dof_hi: float = 5e6) -> Case:
         return level == 0 and centre[-1] < 1.1 * dz
 
     leaves = build_tree(dim, base, extent, periodic, rule if refine else None, 1 if refine else 0)
-    hill = dict(kind="gauss", hc=float(rng.uniform(0.0, 1e3)), half_width=2e3, xc=20e3, yc=20e3)
+    Lx, Lz = extent[0], extent[-1]
+    hill = dict(kind="gauss", hc=float(rng.uniform(0.0, min(1e3, 0.2 * Lz))), half_width=0.1 * Lx,
+                xc=0.5 * Lx, yc=0.5 * extent[1])
     if rng.uniform() < 0.5:
-        init = dict(kind="bubble", amp=2.0, radius=2e3, xc=float(rng.uniform(10e3, 30e3)), zc=3e3, yc=20e3)
+        init = dict(kind="bubble", amp=2.0, radius=0.2 * Lz, xc=float(rng.uniform(0.25, 0.75) * Lx), zc=0.35 * Lz,
+                    yc=0.5 * extent[1])
     else:
         init = dict(kind="inflow", u0=10.0)
     return _finish(

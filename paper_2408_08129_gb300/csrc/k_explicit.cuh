@@ -18,15 +18,13 @@
 
 namespace dg {
 
+// Face node t (< nf * NF) of the face pass: Fh[v][t] = |N| F*.n
 template <int DIM, int DEG, typename T, bool FULL, bool PERT>
-__global__ void __launch_bounds__(256) explicit_face_kernel(MeshView<T> mv, const T* __restrict__ U,
-                                                            T* __restrict__ Fh, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void explicit_face_item(const MeshView<T>& mv, const T* __restrict__ U,
+                                                   T* __restrict__ Fh, int64_t t) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, NF = S::NF, V = S::V;
   const int64_t total = (int64_t)mv.nf * NF;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
   const int f = (int)(t / NF), k = (int)(t % NF);
   const int64_t Nn = mv.n_nodes;
   const int64_t im = mv.fnode_m[t];
@@ -105,6 +103,15 @@ __global__ void __launch_bounds__(256) explicit_face_kernel(MeshView<T> mv, cons
   for (int v = 0; v < V; ++v) Fh[(int64_t)v * total + t] = sj * out[v];
 }
 
+template <int DIM, int DEG, typename T, bool FULL, bool PERT>
+__global__ void __launch_bounds__(256) explicit_face_kernel(MeshView<T> mv, const T* __restrict__ U,
+                                                            T* __restrict__ Fh, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)mv.nf * Shape<DIM, DEG>::NF) return;
+  explicit_face_item<DIM, DEG, T, FULL, PERT>(mv, U, Fh, t);
+}
+
 // Face codes (face << 2 | side, see MeshView::cell_face) of the faces node idx
 // of cell c lies on, one per axis; -1 where the node is interior along that axis.
 // Loaded early so that their latency overlaps other work.
@@ -179,21 +186,18 @@ __device__ __forceinline__ void gather_faces(const MeshView<T>& mv, const T* __r
   gather_faces_codes<DIM, DEG, T, NV>(mv, Fh, codes, idx, sIt, sign_minus, sign_plus, skip_walls, acc);
 }
 
+// Cells [batch*CPB, batch*CPB + CPB) of the cell pass.  Called by a whole
+// block; sF holds V * CPB * NC elements, sDw and sIt the tables (loaded by the
+// caller; read only after the first block barrier).
 template <int DIM, int DEG, typename T, bool FULL, bool PERT>
-__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_cell_kernel(MeshView<T> mv,
-                                                                                 const T* __restrict__ U,
-                                                                                 const T* __restrict__ Fh,
-                                                                                 T* __restrict__ R, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+__device__ __forceinline__ void explicit_cell_batch(const MeshView<T>& mv, const T* __restrict__ U,
+                                                    const T* __restrict__ Fh, T* __restrict__ R, int64_t batch,
+                                                    T (*sF)[Shape<DIM, DEG>::CPB * Shape<DIM, DEG>::NC],
+                                                    const T* sDw, const T* sIt) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, V = S::V, CPB = S::CPB;
-  __shared__ T sF[V][CPB * NC];
-  __shared__ T sDw[N * N];
-  __shared__ T sIt[2 * N * N];
-  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sDw[q] = mv.tab[S::T_DW + q];
-  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int64_t c = (int64_t)blockIdx.x * CPB + lc;
+  const int64_t c = batch * CPB + lc;
   const bool active = (lc < CPB) && (c < mv.n_cells);
   const int64_t Nn = mv.n_nodes;
   const int64_t idx = c * NC + i;
@@ -271,6 +275,22 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_cell_kernel
   const T iwend = mv.tab[S::T_IWEND];
 #pragma unroll
   for (int v = 0; v < V; ++v) R[(int64_t)v * Nn + idx] = (acc[v] + facc[v] * iwend) * ij + src[v];
+}
+
+template <int DIM, int DEG, typename T, bool FULL, bool PERT>
+__global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) explicit_cell_kernel(MeshView<T> mv,
+                                                                                 const T* __restrict__ U,
+                                                                                 const T* __restrict__ Fh,
+                                                                                 T* __restrict__ R, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  using S = Shape<DIM, DEG>;
+  constexpr int N = S::N;
+  __shared__ T sF[S::V][S::CPB * S::NC];
+  __shared__ T sDw[N * N];
+  __shared__ T sIt[2 * N * N];
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) sDw[q] = mv.tab[S::T_DW + q];
+  for (int q = threadIdx.x; q < 2 * N * N; q += blockDim.x) sIt[q] = mv.tab[S::T_IT + q];
+  explicit_cell_batch<DIM, DEG, T, FULL, PERT>(mv, U, Fh, R, blockIdx.x, sF, sDw, sIt);
 }
 
 }  // namespace dg

@@ -65,6 +65,24 @@ struct GmresItem {
   double* lmax;  // [2] Chebyshev bound of this member (device)
 };
 
+// Member packs (k_pack.cuh): one launch of an operator over many meshes of the
+// same dimension and degree, the pack passed as a kernel parameter.
+constexpr int kPack = 32;  // members per packed launch
+template <typename T>
+struct OpPack {
+  MeshView<T> mv[kPack];
+  const T* in[kPack];   // U (explicit), p (gradient), f (divergence)
+  const T* aux[kPack];  // h of the gradient (may be NULL)
+  T* out[kPack];        // R, g, div
+  T* scratch[kPack];    // face buffer (explicit)
+  int start[kPack + 1]; // first CTA of each member (filled by the launchers)
+  int n;
+};
+// FP64 operators over a pack (members of one dimension and degree)
+int op_explicit_pack(dg_ctx* ctx, int dim, int degree, OpPack<double>& P, bool full, cudaStream_t s);
+int op_grad_pack(dg_ctx* ctx, int dim, int degree, OpPack<double>& P, cudaStream_t s);
+int op_div_pack(dg_ctx* ctx, int dim, int degree, OpPack<double>& P, cudaStream_t s);
+
 // upper bound of one member's entry in a batched launch's argument table
 constexpr size_t kBatchArgBytes = 1024;
 

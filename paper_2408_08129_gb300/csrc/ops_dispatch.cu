@@ -68,6 +68,30 @@ int launch_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, i
                                     double*, unsigned long long*, cudaStream_t);                                \
   template int launch_gmres_batched<DIM, T>(dg_ctx*, const GmresItem<T>*, int, int, int*, cudaStream_t);
 
+int op_explicit_pack(dg_ctx* ctx, int dim, int degree, OpPack<double>& P, bool full, cudaStream_t s) {
+  ProfScope ps(ctx, DG_PROF_EXPLICIT, s);
+  if (dim == 2) {
+    DG_DEGREE_SWITCH(degree, return (run_explicit_pack<2, DEG, double>(ctx, P, full, s)))
+  }
+  DG_DEGREE_SWITCH(degree, return (run_explicit_pack<3, DEG, double>(ctx, P, full, s)))
+}
+
+int op_grad_pack(dg_ctx* ctx, int dim, int degree, OpPack<double>& P, cudaStream_t s) {
+  ProfScope ps(ctx, DG_PROF_GRAD, s);
+  if (dim == 2) {
+    DG_DEGREE_SWITCH(degree, return (run_grad_pack<2, DEG, double>(ctx, P, s)))
+  }
+  DG_DEGREE_SWITCH(degree, return (run_grad_pack<3, DEG, double>(ctx, P, s)))
+}
+
+int op_div_pack(dg_ctx* ctx, int dim, int degree, OpPack<double>& P, cudaStream_t s) {
+  ProfScope ps(ctx, DG_PROF_DIV, s);
+  if (dim == 2) {
+    DG_DEGREE_SWITCH(degree, return (run_div_pack<2, DEG, double>(ctx, P, s)))
+  }
+  DG_DEGREE_SWITCH(degree, return (run_div_pack<3, DEG, double>(ctx, P, s)))
+}
+
 DG_INSTANTIATE_OPS(2, double)
 DG_INSTANTIATE_OPS(2, float)
 DG_INSTANTIATE_OPS(3, double)

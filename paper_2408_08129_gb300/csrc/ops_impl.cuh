@@ -13,6 +13,7 @@
 #include "k_explicit.cuh"
 #include "k_gmres.cuh"
 #include "k_implicit.cuh"
+#include "k_pack.cuh"
 #include "ops.h"
 
 namespace dg {
@@ -74,6 +75,65 @@ int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, cudaStrea
   else
     div_cell_kernel<DIM, DEG, T, HELM, false><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
   return check_launch("divergence launch");
+}
+
+// Packed operators: the CTA ranges of the members, then one launch per pass.
+template <int DIM, int DEG, typename T>
+int run_explicit_pack(dg_ctx* ctx, OpPack<T>& P, bool full, cudaStream_t s) {
+  using S = Shape<DIM, DEG>;
+  int nb = 0;
+  for (int j = 0; j < P.n; ++j) {
+    P.start[j] = nb;
+    nb += (int)blocks_for((int64_t)P.mv[j].nf * S::NF, 256);
+  }
+  P.start[P.n] = nb;
+  if (nb > 0) {
+    if (full)
+      explicit_face_pack_kernel<DIM, DEG, T, true, false><<<nb, 256, 0, s>>>(P);
+    else
+      explicit_face_pack_kernel<DIM, DEG, T, false, false><<<nb, 256, 0, s>>>(P);
+    count_launches(ctx, 1);
+  }
+  nb = 0;
+  for (int j = 0; j < P.n; ++j) {
+    P.start[j] = nb;
+    nb += (int)blocks_for(P.mv[j].n_cells, S::CPB);
+  }
+  P.start[P.n] = nb;
+  if (full)
+    explicit_cell_pack_kernel<DIM, DEG, T, true, false><<<nb, S::THREADS, 0, s>>>(P);
+  else
+    explicit_cell_pack_kernel<DIM, DEG, T, false, false><<<nb, S::THREADS, 0, s>>>(P);
+  count_launches(ctx, 1);
+  return check_launch("packed explicit operator launch");
+}
+
+template <int DIM, int DEG, typename T>
+int run_grad_pack(dg_ctx* ctx, OpPack<T>& P, cudaStream_t s) {
+  using S = Shape<DIM, DEG>;
+  int nb = 0;
+  for (int j = 0; j < P.n; ++j) {
+    P.start[j] = nb;
+    nb += (int)blocks_for(P.mv[j].n_cells, S::CPB);
+  }
+  P.start[P.n] = nb;
+  grad_pack_kernel<DIM, DEG, T><<<nb, S::THREADS, 0, s>>>(P);
+  count_launches(ctx, 1);
+  return check_launch("packed gradient launch");
+}
+
+template <int DIM, int DEG, typename T>
+int run_div_pack(dg_ctx* ctx, OpPack<T>& P, cudaStream_t s) {
+  using S = Shape<DIM, DEG>;
+  int nb = 0;
+  for (int j = 0; j < P.n; ++j) {
+    P.start[j] = nb;
+    nb += (int)blocks_for(P.mv[j].n_cells, S::CPB);
+  }
+  P.start[P.n] = nb;
+  div_pack_kernel<DIM, DEG, T><<<nb, S::THREADS, 0, s>>>(P);
+  count_launches(ctx, 1);
+  return check_launch("packed divergence launch");
 }
 
 template <int DIM, int DEG, typename TK>
@@ -263,6 +323,9 @@ int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int 
   template int run_gmres<DIM, DEG, T>(const dg_mesh*, const double*, const T*, const double*, double*, double,    \
                                       double, double, int, int, int, T*, T*, double*, double*, int, double*,      \
                                       double*, unsigned long long*, cudaStream_t);                               \
-  template int run_gmres_batched<DIM, DEG, T>(dg_ctx*, const GmresItem<T>*, int, int, int*, cudaStream_t);
+  template int run_gmres_batched<DIM, DEG, T>(dg_ctx*, const GmresItem<T>*, int, int, int*, cudaStream_t);     \
+  template int run_explicit_pack<DIM, DEG, T>(dg_ctx*, OpPack<T>&, bool, cudaStream_t);                         \
+  template int run_grad_pack<DIM, DEG, T>(dg_ctx*, OpPack<T>&, cudaStream_t);                                   \
+  template int run_div_pack<DIM, DEG, T>(dg_ctx*, OpPack<T>&, cudaStream_t);
 
 }  // namespace dg

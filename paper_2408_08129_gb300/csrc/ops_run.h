@@ -21,4 +21,11 @@ template <int DIM, int DEG, typename TK>
 int run_gmres_batched(dg_ctx* ctx, const GmresItem<TK>* items, int n_items, int restart, int* err,
                       cudaStream_t s);
 
+template <int DIM, int DEG, typename T>
+int run_explicit_pack(dg_ctx* ctx, OpPack<T>& P, bool full, cudaStream_t s);
+template <int DIM, int DEG, typename T>
+int run_grad_pack(dg_ctx* ctx, OpPack<T>& P, cudaStream_t s);
+template <int DIM, int DEG, typename T>
+int run_div_pack(dg_ctx* ctx, OpPack<T>& P, cudaStream_t s);
+
 }  // namespace dg

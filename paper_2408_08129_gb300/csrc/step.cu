@@ -72,155 +72,208 @@ inline unsigned gridn(int64_t n) {
 
 #define GRID_LOOP(i, n) for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-// p' = (g-1)(rho E - |m|^2/(2 rho)) - p_bar and h = gamma p / ((gamma-1) rho)
-__global__ void pressure_kernel(const double* __restrict__ U, const double* __restrict__ pb, int64_t Nn, int dim,
-                                double* __restrict__ pp, double* __restrict__ h) {
-  const int V = dim + 2;
-  GRID_LOOP(i, Nn) {
-    const double rho = U[i];
-    double m2 = 0.0;
-    for (int b = 0; b < dim; ++b) m2 += U[(1 + b) * Nn + i] * U[(1 + b) * Nn + i];
-    const double p = (kGamma - 1.0) * (U[(V - 1) * Nn + i] - 0.5 * m2 / rho);
-    pp[i] = p - pb[i];
-    h[i] = kGamma * p / ((kGamma - 1.0) * rho);
-  }
-}
+// ---- the step's pointwise work, as operations on member views ----------------
+//
+// Each operation works on one node (or one entry of a multi-variable array) of
+// one member; pack_kernel runs it over the nodes of up to kPack members in one
+// launch (the pack is a kernel parameter), so that an ensemble step launches
+// every pointwise phase once, and a single step uses the same code with one
+// member.
 
-// out[b] = h * m[b]
-__global__ void hm_kernel(const double* __restrict__ h, const double* __restrict__ m, int64_t Nn, int dim,
-                          double* __restrict__ out) {
-  GRID_LOOP(i, Nn) {
-    for (int b = 0; b < dim; ++b) out[b * Nn + i] = h[i] * m[b * Nn + i];
-  }
-}
-
-// implicit tendencies: I = (0, -g - rho' grav k, -divhm)
-__global__ void implicit_terms_kernel(const double* __restrict__ rho, const double* __restrict__ rhob,
-                                      const double* __restrict__ g, const double* __restrict__ divhm, double grav,
-                                      int64_t Nn, int dim, double* __restrict__ I) {
-  const int V = dim + 2;
-  GRID_LOOP(i, Nn) {
-    I[i] = 0.0;
-    for (int b = 0; b < dim; ++b) I[(1 + b) * Nn + i] = -g[b * Nn + i];
-    I[dim * Nn + i] -= (rho[i] - rhob[i]) * grav;
-    I[(V - 1) * Nn + i] = -divhm[i];
-  }
-}
-
-struct StageCoef {
-  double ae[2], ai[2];
-  int nprev;
+// what the pointwise operations of the step read and write of one member
+struct StepView {
+  double *U, *E0, *E1, *E2, *I0, *I1, *Ui, *rho, *mhat, *Ehat, *p, *p_prev, *h, *mk, *rhs, *tmpv, *tmps, *g;
+  float* f32;
+  int* flag;
+  const double *rhob, *pb, *tau;
+  int64_t Nn;
+  int dim;
+  double dt, grav, u0;
 };
 
-// rho, mhat, Ehat of an implicit stage from U^n and the earlier tendencies
-__global__ void stage_combine_kernel(const double* __restrict__ U, const double* __restrict__ E0,
-                                     const double* __restrict__ E1, const double* __restrict__ I0,
-                                     const double* __restrict__ I1, StageCoef c, double dt, double dt_aii,
-                                     const double* __restrict__ rhob, double grav, int64_t Nn, int dim,
-                                     double* __restrict__ rho, double* __restrict__ mhat, double* __restrict__ Ehat) {
-  const int V = dim + 2;
-  GRID_LOOP(i, Nn) {
-    double r = c.ae[0] * E0[i];
-    if (c.nprev > 1) r += c.ae[1] * E1[i];
-    const double rh = U[i] + dt * r;
-    rho[i] = rh;
-    for (int b = 0; b < dim; ++b) {
-      const int64_t o = (int64_t)(1 + b) * Nn + i;
-      double s = c.ae[0] * E0[o] + c.ai[0] * I0[o];
-      if (c.nprev > 1) s += c.ae[1] * E1[o] + c.ai[1] * I1[o];
-      double mh = U[o] + dt * s;
-      if (b == dim - 1) mh -= dt_aii * (rh - rhob[i]) * grav;
-      mhat[b * Nn + i] = mh;
-    }
-    const int64_t o = (int64_t)(V - 1) * Nn + i;
-    double s = c.ae[0] * E0[o] + c.ai[0] * I0[o];
-    if (c.nprev > 1) s += c.ae[1] * E1[o] + c.ai[1] * I1[o];
-    Ehat[i] = U[o] + dt * s;
-  }
+struct StepPack {
+  StepView m[kPack];
+  int64_t start[kPack + 1];  // first CTA of each member
+  int n;
+};
+
+__device__ __forceinline__ double* e_of(const StepView& M, int j) { return j == 0 ? M.E0 : (j == 1 ? M.E1 : M.E2); }
+
+template <class Op>
+__global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ StepPack P, const Op op) {
+  int j = 0;
+  while (j + 1 < P.n && (int64_t)blockIdx.x >= P.start[j + 1]) ++j;
+  const StepView& M = P.m[j];
+  const int64_t len = M.Nn * op.width(M.dim);
+  const int64_t stride = (P.start[j + 1] - P.start[j]) * blockDim.x;
+  for (int64_t i = (int64_t)(blockIdx.x - P.start[j]) * blockDim.x + threadIdx.x; i < len; i += stride) op(M, i);
 }
 
-// Picard preparation: h = gamma (p_bar + p')/((g-1) rho);  rhs0 = Ehat - p_bar/(g-1) - |mk|^2/(2 rho);
-// hm = h * mhat
-__global__ void picard_prep_kernel(const double* __restrict__ pp, const double* __restrict__ pb,
-                                   const double* __restrict__ rho, const double* __restrict__ mk,
-                                   const double* __restrict__ mhat, const double* __restrict__ Ehat, int64_t Nn,
-                                   int dim, double* __restrict__ h, double* __restrict__ rhs0,
-                                   double* __restrict__ hm) {
-  GRID_LOOP(i, Nn) {
-    const double r = rho[i];
-    const double hh = kGamma * (pb[i] + pp[i]) / ((kGamma - 1.0) * r);
-    h[i] = hh;
+// p' = (g-1)(rho E - |m|^2/(2 rho)) - p_bar and h = gamma p / ((gamma-1) rho) of U; the step's
+// first operation also clears the member's non-finite flag
+struct OpPressure {
+  __host__ __device__ int width(int) const { return 1; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    const int64_t Nn = M.Nn;
+    const int V = M.dim + 2;
+    if (i == 0) *M.flag = 0;
+    const double rho = M.U[i];
     double m2 = 0.0;
-    for (int b = 0; b < dim; ++b) {
-      m2 += mk[b * Nn + i] * mk[b * Nn + i];
-      hm[b * Nn + i] = hh * mhat[b * Nn + i];
-    }
-    rhs0[i] = Ehat[i] - pb[i] / (kGamma - 1.0) - 0.5 * m2 / r;
+    for (int b = 0; b < M.dim; ++b) m2 += M.U[(1 + b) * Nn + i] * M.U[(1 + b) * Nn + i];
+    const double p = (kGamma - 1.0) * (M.U[(V - 1) * Nn + i] - 0.5 * m2 / rho);
+    M.p_prev[i] = p - M.pb[i];
+    M.h[i] = kGamma * p / ((kGamma - 1.0) * rho);
   }
-}
+};
+
+// tmpv[b] = h * m[b], m the momentum of U (from_mk = 0) or mk (1)
+struct OpHm {
+  int from_mk;
+  __host__ __device__ int width(int) const { return 1; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    const double* m = from_mk ? M.mk : M.U + M.Nn;
+    for (int b = 0; b < M.dim; ++b) M.tmpv[b * M.Nn + i] = M.h[i] * m[b * M.Nn + i];
+  }
+};
+
+// implicit tendencies I_k = (0, -g - rho' grav k, -div(h m)) with rho from U (k = 0) or Ui (k = 1)
+struct OpImplicitTerms {
+  int k;
+  __host__ __device__ int width(int) const { return 1; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    const int64_t Nn = M.Nn;
+    const int V = M.dim + 2;
+    const double* rho = k ? M.Ui : M.U;
+    double* I = k ? M.I1 : M.I0;
+    I[i] = 0.0;
+    for (int b = 0; b < M.dim; ++b) I[(1 + b) * Nn + i] = -M.g[b * Nn + i];
+    I[M.dim * Nn + i] -= (rho[i] - M.rhob[i]) * M.grav;
+    I[(V - 1) * Nn + i] = -M.tmps[i];
+  }
+};
+
+// rho, mhat, Ehat of implicit stage `stage` from U^n and the earlier tendencies; p = p_prev
+// (the Picard loop starts from the previous stage's pressure) and mk = mhat
+struct OpStageCombine {
+  int stage;
+  double ae[2], ai[2], aii;  // tableau rows (times dt in the operation)
+  __host__ __device__ int width(int) const { return 1; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    const int64_t Nn = M.Nn;
+    const int V = M.dim + 2;
+    const double dt = M.dt, dta = dt * aii;
+    double r = ae[0] * M.E0[i];
+    if (stage > 1) r += ae[1] * M.E1[i];
+    const double rh = M.U[i] + dt * r;
+    M.rho[i] = rh;
+    for (int b = 0; b < M.dim; ++b) {
+      const int64_t o = (int64_t)(1 + b) * Nn + i;
+      double s = ae[0] * M.E0[o] + ai[0] * M.I0[o];
+      if (stage > 1) s += ae[1] * M.E1[o] + ai[1] * M.I1[o];
+      double mh = M.U[o] + dt * s;
+      if (b == M.dim - 1) mh -= dta * (rh - M.rhob[i]) * M.grav;
+      M.mhat[b * Nn + i] = mh;
+      M.mk[b * Nn + i] = mh;
+    }
+    const int64_t o = (int64_t)(V - 1) * Nn + i;
+    double s = ae[0] * M.E0[o] + ai[0] * M.I0[o];
+    if (stage > 1) s += ae[1] * M.E1[o] + ai[1] * M.I1[o];
+    M.Ehat[i] = M.U[o] + dt * s;
+    M.p[i] = M.p_prev[i];
+  }
+};
+
+// Picard preparation: h = gamma (p_bar + p')/((g-1) rho); rhs = Ehat - p_bar/(g-1) - |mk|^2/(2 rho);
+// tmpv = h * mhat
+struct OpPicardPrep {
+  __host__ __device__ int width(int) const { return 1; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    const int64_t Nn = M.Nn;
+    const double r = M.rho[i];
+    const double hh = kGamma * (M.pb[i] + M.p[i]) / ((kGamma - 1.0) * r);
+    M.h[i] = hh;
+    double m2 = 0.0;
+    for (int b = 0; b < M.dim; ++b) {
+      m2 += M.mk[b * Nn + i] * M.mk[b * Nn + i];
+      M.tmpv[b * Nn + i] = hh * M.mhat[b * Nn + i];
+    }
+    M.rhs[i] = M.Ehat[i] - M.pb[i] / (kGamma - 1.0) - 0.5 * m2 / r;
+  }
+};
+
+// rhs -= dt a_ii div(h mhat); FP32 forms also get h in FP32 for their Krylov mat-vecs
+struct OpRhsFinish {
+  double aii;
+  int f32;
+  __host__ __device__ int width(int) const { return 1; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    M.rhs[i] += -(M.dt * aii) * M.tmps[i];
+    if (f32) M.f32[i] = (float)M.h[i];
+  }
+};
+
+// mk = mhat - dt a_ii grad p'
+struct OpMomentum {
+  double aii;
+  __host__ __device__ int width(int dim) const { return dim; }
+  __device__ void operator()(const StepView& M, int64_t i) const { M.mk[i] = M.mhat[i] - (M.dt * aii) * M.g[i]; }
+};
+
+// stage state: (rho, mk, (p_bar + p')/(g-1) + |mk|^2/(2 rho))
+struct OpStageState {
+  __host__ __device__ int width(int) const { return 1; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    const int64_t Nn = M.Nn;
+    const int V = M.dim + 2;
+    const double r = M.rho[i];
+    double m2 = 0.0;
+    M.Ui[i] = r;
+    for (int b = 0; b < M.dim; ++b) {
+      const double mb = M.mk[b * Nn + i];
+      M.Ui[(1 + b) * Nn + i] = mb;
+      m2 += mb * mb;
+    }
+    M.Ui[(V - 1) * Nn + i] = (M.pb[i] + M.p[i]) / (kGamma - 1.0) + 0.5 * m2 / r;
+  }
+};
+
+// Rayleigh damping layer: E_k -= tau (X - U_ref), X = U (k = 0) or Ui, U_ref = the background with
+// the uniform x-velocity u0 (rho_b, rho_b u0, 0.., p_b/(gamma-1) + rho_b u0^2/2); no-op without a layer
+struct OpSponge {
+  int k;
+  __host__ __device__ int width(int) const { return 1; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    if (!M.tau) return;
+    const double t = M.tau[i];
+    if (t == 0.0) return;
+    const int64_t n = M.Nn;
+    const double* X = k ? M.Ui : M.U;
+    double* E = e_of(M, k);
+    const double rb = M.rhob[i], u0 = M.u0;
+    E[i] -= t * (X[i] - rb);
+    E[n + i] -= t * (X[n + i] - rb * u0);
+    for (int b = 1; b < M.dim; ++b) E[(int64_t)(1 + b) * n + i] -= t * X[(int64_t)(1 + b) * n + i];
+    const int64_t ie = (int64_t)(M.dim + 1) * n + i;
+    E[ie] -= t * (X[ie] - (M.pb[i] / (kGamma - 1.0) + 0.5 * rb * u0 * u0));
+  }
+};
+
+// U = Ui + dt sum_j c_j E_j; flag non-finite values
+struct OpFinal {
+  double c[3];  // b_j - A[2][j]
+  __host__ __device__ int width(int dim) const { return dim + 2; }
+  __device__ void operator()(const StepView& M, int64_t i) const {
+    const double v = M.Ui[i] + (M.dt * c[0]) * M.E0[i] + (M.dt * c[1]) * M.E1[i] + (M.dt * c[2]) * M.E2[i];
+    M.U[i] = v;
+    if (!isfinite(v)) *M.flag = 1;
+  }
+};
+
 
 // ax = b - ax (in place)
 __global__ void sub_from_kernel(const double* b, double* ax, int64_t n) {
   GRID_LOOP(i, n) { ax[i] = b[i] - ax[i]; }
 }
-
-// y += c * x
-__global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double c, int64_t n) {
-  GRID_LOOP(i, n) { y[i] += c * x[i]; }
-}
-
-// mk = mhat - c * g
-__global__ void momentum_kernel(const double* __restrict__ mhat, const double* __restrict__ g, double c, int64_t n,
-                                double* __restrict__ mk) {
-  GRID_LOOP(i, n) { mk[i] = mhat[i] - c * g[i]; }
-}
-
-// stage state: (rho, mk, (p_bar + p')/(g-1) + |mk|^2/(2 rho))
-__global__ void stage_state_kernel(const double* __restrict__ rho, const double* __restrict__ mk,
-                                   const double* __restrict__ pp, const double* __restrict__ pb, int64_t Nn, int dim,
-                                   double* __restrict__ Ui) {
-  const int V = dim + 2;
-  GRID_LOOP(i, Nn) {
-    const double r = rho[i];
-    double m2 = 0.0;
-    Ui[i] = r;
-    for (int b = 0; b < dim; ++b) {
-      const double mb = mk[b * Nn + i];
-      Ui[(1 + b) * Nn + i] = mb;
-      m2 += mb * mb;
-    }
-    Ui[(V - 1) * Nn + i] = (pb[i] + pp[i]) / (kGamma - 1.0) + 0.5 * m2 / r;
-  }
-}
-
-// U = Ui + dt sum_j c_j E_j ; flag non-finite values
-__global__ void final_kernel(const double* __restrict__ Ui, const double* __restrict__ E0,
-                             const double* __restrict__ E1, const double* __restrict__ E2, double c0, double c1,
-                             double c2, int64_t n, double* __restrict__ U, int* __restrict__ flag) {
-  GRID_LOOP(i, n) {
-    const double v = Ui[i] + c0 * E0[i] + c1 * E1[i] + c2 * E2[i];
-    U[i] = v;
-    if (!isfinite(v)) *flag = 1;
-  }
-}
-
-// Rayleigh damping layer: E -= tau (U - U_ref), U_ref = background with the
-// uniform x-velocity u0 (rho_b, rho_b u0, 0.., p_b/(gamma-1) + rho_b u0^2/2)
-__global__ void sponge_kernel(const double* __restrict__ U, const double* __restrict__ tau,
-                              const double* __restrict__ rhob, const double* __restrict__ pb, double u0, int64_t n,
-                              int dim, double* __restrict__ E) {
-  GRID_LOOP(i, n) {
-    const double t = tau[i];
-    if (t == 0.0) continue;
-    const double rb = rhob[i];
-    E[i] -= t * (U[i] - rb);
-    E[n + i] -= t * (U[n + i] - rb * u0);
-    for (int b = 1; b < dim; ++b) E[(int64_t)(1 + b) * n + i] -= t * U[(int64_t)(1 + b) * n + i];
-    const int64_t ie = (int64_t)(dim + 1) * n + i;
-    E[ie] -= t * (U[ie] - (pb[i] / (kGamma - 1.0) + 0.5 * rb * u0 * u0));
-  }
-}
-
 __global__ void to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
   GRID_LOOP(i, n) { y[i] = (float)x[i]; }
 }
@@ -322,20 +375,6 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
 // new state directly, with no correction step after them, so they stay in
 // FP64 in both precision modes; the FP32 form puts the Krylov mat-vecs (the
 // bulk of the work) in FP32 and recovers FP64 accuracy by the FP64 residual.
-int step_explicit(dg_state* S, const double* U, double* E, cudaStream_t s) {
-  const dg_mesh* m = S->mesh;
-  int rc = op_explicit<double>(m, U, E, m->d_face_scratch64, false, s, nullptr);
-  if (rc != DG_OK || !m->d_tau) return rc;
-  sponge_kernel<<<gridn(S->Nn), 256, 0, s>>>(U, m->d_tau, m->v64.rhob, m->v64.pb, m->desc.sponge_u0, S->Nn, S->dim, E);
-  count_launches(S->ctx, 1);
-  return check("sponge layer");
-}
-int step_grad(dg_state* S, const double* p, double* g, cudaStream_t s) {
-  return op_grad<double>(S->mesh, p, nullptr, g, s, nullptr);
-}
-int step_div(dg_state* S, const double* f, double* out, cudaStream_t s) {
-  return op_div<double>(S->mesh, f, out, s, nullptr);
-}
 
 }  // namespace
 
@@ -481,62 +520,157 @@ struct Member {
 
 inline double stage_dta(const Member& M, int i) { return M.dt * AIM[i][i]; }
 
-int phase_stage1(Member& M, cudaStream_t s) {
-  dg_state* S = M.S;
-  const int64_t Nn = S->Nn;
-  const int dim = S->dim;
-  const unsigned gb = gridn(Nn);
-  const MeshView<double>& mv = M.m->v64;
-  int rc;
-  pressure_kernel<<<gb, 256, 0, s>>>(S->U, mv.pb, Nn, dim, S->p_prev, S->h);
-  count_launches(S->ctx, 1);
-  if ((rc = step_explicit(S, S->U, S->E[0], s)) != DG_OK) return rc;
-  if ((rc = step_grad(S, S->p_prev, S->g, s)) != DG_OK) return rc;
-  hm_kernel<<<gb, 256, 0, s>>>(S->h, S->U + Nn, Nn, dim, S->tmpv);
-  count_launches(S->ctx, 1);
-  if ((rc = step_div(S, S->tmpv, S->tmps, s)) != DG_OK) return rc;
-  implicit_terms_kernel<<<gb, 256, 0, s>>>(S->U, mv.rhob, S->g, S->tmps, M.m->desc.gravity, Nn, dim, S->I[0]);
-  count_launches(S->ctx, 1);
-  return check("stage 1");
+// ---- the step's phases over a list of members ----
+
+StepView step_view(const Member& M) {
+  const dg_state* S = M.S;
+  StepView v;
+  v.U = S->U;
+  v.E0 = S->E[0];
+  v.E1 = S->E[1];
+  v.E2 = S->E[2];
+  v.I0 = S->I[0];
+  v.I1 = S->I[1];
+  v.Ui = S->Ui;
+  v.rho = S->rho;
+  v.mhat = S->mhat;
+  v.Ehat = S->Ehat;
+  v.p = S->p;
+  v.p_prev = S->p_prev;
+  v.h = S->h;
+  v.mk = S->mk;
+  v.rhs = S->rhs;
+  v.tmpv = S->tmpv;
+  v.tmps = S->tmps;
+  v.g = S->g;
+  v.f32 = S->f32;
+  v.flag = S->flag;
+  v.rhob = M.m->v64.rhob;
+  v.pb = M.m->v64.pb;
+  v.tau = M.m->d_tau;
+  v.Nn = S->Nn;
+  v.dim = S->dim;
+  v.dt = M.dt;
+  v.grav = M.m->desc.gravity;
+  v.u0 = M.m->desc.sponge_u0;
+  return v;
 }
 
-int phase_stage_begin(Member& M, int i, cudaStream_t s) {
-  dg_state* S = M.S;
-  const int64_t Nn = S->Nn;
-  const int dim = S->dim;
-  StageCoef c{};
-  c.nprev = i;
-  for (int j = 0; j < i; ++j) {
-    c.ae[j] = AEX[i][j];
-    c.ai[j] = AIM[i][j];
+// one launch of a pointwise operation over the members (one per kPack members)
+template <class Op>
+int launch_pack(dg_ctx* ctx, std::vector<Member>& M, const Op& op, cudaStream_t s) {
+  for (size_t first = 0; first < M.size(); first += kPack) {
+    StepPack P;
+    P.n = (int)std::min(M.size() - first, (size_t)kPack);
+    int64_t nb = 0;
+    for (int j = 0; j < P.n; ++j) {
+      P.m[j] = step_view(M[first + j]);
+      P.start[j] = nb;
+      const int64_t len = P.m[j].Nn * op.width(P.m[j].dim);
+      nb += std::max<int64_t>(1, std::min<int64_t>((len + 255) / 256, 2048));
+    }
+    P.start[P.n] = nb;
+    pack_kernel<Op><<<(unsigned)nb, 256, 0, s>>>(P, op);
+    count_launches(ctx, 1);
   }
-  stage_combine_kernel<<<gridn(Nn), 256, 0, s>>>(S->U, S->E[0], S->E[1], S->I[0], S->I[1], c, M.dt,
-                                                 stage_dta(M, i), M.m->v64.rhob, M.m->desc.gravity, Nn, dim, S->rho,
-                                                 S->mhat, S->Ehat);
-  count_launches(S->ctx, 1);
-  DG_CUDA(cudaMemcpyAsync(S->p, S->p_prev, Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  DG_CUDA(cudaMemcpyAsync(S->mk, S->mhat, (size_t)dim * Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  return check("stage begin");
+  return check("pointwise step operation");
+}
+
+// members grouped by (dimension, degree): the packed FP64 operators need one shape
+std::vector<std::vector<Member*>> shape_groups(std::vector<Member>& M) {
+  std::vector<std::vector<Member*>> g;
+  std::vector<int> key;
+  for (auto& mm : M) {
+    const int k = mm.m->dim * 16 + mm.m->degree;
+    size_t j = 0;
+    for (; j < key.size(); ++j)
+      if (key[j] == k) break;
+    if (j == key.size()) {
+      key.push_back(k);
+      g.emplace_back();
+    }
+    g[j].push_back(&mm);
+  }
+  return g;
+}
+
+// one FP64 operator over every member: kind 0 explicit (U -> E0, or Ui -> E_k for k > 0),
+// 1 gradient (p_prev, or p if k = 1, -> g), 2 divergence (tmpv -> tmps)
+int launch_dg(dg_ctx* ctx, std::vector<Member>& M, int kind, int k, cudaStream_t s) {
+  int rc;
+  for (auto& grp : shape_groups(M)) {
+    for (size_t first = 0; first < grp.size(); first += kPack) {
+      OpPack<double> P;
+      P.n = (int)std::min(grp.size() - first, (size_t)kPack);
+      for (int j = 0; j < P.n; ++j) {
+        const Member& mm = *grp[first + j];
+        dg_state* S = mm.S;
+        P.mv[j] = mm.m->v64;
+        P.aux[j] = nullptr;
+        P.scratch[j] = mm.m->d_face_scratch64;
+        if (kind == 0) {
+          P.in[j] = k == 0 ? S->U : S->Ui;
+          P.out[j] = S->E[k];
+        } else if (kind == 1) {
+          P.in[j] = k == 0 ? S->p_prev : S->p;
+          P.out[j] = S->g;
+        } else {
+          P.in[j] = S->tmpv;
+          P.out[j] = S->tmps;
+        }
+      }
+      const int dim = grp[first]->m->dim, deg = grp[first]->m->degree;
+      rc = kind == 0 ? op_explicit_pack(ctx, dim, deg, P, false, s)
+                     : (kind == 1 ? op_grad_pack(ctx, dim, deg, P, s) : op_div_pack(ctx, dim, deg, P, s));
+      if (rc != DG_OK) return rc;
+    }
+  }
+  return DG_OK;
+}
+
+bool any_layer(const std::vector<Member>& M) {
+  for (const auto& mm : M)
+    if (mm.m->d_tau) return true;
+  return false;
+}
+
+// the explicit tendency E_k of U (k = 0) or of the stage state Ui, with the damping layer
+int phase_explicit(dg_ctx* ctx, std::vector<Member>& M, int k, cudaStream_t s) {
+  int rc = launch_dg(ctx, M, 0, k, s);
+  if (rc != DG_OK || !any_layer(M)) return rc;
+  return launch_pack(ctx, M, OpSponge{k}, s);
+}
+
+// stage 1: tendencies of U^n (explicit, and the implicit ones with the pressure of U^n)
+int phase_stage1(dg_ctx* ctx, std::vector<Member>& M, cudaStream_t s) {
+  int rc;
+  if ((rc = launch_pack(ctx, M, OpPressure{}, s)) != DG_OK) return rc;
+  if ((rc = phase_explicit(ctx, M, 0, s)) != DG_OK) return rc;
+  if ((rc = launch_dg(ctx, M, 1, 0, s)) != DG_OK) return rc;
+  if ((rc = launch_pack(ctx, M, OpHm{0}, s)) != DG_OK) return rc;
+  if ((rc = launch_dg(ctx, M, 2, 0, s)) != DG_OK) return rc;
+  return launch_pack(ctx, M, OpImplicitTerms{0}, s);
+}
+
+int phase_stage_begin(dg_ctx* ctx, std::vector<Member>& M, int i, cudaStream_t s) {
+  OpStageCombine op{};
+  op.stage = i;
+  for (int j = 0; j < i; ++j) {
+    op.ae[j] = AEX[i][j];
+    op.ai[j] = AIM[i][j];
+  }
+  op.aii = AIM[i][i];
+  return launch_pack(ctx, M, op, s);
 }
 
 // right-hand side of the Helmholtz problem for the current Picard iterate
-int phase_picard_pre(Member& M, int i, cudaStream_t s) {
-  dg_state* S = M.S;
-  const int64_t Nn = S->Nn;
-  const unsigned gb = gridn(Nn);
+int phase_picard_pre(dg_ctx* ctx, std::vector<Member>& M, int i, cudaStream_t s) {
   int rc;
-  if (M.nsolve >= 64) return fail(DG_EINVAL, "too many Picard iterations per step (at most 32)");
-  picard_prep_kernel<<<gb, 256, 0, s>>>(S->p, M.m->v64.pb, S->rho, S->mk, S->mhat, S->Ehat, Nn, S->dim, S->h,
-                                        S->rhs, S->tmpv);
-  count_launches(S->ctx, 1);
-  if ((rc = step_div(S, S->tmpv, S->tmps, s)) != DG_OK) return rc;
-  axpy_kernel<<<gb, 256, 0, s>>>(S->rhs, S->tmps, -stage_dta(M, i), Nn);
-  count_launches(S->ctx, 1);
-  if (M.o.precision == DG_FP32) {
-    to_f32_kernel<<<gb, 256, 0, s>>>(S->h, S->f32, Nn);  // h for the FP32 Arnoldi mat-vecs
-    count_launches(S->ctx, 1);
-  }
-  return check("picard");
+  for (auto& mm : M)
+    if (mm.nsolve >= 64) return fail(DG_EINVAL, "too many Picard iterations per step (at most 32)");
+  if ((rc = launch_pack(ctx, M, OpPicardPrep{}, s)) != DG_OK) return rc;
+  if ((rc = launch_dg(ctx, M, 2, 0, s)) != DG_OK) return rc;
+  return launch_pack(ctx, M, OpRhsFinish{AIM[i][i], M[0].o.precision == DG_FP32 ? 1 : 0}, s);
 }
 
 // Solver forms the autotuner chooses among
@@ -616,45 +750,29 @@ int phase_solve_single(Member& M, int i, cudaStream_t s) {
   return rc;
 }
 
-int phase_picard_post(Member& M, int i, cudaStream_t s) {
-  dg_state* S = M.S;
+int phase_picard_post(dg_ctx* ctx, std::vector<Member>& M, int i, cudaStream_t s) {
   int rc;
-  if ((rc = step_grad(S, S->p, S->g, s)) != DG_OK) return rc;
-  momentum_kernel<<<gridn(S->Nn), 256, 0, s>>>(S->mhat, S->g, stage_dta(M, i), (int64_t)S->dim * S->Nn, S->mk);
-  count_launches(S->ctx, 1);
-  return check("momentum update");
+  if ((rc = launch_dg(ctx, M, 1, 1, s)) != DG_OK) return rc;
+  return launch_pack(ctx, M, OpMomentum{AIM[i][i]}, s);
 }
 
-int phase_stage_end(Member& M, int i, cudaStream_t s) {
-  dg_state* S = M.S;
-  const int64_t Nn = S->Nn;
-  const int dim = S->dim;
-  const unsigned gb = gridn(Nn);
+int phase_stage_end(dg_ctx* ctx, std::vector<Member>& M, int i, cudaStream_t s) {
   int rc;
-  stage_state_kernel<<<gb, 256, 0, s>>>(S->rho, S->mk, S->p, M.m->v64.pb, Nn, dim, S->Ui);
-  count_launches(S->ctx, 1);
-  if ((rc = step_explicit(S, S->Ui, S->E[i], s)) != DG_OK) return rc;
+  if ((rc = launch_pack(ctx, M, OpStageState{}, s)) != DG_OK) return rc;
+  if ((rc = phase_explicit(ctx, M, i, s)) != DG_OK) return rc;
   if (i == 1) {
-    hm_kernel<<<gb, 256, 0, s>>>(S->h, S->mk, Nn, dim, S->tmpv);
-    count_launches(S->ctx, 1);
-    if ((rc = step_div(S, S->tmpv, S->tmps, s)) != DG_OK) return rc;
-    implicit_terms_kernel<<<gb, 256, 0, s>>>(S->Ui, M.m->v64.rhob, S->g, S->tmps, M.m->desc.gravity, Nn, dim,
-                                             S->I[1]);
-    count_launches(S->ctx, 1);
+    if ((rc = launch_pack(ctx, M, OpHm{1}, s)) != DG_OK) return rc;
+    if ((rc = launch_dg(ctx, M, 2, 0, s)) != DG_OK) return rc;
+    if ((rc = launch_pack(ctx, M, OpImplicitTerms{1}, s)) != DG_OK) return rc;
   }
-  std::swap(S->p, S->p_prev);
-  return check("stage end");
+  for (auto& mm : M) std::swap(mm.S->p, mm.S->p_prev);
+  return DG_OK;
 }
 
-int phase_final(Member& M, cudaStream_t s) {
-  dg_state* S = M.S;
-  const double dt = M.dt;
-  DG_CUDA(cudaMemsetAsync(S->flag, 0, sizeof(int), s));
-  final_kernel<<<gridn(S->Nn), 256, 0, s>>>(S->Ui, S->E[0], S->E[1], S->E[2], dt * (BW[0] - AEX[2][0]),
-                                            dt * (BW[1] - AEX[2][1]), dt * (BW[2] - AEX[2][2]),
-                                            (int64_t)S->V * S->Nn, S->U, S->flag);
-  count_launches(S->ctx, 1);
-  return check("final combination");
+int phase_final(dg_ctx* ctx, std::vector<Member>& M, cudaStream_t s) {
+  OpFinal op{};
+  for (int j = 0; j < 3; ++j) op.c[j] = BW[j] - AEX[2][j];
+  return launch_pack(ctx, M, op, s);
 }
 
 // after the stream has been synchronised: solve results and the non-finite flag
@@ -689,8 +807,8 @@ int prepare_member(Member& M, dg_ctx* ctx, const dg_mesh* m, dg_state* S, double
 
 extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double dt, const dg_solver_opts* opts,
                              dg_step_stats* stats, void* stream) {
-  Member M;
-  int rc = prepare_member(M, ctx, m, S, dt, opts);
+  std::vector<Member> M(1);
+  int rc = prepare_member(M[0], ctx, m, S, dt, opts);
   if (rc != DG_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   ProfScope step_scope(ctx, DG_PROF_STEP, s);
@@ -698,39 +816,30 @@ extern "C" int imex_rk2_step(dg_ctx* ctx, const dg_mesh* m, dg_state* S, double 
   do {                                  \
     if ((rc = (x)) != DG_OK) return rc; \
   } while (0)
-  RUN(phase_stage1(M, s));
+  RUN(phase_stage1(ctx, M, s));
   for (int i = 1; i <= 2; ++i) {
-    RUN(phase_stage_begin(M, i, s));
-    for (int it = 0; it < M.o.picard; ++it) {
-      RUN(phase_picard_pre(M, i, s));
-      RUN(phase_solve_single(M, i, s));
-      RUN(phase_picard_post(M, i, s));
+    RUN(phase_stage_begin(ctx, M, i, s));
+    for (int it = 0; it < M[0].o.picard; ++it) {
+      RUN(phase_picard_pre(ctx, M, i, s));
+      RUN(phase_solve_single(M[0], i, s));
+      RUN(phase_picard_post(ctx, M, i, s));
     }
-    RUN(phase_stage_end(M, i, s));
+    RUN(phase_stage_end(ctx, M, i, s));
   }
-  RUN(phase_final(M, s));
+  RUN(phase_final(ctx, M, s));
 #undef RUN
   int flag = 0;
   double sol[256];
   DG_CUDA(cudaMemcpyAsync(&flag, S->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DG_CUDA(cudaMemcpyAsync(sol, S->solve_out, 4 * M.nsolve * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaMemcpyAsync(sol, S->solve_out, 4 * M[0].nsolve * sizeof(double), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
-  const int status = member_finish(M, sol, flag);
-  if (stats) *stats = M.st;
+  const int status = member_finish(M[0], sol, flag);
+  if (stats) *stats = M[0].st;
   return status;
 }
 
 namespace dg {
 namespace {
-
-// Parallel branches for the per-member phases of a captured batch step: each
-// segment of member work forks from the main stream, member i runs on branch
-// i mod K, and the branches join before the next batched solve.
-struct Branches {
-  std::vector<cudaStream_t> st;
-  std::vector<cudaEvent_t> join;
-  cudaEvent_t fork = nullptr;
-};
 
 // Krylov method of a member's solves inside a batched launch: krylov = AUTO
 // takes the mesh's tuned persistent form, else Chebyshev (a batch cannot time
@@ -807,56 +916,26 @@ int solve_all(dg_ctx* ctx, std::vector<Member>& M, const dg_solver_opts& o, int 
   return DG_OK;
 }
 
-// One IMEX-RK2 step of every member: the per-member phases (on branches if
-// given) between the batched solves of each Picard iteration.
-int batch_phases(dg_ctx* ctx, std::vector<Member>& M, const dg_solver_opts& o, int* err, cudaStream_t s,
-                 const Branches* br) {
+// One IMEX-RK2 step of every member: each phase is one packed launch per
+// operation over all members (per (dimension, degree) group for the DG
+// operators), between the batched solves of each Picard iteration.
+int batch_phases(dg_ctx* ctx, std::vector<Member>& M, const dg_solver_opts& o, int* err, cudaStream_t s) {
   int rc;
-  // run body(member, stream) for every member, forked over the branches
-  auto segment = [&](auto&& body) -> int {
-    const int K = br ? (int)br->st.size() : 0;
-    if (K == 0) {
-      for (auto& mm : M)
-        if ((rc = body(mm, s)) != DG_OK) return rc;
-      return DG_OK;
-    }
-    DG_CUDA(cudaEventRecord(br->fork, s));
-    for (int k = 0; k < K; ++k) DG_CUDA(cudaStreamWaitEvent(br->st[k], br->fork, 0));
-    for (size_t i = 0; i < M.size(); ++i)
-      if ((rc = body(M[i], br->st[i % K])) != DG_OK) return rc;
-    for (int k = 0; k < K; ++k) {
-      DG_CUDA(cudaEventRecord(br->join[k], br->st[k]));
-      DG_CUDA(cudaStreamWaitEvent(s, br->join[k], 0));
-    }
-    return DG_OK;
-  };
 #define RUN(x)                          \
   do {                                  \
     if ((rc = (x)) != DG_OK) return rc; \
   } while (0)
-  RUN(segment([&](Member& mm, cudaStream_t t) {
-    int r;
-    if ((r = phase_stage1(mm, t)) != DG_OK) return r;
-    if ((r = phase_stage_begin(mm, 1, t)) != DG_OK) return r;
-    return phase_picard_pre(mm, 1, t);
-  }));
+  RUN(phase_stage1(ctx, M, s));
   for (int i = 1; i <= 2; ++i) {
+    RUN(phase_stage_begin(ctx, M, i, s));
     for (int it = 0; it < o.picard; ++it) {
+      RUN(phase_picard_pre(ctx, M, i, s));
       RUN(solve_all(ctx, M, o, i, err, s));
-      const bool last = it == o.picard - 1;
-      RUN(segment([&](Member& mm, cudaStream_t t) {
-        int r;
-        if ((r = phase_picard_post(mm, i, t)) != DG_OK) return r;
-        if (!last) return phase_picard_pre(mm, i, t);
-        if ((r = phase_stage_end(mm, i, t)) != DG_OK) return r;
-        if (i == 1) {
-          if ((r = phase_stage_begin(mm, 2, t)) != DG_OK) return r;
-          return phase_picard_pre(mm, 2, t);
-        }
-        return phase_final(mm, t);
-      }));
+      RUN(phase_picard_post(ctx, M, i, s));
     }
+    RUN(phase_stage_end(ctx, M, i, s));
   }
+  RUN(phase_final(ctx, M, s));
 #undef RUN
   return DG_OK;
 }
@@ -907,7 +986,7 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* const* meshes, d
   ProfScope step_scope(ctx, DG_PROF_STEP, s);
   int* err = ctx->d_batch_err;
   DG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-  if ((rc = batch_phases(ctx, M, M[0].o, err, s, nullptr)) != DG_OK) return rc;
+  if ((rc = batch_phases(ctx, M, M[0].o, err, s)) != DG_OK) return rc;
   // read every member's flag and solve results with one synchronisation
   std::vector<int> flags(n, 0);
   std::vector<double> sol((size_t)n * 256, 0.0);
@@ -929,7 +1008,6 @@ struct dg_batch_plan {
   std::vector<dg::Member> M;
   int n = 0;
   cudaStream_t cs = nullptr;  // capture stream
-  dg::Branches br;
   dg::BatchArena arena;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -943,9 +1021,6 @@ extern "C" int dg_batch_plan_destroy(dg_batch_plan* P) {
   cudaSetDevice(P->ctx->device);
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
-  for (auto st : P->br.st) cudaStreamDestroy(st);
-  for (auto ev : P->br.join) cudaEventDestroy(ev);
-  if (P->br.fork) cudaEventDestroy(P->br.fork);
   if (P->cs) cudaStreamDestroy(P->cs);
   if (P->arena.dev) cudaFree(P->arena.dev);
   if (P->h_flags) cudaFreeHost(P->h_flags);
@@ -980,16 +1055,6 @@ extern "C" int dg_batch_plan_create(dg_ctx* ctx, int n, const dg_mesh* const* me
   };
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking);
-  const int K = std::min(n, 16);
-  for (int k = 0; k < K && e == cudaSuccess; ++k) {
-    cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
-    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) P->br.st.push_back(st);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) P->br.join.push_back(ev);
-  }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->br.fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost(&P->h_flags, (n + 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&P->h_sol, (size_t)n * 256 * sizeof(double));
   // argument tables of the batched launches: per launch at most one table of
@@ -1013,7 +1078,7 @@ extern "C" int dg_batch_plan_create(dg_ctx* ctx, int n, const dg_mesh* const* me
     rc = DG_OK;
     e = cudaMemsetAsync(err, 0, sizeof(int), P->cs);
     if (e != cudaSuccess) rc = cuda_fail(e, "batch plan capture");
-    if (rc == DG_OK) rc = batch_phases(ctx, P->M, o, err, P->cs, &P->br);
+    if (rc == DG_OK) rc = batch_phases(ctx, P->M, o, err, P->cs);
     for (int i = 0; i < n && rc == DG_OK; ++i) {
       e = cudaMemcpyAsync(&P->h_flags[i], P->M[i].S->flag, sizeof(int), cudaMemcpyDeviceToHost, P->cs);
       if (e == cudaSuccess)

@@ -452,11 +452,13 @@ def tiny_case(
 def request_case(seed: int, dof_lo: float = 1e4, dof_hi: float = 5e6) -> Case:
     """One serving request: 2D or 3D (50/50), degree 2-5, DoF log-uniform in [dof_lo, dof_hi].
 
-    The base grid is sized to the drawn DoF (x by y by z/2 cells) at a fixed
-    resolution of 1 km per base cell, so the domain grows with the request and
-    every request stays resolved (coarse cells of several km at low degree,
-    run for hundreds of steps, go unstable in the collocated discretisation:
-    the aliasing of the nonlinear fluxes is not damped).  A seeded hill of up
+    The base grid is sized to the drawn DoF (x by y by z/2 cells) with base
+    cells of 1 km (finer when the domain would exceed 20 km in height, where the
+    constant-N atmosphere's pressure runs out), so the domain grows with small
+    requests and every request stays resolved (coarse cells of several km at
+    low degree, run for hundreds of steps, go unstable in the collocated
+    discretisation: the aliasing of the nonlinear fluxes is not damped).  A
+    seeded hill of up
     to a fifth of the domain height (at most 1 km) and half-width a tenth of
     the domain length, a bubble (radius a fifth of the height) or an inflow,
     0 or 1 refinement level near the ground.
@@ -467,13 +469,13 @@ def request_case(seed: int, dof_lo: float = 1e4, dof_hi: float = 5e6) -> Case:
     dof = float(np.exp(rng.uniform(np.log(dof_lo), np.log(dof_hi))))
     V = dim + 2
     cells = dof / (V * (degree + 1) ** dim)
-    h = 1e3
     if dim == 2:
         nx = max(4, 2 * int(round(math.sqrt(2.0 * cells) / 2)))
         base, periodic = (nx, nx // 2), (True, False)
     else:
         nx = max(4, 2 * int(round((2.0 * cells) ** (1.0 / 3.0) / 2)))
         base, periodic = (nx, nx, nx // 2), (True, True, False)
+    h = min(1e3, 20e3 / base[-1])
     extent = tuple(b * h for b in base)
     refine = bool(rng.uniform() < 0.5)
     dz = extent[-1] / base[-1]

@@ -68,6 +68,29 @@ __device__ __forceinline__ double rsqrt64(double x) {
   return y;
 }
 
+// 2^-l for a refinement level 0 <= l < 127, built from its IEEE-754 fields
+template <typename T>
+__device__ __forceinline__ T pow2_neg(int l);
+template <>
+__device__ __forceinline__ float pow2_neg<float>(int l) {
+  return __int_as_float((127 - l) << 23);
+}
+template <>
+__device__ __forceinline__ double pow2_neg<double>(int l) {
+  return __longlong_as_double((long long)(1023 - l) << 52);
+}
+// correctly rounded 1/x (the value of 1 / x), through CUDA's reciprocal intrinsics
+template <typename T>
+__device__ __forceinline__ T recip(T x);
+template <>
+__device__ __forceinline__ float recip<float>(float x) {
+  return __frcp_rn(x);
+}
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  return __drcp_rn(x);
+}
+
 // Metric terms of node id of a cell whose x (and y) are affine, from the
 // heights above the computational coordinates in shared memory (sz: the
 // cell's NC values) and the cell's half widths (hb * 2^-level per axis):
@@ -80,7 +103,7 @@ template <int DIM, int DEG, typename T>
 __device__ __forceinline__ void metric_from_z(const MeshView<T>& mv, int64_t c, const T* sz, const int* id,
                                               const T* sD, T (&Ja)[DIM][DIM], T& invJ) {
   constexpr int N = DEG + 1;
-  const T scale = T(1) / T(1 << mv.cell_level[c]);
+  const T scale = pow2_neg<T>(mv.cell_level[c]);
   T zd[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
@@ -100,7 +123,7 @@ __device__ __forceinline__ void metric_from_z(const MeshView<T>& mv, int64_t c, 
     Ja[0][1] = T(0);
     Ja[1][0] = -zd[0];
     Ja[1][1] = ax;
-    invJ = T(1) / (ax * zd[1]);
+    invJ = recip<T>(ax * zd[1]);
   } else {
     const T ay = mv.hb[1] * scale;
     Ja[0][0] = ay * zd[DIM - 1];
@@ -112,7 +135,7 @@ __device__ __forceinline__ void metric_from_z(const MeshView<T>& mv, int64_t c, 
     Ja[DIM - 1][0] = -ay * zd[0];
     Ja[DIM - 1][1] = -ax * zd[1];
     Ja[DIM - 1][DIM - 1] = ax * ay;
-    invJ = T(1) / (ax * ay * zd[DIM - 1]);
+    invJ = recip<T>(ax * ay * zd[DIM - 1]);
   }
 }
 

@@ -25,8 +25,10 @@ namespace dg {
 // Interpolated coarse value of an NV-component field at fine face node k of
 // subface position s, from the coarse cell's values on its face lfp:
 // X[v * vstride + cbase + face_node(lfp, j)] (global memory or a shared tile).
+// (Node indices are below 2^31, so they are 32-bit here; the field offsets
+// v * vstride are taken once per field.)
 template <int DIM, int DEG, typename T, int NV>
-__device__ __forceinline__ void coarse_interp(const T* __restrict__ X, int64_t vstride, int64_t cbase, int lfp,
+__device__ __forceinline__ void coarse_interp(const T* __restrict__ X, int64_t vstride, int cbase, int lfp,
                                               int s, int k, const T* sI, T* out) {
   constexpr int N = DEG + 1;
 #pragma unroll
@@ -34,9 +36,9 @@ __device__ __forceinline__ void coarse_interp(const T* __restrict__ X, int64_t v
   if (DIM == 2) {
     const T* Is = sI + s * N * N + k * N;
     for (int j = 0; j < N; ++j) {
-      const int64_t ic = cbase + face_node<DIM, DEG>(lfp, j);
+      const int ic = cbase + face_node<DIM, DEG>(lfp, j);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) out[v] += Is[j] * X[(int64_t)v * vstride + ic];
+      for (int v = 0; v < NV; ++v) out[v] += Is[j] * (X + v * vstride)[ic];
     }
   } else {
     const int k1 = k % N, k2 = k / N;
@@ -45,10 +47,10 @@ __device__ __forceinline__ void coarse_interp(const T* __restrict__ X, int64_t v
 #pragma unroll 1
     for (int j2 = 0; j2 < N; ++j2)
       for (int j1 = 0; j1 < N; ++j1) {
-        const int64_t ic = cbase + face_node<DIM, DEG>(lfp, j1 + N * j2);
+        const int ic = cbase + face_node<DIM, DEG>(lfp, j1 + N * j2);
         const T wgt = I1[j1] * I2[j2];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) out[v] += wgt * X[(int64_t)v * vstride + ic];
+        for (int v = 0; v < NV; ++v) out[v] += wgt * (X + v * vstride)[ic];
       }
   }
 }
@@ -161,11 +163,11 @@ __device__ __forceinline__ void coarse_pass(const MeshView<T>& mv, bool active, 
 // term) where the node is interior along the axis.  Loaded early so that
 // their latency overlaps other work.
 template <int DIM, int DEG, typename T>
-__device__ __forceinline__ void load_face_links(const MeshView<T>& mv, int64_t c, const int* id, int* links) {
+__device__ __forceinline__ void load_face_links(const MeshView<T>& mv, int c, const int* id, int* links) {
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     links[a] = 3;
-    if (id[a] == 0 || id[a] == DEG) links[a] = mv.cell_link[c * 2 * DIM + 2 * a + (id[a] == DEG ? 1 : 0)];
+    if (id[a] == 0 || id[a] == DEG) links[a] = mv.cell_link[2 * DIM * c + 2 * a + (id[a] == DEG ? 1 : 0)];
   }
 }
 
@@ -177,13 +179,13 @@ template <int DIM, int DEG, typename T, int NV>
 __device__ __forceinline__ void other_trace(const T* __restrict__ X, int64_t vstride, int link, int a, const int* id,
                                             const T* sI, T* out) {
   constexpr int NC = Shape<DIM, DEG>::NC;
-  const int64_t nb = (int64_t)((unsigned)link >> 4);
+  const int nb = (int)((unsigned)link >> 4);
   const int lfo = 2 * a + (id[a] == DEG ? 0 : 1);  // the neighbour's face is the opposite one
   const int kt = tangential_index<DIM, DEG>(a, id);
   if ((link & 3) == 0) {
-    const int64_t o = nb * NC + face_node<DIM, DEG>(lfo, kt);
+    const int o = nb * NC + face_node<DIM, DEG>(lfo, kt);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) out[v] = X[(int64_t)v * vstride + o];
+    for (int v = 0; v < NV; ++v) out[v] = (X + v * vstride)[o];
   } else {
     coarse_interp<DIM, DEG, T, NV>(X, vstride, nb * NC, lfo, (link >> 2) & 3, kt, sI, out);
   }
@@ -209,10 +211,10 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int64_t c = batch * CPB + lc;
+  const int c = (int)batch * CPB + lc;
   const bool active = (lc < CPB) && (c < mv.n_cells);
   const int64_t Nn = mv.n_nodes;
-  const int64_t idx = c * NC + i;
+  const int idx = c * NC + i;
   int id[3] = {i % N, (i / N) % N, i / (N * N)};
   int links[DIM];
   T Jl[DIM][DIM];
@@ -231,7 +233,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
+        for (int b = 0; b < DIM; ++b) Jl[a][b] = (mv.Ja + (a * DIM + b) * Nn)[idx];
       scale = mv.invJ[idx] * (h ? h[idx] : T(1));
     }
     // neighbour traces: issued before the barrier, their latency overlaps it
@@ -289,7 +291,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
       T s = facc[b] * iwend;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) s += Jl[a][b] * dp[a];
-      g[(int64_t)b * Nn + idx] = s * scale;
+      (g + b * Nn)[idx] = s * scale;
     }
   }
   __syncthreads();
@@ -310,10 +312,10 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int64_t c = batch * CPB + lc;
+  const int c = (int)batch * CPB + lc;
   const bool active = (lc < CPB) && (c < mv.n_cells);
   const int64_t Nn = mv.n_nodes;
-  const int64_t idx = c * NC + i;
+  const int idx = c * NC + i;
   int id[3] = {i % N, (i / N) % N, i / (N * N)};
   int links[DIM];
   T ft[DIM];  // Ja^a . f for each axis a
@@ -324,7 +326,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch, &nmax);
   if (active) {
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) fv[b] = fld[(int64_t)b * Nn + idx];
+    for (int b = 0; b < DIM; ++b) fv[b] = (fld + b * Nn)[idx];
     load_face_links<DIM, DEG, T>(mv, c, id, links);
     if (HELM) pv = p[idx];
     if (GZ) {
@@ -334,7 +336,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) Jl[a][b] = mv.Ja[(int64_t)(a * DIM + b) * Nn + idx];
+        for (int b = 0; b < DIM; ++b) Jl[a][b] = (mv.Ja + (a * DIM + b) * Nn)[idx];
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         T s = T(0);
@@ -394,13 +396,13 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, bmask, nmax, sII + 2 * N * N, T(-1), sJ, &facc,
                               [&](int f, int lf, int s, int q, int j, T* buf) {
                                 const int64_t t = (int64_t)(f + s) * NF + q;
-                                const int64_t im = mv.fnode_m[t];
+                                const int im = mv.fnode_m[t];
                                 T fc[DIM];
                                 coarse_interp<DIM, DEG, T, DIM>(fld, Nn, c * NC, lf, s, q, sII, fc);
                                 T sum = T(0);
 #pragma unroll
                                 for (int b = 0; b < DIM; ++b)
-                                  sum += (fld[(int64_t)b * Nn + im] + fc[b]) * mv.fn[(int64_t)b * total + t];
+                                  sum += ((fld + b * Nn)[im] + fc[b]) * (mv.fn + b * total)[t];
                                 buf[lc * NP + j] = T(0.5) * mv.fsj[t] * sum;
                               });
   if (active) {

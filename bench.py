@@ -314,6 +314,23 @@ def precision_forms_3d(dg, torch, case_name="hill3d", steps=2, inner_tol=1e-6):
     return out
 
 
+def cta_pass_summary(grad_ns, div_ns, coarse, steps):
+    """Per-CTA pass clocks of the persistent Chebyshev solve, per step: the slowest CTA against the
+    mean one, split by whether the CTA's cell batch holds a coarse side (the 2:1 face work)."""
+    used = (grad_ns + div_ns) > 0
+    if not used.any():
+        return None
+    g, d, c = grad_ns[used] / 1e3 / steps, div_ns[used] / 1e3 / steps, coarse[used] > 0
+    out = {"ctas": int(used.sum()), "coarse_ctas": int(c.sum()),
+           "grad_max": float(g.max()), "grad_mean": float(g.mean()),
+           "div_max": float(d.max()), "div_mean": float(d.mean())}
+    for name, sel in (("coarse", c), ("plain", ~c)):
+        if sel.any():
+            out["grad_mean_" + name] = float(g[sel].mean())
+            out["div_mean_" + name] = float(d[sel].mean())
+    return out
+
+
 def spectrum_of(state):
     """Condition number of the state's last Helmholtz operator: the power-iteration upper bound the
     Chebyshev solves keep (less its 5% margin) over the lower bound 1/(gamma-1) = 2.5 (0 if the
@@ -670,6 +687,7 @@ def main():
     launches = dg.dg_launch_count(ctx) - launches0
     prof = dg.dg_profile_read(ctx)
     phases = dg.dg_profile_read_gmres_phases(ctx)
+    cta_passes = cta_pass_summary(*dg.dg_profile_read_cta_passes(ctx), args.steps)
     dg.dg_profile_enable(ctx, False)
     total_ms = sum(times)
     if world > 1:
@@ -828,6 +846,7 @@ def main():
         "breakdown_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "gmres_phase_us_per_iteration": {k: 1e3 * v / max(1, phases["iterations"]) for k, v in phases.items()
                                          if k not in ("iterations", "second_passes")},
+        "cta_pass_us_per_step": cta_passes,
         "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in stats),
         "helmholtz_kappa": kappa,
         "autotuned_solver": tuned,

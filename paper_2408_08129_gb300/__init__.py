@@ -36,6 +36,7 @@ from .api import (  # noqa: F401
     dg_peak_fma,
     dg_profile_enable,
     dg_profile_read,
+    dg_profile_read_cta_passes,
     dg_profile_read_gmres_phases,
     dg_profile_reset,
     imex_rk2_step,

@@ -108,6 +108,7 @@ def _load():
         "dg_profile_reset": (c_int, [P]),
         "dg_launch_count": (c_int, [P, P]),
         "dg_profile_read_gmres_phases": (c_int, [P, P]),
+        "dg_profile_read_cta_passes": (c_int, [P, P, P, P, c_int]),
         "dg_mesh_create": (c_int, [P, ctypes.POINTER(MeshDesc), ctypes.POINTER(P)]),
         "dg_mesh_destroy": (c_int, [P]),
         "dg_mesh_get_info": (c_int, [P, ctypes.POINTER(MeshInfo)]),

@@ -219,6 +219,16 @@ def dg_profile_read_gmres_phases(ctx):
     return out
 
 
+def dg_profile_read_cta_passes(ctx, max_ctas=512):
+    """Per-CTA pass clocks of the persistent Chebyshev solves: (grad_ns, div_ns, coarse) arrays."""
+    g = np.zeros(max_ctas)
+    d = np.zeros(max_ctas)
+    c = np.zeros(max_ctas, dtype=np.int32)
+    check(lib.dg_profile_read_cta_passes(ctx.handle, g.ctypes.data, d.ctypes.data, c.ctypes.data, int(max_ctas)),
+          "dg_profile_read_cta_passes")
+    return g, d, c
+
+
 def dg_math_selftest(op, x, y, stream=None):
     """Device self-test of the library's FP64 math (op 0: the Newton 1/sqrt); x, y: CUDA float64 tensors."""
     check(lib.dg_math_selftest(int(op), _ptr(x), _ptr(y), x.numel(), _stream(stream)), "dg_math_selftest")

@@ -1,4 +1,5 @@
 // Context, error reporting and the operator entry points of the C ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -11,6 +12,8 @@ namespace dg {
 
 namespace {
 thread_local std::string g_last_error;
+// profiling words on the device: 16 phase accumulators, then 3 x 512 per-CTA pass clocks
+constexpr size_t kPhaseWords = 16 + 3 * 512;
 }
 
 int fail(int status, const std::string& msg) {
@@ -166,8 +169,8 @@ extern "C" int dg_profile_enable(dg_ctx* c, int on) {
     for (auto& e : c->ev_pool) DG_CUDA(cudaEventCreate(&e));
   }
   if (on && !c->d_phase) {
-    DG_CUDA(cudaMalloc(&c->d_phase, 16 * sizeof(unsigned long long)));
-    DG_CUDA(cudaMemset(c->d_phase, 0, 16 * sizeof(unsigned long long)));
+    DG_CUDA(cudaMalloc(&c->d_phase, kPhaseWords * sizeof(unsigned long long)));
+    DG_CUDA(cudaMemset(c->d_phase, 0, kPhaseWords * sizeof(unsigned long long)));
   }
   if (!on && c->prof) prof_resolve(c);
   c->prof = on != 0;
@@ -210,10 +213,26 @@ extern "C" int dg_profile_read_gmres_phases(dg_ctx* c, double* ns) {
   return DG_OK;
 }
 
+extern "C" int dg_profile_read_cta_passes(dg_ctx* c, double* grad_ns, double* div_ns, int* coarse, int max_ctas) {
+  if (!c || max_ctas < 0 || (max_ctas > 0 && (!grad_ns || !div_ns || !coarse))) return fail(DG_EINVAL, "bad arguments");
+  std::vector<unsigned long long> h(kPhaseWords, 0ull);
+  if (c->d_phase) {
+    DG_CUDA(cudaDeviceSynchronize());
+    DG_CUDA(cudaMemcpy(h.data(), c->d_phase, kPhaseWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  }
+  const int n = std::min(max_ctas, 512);
+  for (int i = 0; i < n; ++i) {
+    grad_ns[i] = (double)h[16 + i];
+    div_ns[i] = (double)h[16 + 512 + i];
+    coarse[i] = (int)h[16 + 1024 + i];
+  }
+  return DG_OK;
+}
+
 extern "C" int dg_profile_reset(dg_ctx* c) {
   if (!c) return fail(DG_EINVAL, "null context");
   prof_resolve(c);
-  if (c->d_phase) DG_CUDA(cudaMemset(c->d_phase, 0, 16 * sizeof(unsigned long long)));
+  if (c->d_phase) DG_CUDA(cudaMemset(c->d_phase, 0, kPhaseWords * sizeof(unsigned long long)));
   for (int i = 0; i < DG_PROF_N; ++i) {
     c->prof_ms[i] = 0.0;
     c->prof_n[i] = 0;

@@ -51,7 +51,9 @@ struct GmresPArgs {
   double* gv;             // [dim][n] gradient scratch (doubles), reused as TK
   double* partial;        // >= 2 x (CTAs of the solve) doubles
   double* out;            // [4]: iterations, relative residual, converged (0/1), ||b||
-  unsigned long long* phase;  // optional [16] ns per phase accumulated by block 0 (NULL = off)
+  unsigned long long* phase;  // optional [16] ns per phase accumulated by block 0, then per CTA
+                              // [512] gradient-pass ns, [512] divergence-pass ns and [512] flags
+                              // (batch holds a coarse side) of the Chebyshev solve (NULL = off)
   double alpha;           // (a_ii dt)^2
   double tol;             // target ||b - A x|| / ||b|| (checked on the FP64 residual)
   double inner_tol;       // TK = float: residual reduction per cycle
@@ -1144,6 +1146,7 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
 // recomputed at every restart; TK = float restarts whenever the residual has
 // dropped by inner_tol (iterative refinement).
 constexpr int kPowerIters = 24;
+constexpr int kCtaClocks = 512;  // CTAs with a per-CTA pass clock
 constexpr double kLmaxMargin = 1.05;
 
 // The GMRES fallback of the Chebyshev solve, kept out of line: inlined, its
@@ -1358,6 +1361,12 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     double rho = rho0;
     const int64_t nb = (a.mvk.n_cells + S::CPB - 1) / S::CPB;
     bool have_prev = false;  // residual partials of the previous step are waiting in a.partial
+    // per-CTA pass clocks (profiling): own gradient and divergence work, before the grid barriers
+    unsigned long long* cta_clock = a.phase ? a.phase + 16 : nullptr;
+    if (cta_clock && sg.rank < kCtaClocks) {
+      const unsigned cm = sg.rank < nb ? batch_coarse_mask<DIM, DEG, TK>(a.mvk, sg.rank) : 0u;
+      if (threadIdx.x == 0) cta_clock[2 * kCtaClocks + sg.rank] = cm ? 1ull : 0ull;
+    }
     while (true) {
       // the next step's recurrence coefficients, by one thread, while the others start the
       // gradient pass (the FP64 division is off the critical path); read after the grid
@@ -1375,8 +1384,10 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       float pv = 0.0f;
       if (have_prev)
         for (int i = threadIdx.x; i < G; i += blockDim.x) pv += ((const float*)a.partial)[i];
+      const unsigned long long tg0 = cta_clock ? PhaseClock::now() : 0ull;
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         grad_cell_batch<DIM, DEG, TK>(a.mvk, d, a.hk, gvk, bt, scellk, sJk, sDk, sIIk);
+      if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks) cta_clock[sg.rank] += PhaseClock::now() - tg0;
       if (have_prev) {
         const float rn2 = block_allsum_f(pv, sred);  // (||r|| / beta)^2
         pc.mark(PH_UPDATE);
@@ -1410,9 +1421,12 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
           racc += rs * rs;
         }
       };
+      const unsigned long long td0 = cta_clock ? PhaseClock::now() : 0ull;
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         div_cell_batch<DIM, DEG, TK, true>(a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi, bt, scellk, sJk, sDwk,
                                            sIIk);
+      if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks)
+        cta_clock[kCtaClocks + sg.rank] += PhaseClock::now() - td0;
       if (want) {
         const float t = block_sum_f(racc, sred);
         if (threadIdx.x == 0) ((float*)a.partial)[sg.rank] = t;  // FP32 partials for the stop test

@@ -321,13 +321,13 @@ def cta_pass_summary(grad_ns, div_ns, coarse, steps):
     if not used.any():
         return None
     g, d, c = grad_ns[used] / 1e3 / steps, div_ns[used] / 1e3 / steps, coarse[used] > 0
-    out = {"ctas": int(used.sum()), "coarse_ctas": int(c.sum()),
-           "grad_max": float(g.max()), "grad_mean": float(g.mean()),
-           "div_max": float(d.max()), "div_mean": float(d.mean())}
+    out = {"ctas": int(used.sum()), "coarse_ctas": int(c.sum())}
     for name, sel in (("coarse", c), ("plain", ~c)):
         if sel.any():
             out["grad_mean_" + name] = float(g[sel].mean())
+            out["grad_max_" + name] = float(g[sel].max())
             out["div_mean_" + name] = float(d[sel].mean())
+            out["div_max_" + name] = float(d[sel].max())
     return out
 
 
@@ -686,8 +686,6 @@ def main():
             times.append(ev0.elapsed_time(ev1))
     launches = dg.dg_launch_count(ctx) - launches0
     prof = dg.dg_profile_read(ctx)
-    phases = dg.dg_profile_read_gmres_phases(ctx)
-    cta_passes = cta_pass_summary(*dg.dg_profile_read_cta_passes(ctx), args.steps)
     dg.dg_profile_enable(ctx, False)
     total_ms = sum(times)
     if world > 1:
@@ -697,6 +695,17 @@ def main():
     value = whole_job_value(world, dof, args.steps, total_ms)
 
     U64 = state.download()
+    # a few more (untimed) steps with the clocks inside the persistent solves on: per-phase time
+    # as seen by block 0, and every CTA's own gradient and divergence passes
+    clock_steps = max(1, min(args.steps, 5))
+    dg.dg_profile_reset(ctx)
+    dg.dg_profile_enable(ctx, 2)
+    for _ in range(clock_steps):
+        dg.imex_rk2_step(ctx, mesh, state, case.dt, opts)
+    phases = dg.dg_profile_read_gmres_phases(ctx)
+    cta_passes = cta_pass_summary(*dg.dg_profile_read_cta_passes(ctx), clock_steps)
+    dg.dg_profile_enable(ctx, False)
+    state.upload(U64)
     kappa = spectrum_of(state)
 
     Ubg = torch.empty(mesh.shape(), dtype=torch.float64, device="cuda")
@@ -768,7 +777,7 @@ def main():
                             for v in range(mesh.n_vars))}
             # one more (untimed) step with the per-phase clock of the persistent solve on
             dg.dg_profile_reset(ctx)
-            dg.dg_profile_enable(ctx, True)
+            dg.dg_profile_enable(ctx, 2)
             dg.imex_rk2_step(ctx, mesh, state, case.dt, o)
             ph = dg.dg_profile_read_gmres_phases(ctx)
             dg.dg_profile_enable(ctx, False)

@@ -98,14 +98,16 @@ typedef enum {
 } dg_prof_category;
 /* Turn event timing on (1) or off (0) for every call made with this context.
  * Events are recorded on the stream of each call; the overhead is one event
- * pair per operator launch. */
+ * pair per operator launch.  on = 2 also turns on the clocks inside the
+ * persistent solves (dg_profile_read_gmres_phases, dg_profile_read_cta_passes),
+ * which cost a little time of their own. */
 int dg_profile_enable(dg_ctx* ctx, int on);
 /* Synchronise the device, then copy the accumulated milliseconds and call
  * counts per category into ms[DG_PROF_N] and counts[DG_PROF_N] (host arrays). */
 int dg_profile_read(dg_ctx* ctx, double* ms, long long* counts);
 int dg_profile_reset(dg_ctx* ctx);
 /* Nanoseconds spent in each phase of the fused GMRES solves while profiling
- * was on, as seen by block 0 (a phase that ends at a grid barrier includes the
+ * was on at level 2, as seen by block 0 (a phase that ends at a grid barrier includes the
  * wait for the slowest block), into ns[16]: 1 gradient (one cell pass with its
  * face terms), 3 divergence (the same), 4 wait at the barrier after the
  * Gram-Schmidt dots, 5 wait at the barrier after the basis update, 6 second
@@ -114,7 +116,7 @@ int dg_profile_reset(dg_ctx* ctx);
  * column and Givens rotation, 12 update coefficients, 13 basis update (work);
  * ns[14] = second passes, ns[15] = GMRES iterations.  Synchronises the device. */
 int dg_profile_read_gmres_phases(dg_ctx* ctx, double* ns);
-/* Per-CTA clocks of the Chebyshev solves while profiling was on: for CTA i <
+/* Per-CTA clocks of the Chebyshev solves while profiling was on at level 2: for CTA i <
  * max_ctas (at most 512) of the persistent launch, the nanoseconds of its own
  * gradient passes (grad_ns[i]) and divergence passes (div_ns[i]), summed over
  * the steps and solves, before the grid barriers; coarse[i] = 1 if its cell

@@ -191,7 +191,7 @@ PROF_CATEGORIES = {0: "explicit", 1: "helmholtz", 2: "grad", 3: "div", 4: "krylo
 
 
 def dg_profile_enable(ctx, on=True):
-    check(lib.dg_profile_enable(ctx.handle, 1 if on else 0), "dg_profile_enable")
+    check(lib.dg_profile_enable(ctx.handle, int(on)), "dg_profile_enable")
 
 
 def dg_profile_reset(ctx):

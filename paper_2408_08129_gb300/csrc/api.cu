@@ -174,6 +174,7 @@ extern "C" int dg_profile_enable(dg_ctx* c, int on) {
   }
   if (!on && c->prof) prof_resolve(c);
   c->prof = on != 0;
+  c->prof_clocks = on >= 2;
   return DG_OK;
 }
 

@@ -87,6 +87,18 @@ struct MeshView {
   const T* bg_tab;
   T bg_z0, bg_idz;
   int bg_m;
+  // Coarse sides of the 2:1 faces per cell batch of the implicit cell passes
+  // (CPB consecutive cells): batch b's entries are [cb_start[b], cb_start[b+1]),
+  // per cell in order, per coarse local face in order (a slot), per fine point
+  // j = s NF + q of the face's subfaces; ce_meta = lc | lf << 6 | j << 9,
+  // ce_node = the fine-side node, ce_w[b * n_ce + e] = 1/2 |N| n_b at it.
+  // cell_coarse[c] = coarse-face mask | (batch slot of the cell's first one) << 8.
+  const int* cb_start;
+  const int* cell_coarse;
+  const int* ce_meta;
+  const int* ce_node;
+  const T* ce_w;
+  int n_ce;
 };
 
 }  // namespace dg
@@ -116,6 +128,7 @@ struct dg_ctx {
   cudaStream_t own_stream = nullptr;
   // optional per-operator timing with CUDA events (see dg_profile_*)
   bool prof = false;
+  bool prof_clocks = false;  // in-kernel phase and per-CTA clocks of the persistent solves too
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_next = 0;
   std::vector<std::pair<int, size_t>> ev_pending;  // (category, index of the start event)

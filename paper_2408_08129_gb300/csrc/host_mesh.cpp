@@ -609,9 +609,54 @@ int build_mesh(dg_mesh* m) {
   for (int64_t c = 0; c < K; ++c)
     for (int lf = 0; lf < 2 * dim; ++lf)
       if ((cell_face[c * 2 * dim + lf] & 3) == 2) cell_cmask[c] |= 1 << lf;
-  const size_t n_int = (size_t)5 * nf + 2 * cell_face.size() + 2 * (size_t)nf * NF + 2 * (size_t)K;
+  // Coarse sides of the 2:1 faces listed per cell batch (the batches of the one-thread-per-node
+  // cell passes: cpb consecutive cells), for the implicit passes: batch b's entries are
+  // [cb_start[b], cb_start[b+1]), per cell of the batch in order, per coarse local face in
+  // order (a slot), one entry per fine point j = s NF + q of the face's subfaces: ce_meta =
+  // lc | lf << 6 | j << 9, ce_node = the fine node, ce_w[b] = 1/2 |N| n_b there (fsj fn / 2).
+  // cell_coarse[c] = cmask | (batch slot of the cell's first coarse face) << 8.
+  const int cpb = nc >= 256 ? 1 : 256 / nc;
+  const int nsubf = 1 << (dim - 1), np_c = nsubf * NF;
+  const int64_t nbat = (K + cpb - 1) / cpb;
+  std::vector<int> cb_start((size_t)nbat + 1, 0), cell_coarse(K, 0), ce_meta, ce_node;
+  std::vector<double> ce_w;
+  for (int64_t bt = 0; bt < nbat; ++bt) {
+    cb_start[bt] = (int)ce_meta.size();
+    int slot = 0;
+    for (int lc = 0; lc < cpb && bt * cpb + lc < K; ++lc) {
+      const int64_t c = bt * cpb + lc;
+      cell_coarse[c] = cell_cmask[c] | (slot << 8);
+      for (int lf = 0; lf < 2 * dim; ++lf) {
+        if (!((cell_cmask[c] >> lf) & 1)) continue;
+        const int f = cell_face[c * 2 * dim + lf] >> 2;
+        for (int j = 0; j < np_c; ++j) {
+          const size_t t = (size_t)(f + j / NF) * NF + (size_t)(j % NF);
+          ce_meta.push_back(lc | (lf << 6) | (j << 9));
+          ce_node.push_back(fnode_m[t]);
+        }
+        ++slot;
+      }
+    }
+  }
+  cb_start[nbat] = (int)ce_meta.size();
+  const size_t n_ce = ce_meta.size();
+  ce_w.assign((size_t)dim * n_ce, 0.0);
+  for (int64_t bt = 0, e = 0; bt < nbat; ++bt)
+    for (int lc = 0; lc < cpb && bt * cpb + lc < K; ++lc) {
+      const int64_t c = bt * cpb + lc;
+      for (int lf = 0; lf < 2 * dim; ++lf) {
+        if (!((cell_cmask[c] >> lf) & 1)) continue;
+        const int f = cell_face[c * 2 * dim + lf] >> 2;
+        for (int j = 0; j < np_c; ++j, ++e) {
+          const size_t t = (size_t)(f + j / NF) * NF + (size_t)(j % NF);
+          for (int b = 0; b < dim; ++b) ce_w[(size_t)b * n_ce + e] = 0.5 * fsj[t] * fn[(size_t)b * nf * NF + t];
+        }
+      }
+    }
+  const size_t n_int = (size_t)5 * nf + 2 * cell_face.size() + 2 * (size_t)nf * NF + 2 * (size_t)K +
+                       cb_start.size() + cell_coarse.size() + 2 * n_ce;
   const size_t n_real = (size_t)dim * dim * m->Nn + 5 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size() +
-                        (size_t)K + bgtab.size();
+                        (size_t)K + bgtab.size() + ce_w.size();
   auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
   DG_CUDA(cudaSetDevice(m->ctx->device));
   DG_CUDA(cudaMalloc(&m->d_int, pad(n_int) * sizeof(int)));
@@ -638,6 +683,8 @@ int build_mesh(dg_mesh* m) {
   ibuf.insert(ibuf.end(), cell_cmask.begin(), cell_cmask.end());
   for (int64_t c = 0; c < K; ++c) ibuf.push_back((int)m->level[c]);
   ibuf.insert(ibuf.end(), cell_link.begin(), cell_link.end());
+  const size_t o_cb = ibuf.size();
+  for (auto* v : {&cb_start, &cell_coarse, &ce_meta, &ce_node}) ibuf.insert(ibuf.end(), v->begin(), v->end());
   DG_CUDA(cudaMemcpy(m->d_int, ibuf.data(), ibuf.size() * sizeof(int), cudaMemcpyHostToDevice));
 
   std::vector<double> rbuf;
@@ -664,6 +711,8 @@ int build_mesh(dg_mesh* m) {
   rbuf.insert(rbuf.end(), zeta0.begin(), zeta0.end());
   size_t o_bg = rbuf.size();
   rbuf.insert(rbuf.end(), bgtab.begin(), bgtab.end());
+  size_t o_cew = rbuf.size();
+  rbuf.insert(rbuf.end(), ce_w.begin(), ce_w.end());
   DG_CUDA(cudaMemcpy(m->d_f64, rbuf.data(), rbuf.size() * sizeof(double), cudaMemcpyHostToDevice));
   std::vector<float> fbuf(rbuf.begin(), rbuf.end());
   DG_CUDA(cudaMemcpy(m->d_f32, fbuf.data(), fbuf.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -704,6 +753,12 @@ int build_mesh(dg_mesh* m) {
     v.bg_z0 = (decltype(v.gravity))zlo;
     v.bg_idz = (decltype(v.gravity))(1.0 / bg_dz);
     v.bg_m = bg_m;
+    v.cb_start = ib + o_cb;
+    v.cell_coarse = v.cb_start + cb_start.size();
+    v.ce_meta = v.cell_coarse + K;
+    v.ce_node = v.ce_meta + n_ce;
+    v.ce_w = base + o_cew;
+    v.n_ce = (int)n_ce;
   };
   fill(m->v64, (const double*)m->d_f64);
   fill(m->v32, (const float*)m->d_f32);

@@ -212,6 +212,16 @@ __device__ __forceinline__ double gather_allsum(const double* part, int cnt, dou
   return block_allsum(v, sred);
 }
 
+// square root of the same sum, taken by thread 0 and returned to every thread
+__device__ __forceinline__ double gather_allnorm(const double* part, int cnt, double* sred) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) v += part[i];
+  const double r = block_sum(v, sred);
+  if (threadIdx.x == 0) sred[0] = sqrt(r);
+  __syncthreads();
+  return sred[0];
+}
+
 // the same for the strided sub-array part[off], part[off + stride], ... (cnt entries)
 __device__ __forceinline__ double gather_allsum_strided(const double* part, int cnt, int stride, int off,
                                                         double* sred) {
@@ -220,6 +230,31 @@ __device__ __forceinline__ double gather_allsum_strided(const double* part, int 
   return block_allsum(v, sred);
 }
 
+
+// three FP64 sums over the block with one pair of block barriers; the results
+// in thread 0 (sred holds 3 x 32 doubles)
+__device__ __forceinline__ void block_sum3(double& x, double& y, double& z, double* sred) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+    z += __shfl_down_sync(0xffffffffu, z, o);
+  }
+  const int nw = (int)(blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    sred[threadIdx.x >> 5] = x;
+    sred[32 + (threadIdx.x >> 5)] = y;
+    sred[64 + (threadIdx.x >> 5)] = z;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool in = (int)threadIdx.x < nw;
+    x = warp0_tree(in ? sred[threadIdx.x] : 0.0, nw);
+    y = warp0_tree(in ? sred[32 + threadIdx.x] : 0.0, nw);
+    z = warp0_tree(in ? sred[64 + threadIdx.x] : 0.0, nw);
+  }
+}
 
 // copy cnt global partial sums (no more than the staging area holds) into
 // shared memory with all threads
@@ -461,7 +496,7 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
   double* zc = hf + (m + 1);         // [m+1] z = H a
   double* dv = zc + (m + 1);         // [m+1] d
   double* sred = dv + (m + 1);       // [32]
-  double* sc = sred + 32;            // [8]: 0 ||b||, 1 resid, 2 beta, 3 rho, 4 c
+  double* sc = sred + 32;            // [8]: 1 resid, 3 rho, 4 c, 5 1/rho
   int* sflag = (int*)(sc + 8);       // [4]: 0 stop cycle, 1 converged
   double* t64 = (double*)(sflag + 4);  // FP64 tables D, Dw, I|It
   double* sD64 = t64;
@@ -497,7 +532,7 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
     if (threadIdx.x == 0) a.partial[sg.rank] = s;
   }
   sg.sync();
-  const double bn = sqrt(gather_allsum(a.partial, G, sred));
+  const double bn = gather_allnorm(a.partial, G, sred);
   if (bn == 0.0) {
     for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
     if (sg.rank == 0 && threadIdx.x == 0) {
@@ -531,7 +566,7 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
     }
     sg.sync();
     pc.mark(PH_RESIDUAL);
-    const double beta = sqrt(gather_allsum(a.partial, G, sred));
+    const double beta = gather_allnorm(a.partial, G, sred);
     if (threadIdx.x == 0) {
       sflag[1] = (beta <= a.tol * bn) ? 1 : 0;
       sflag[0] = 0;
@@ -624,7 +659,11 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
           const double rho = ok ? rho2 * irho : 0.0;
           sc[3] = rho;
           sc[5] = irho;
-          sc[6] = s2;
+          // first-pass entry k of the new column and the weight c of u_k in u_{k+1}
+          const double zk = k > 0 ? rho * av[k - 1] : 0.0;
+          const double hk = ((bv[k] - s2) * irho - zk) * irho;
+          hf[k] = hk;
+          sc[4] = (zk * irho + hk) * irho;
           int stop = 0;
           if (k == 0) {
             gg[0] = rho;
@@ -672,18 +711,14 @@ __device__ __forceinline__ void gmres_body(const GmresPArgs<TK>& a, Sync& sg, un
       }
       kd = k;
       if (sflag[0]) break;
-      // first pass of column k and the weights of u_{k+1}; every thread forms the scalars
+      // first pass of column k and the weights of u_{k+1} (the scalars from lane 0)
       const double irho = sc[5];
-      const double zk = k > 0 ? sc[3] * av[k - 1] : 0.0;
-      const double hk = ((bv[k] - sc[6]) * irho - zk) * irho;
-      const double cu = (zk * irho + hk) * irho;
+      const double cu = sc[4];
       if ((int)threadIdx.x < k) {
         const int i = threadIdx.x;
         const double h = (bv[i] - zc[i]) * irho;
         hf[i] = h;
         dv[i] = zc[i] * irho + h - cu * av[i];
-      } else if ((int)threadIdx.x == k) {
-        hf[k] = hk;
       }
       __syncthreads();
       pc.mark(PH_COEFS);
@@ -786,7 +821,7 @@ __device__ __forceinline__ void gmres_cgs2_body(const GmresPArgs<TK>& a, Sync& s
     if (threadIdx.x == 0) a.partial[sg.rank] = s;
   }
   sg.sync();
-  const double bn = sqrt(gather_allsum(a.partial, G, sred));
+  const double bn = gather_allnorm(a.partial, G, sred);
   if (bn == 0.0) {
     for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
     if (sg.rank == 0 && threadIdx.x == 0) {
@@ -820,7 +855,7 @@ __device__ __forceinline__ void gmres_cgs2_body(const GmresPArgs<TK>& a, Sync& s
     }
     sg.sync();
     pc.mark(PH_RESIDUAL);
-    const double beta = sqrt(gather_allsum(a.partial, G, sred));
+    const double beta = gather_allnorm(a.partial, G, sred);
     if (threadIdx.x == 0) {
       sc[2] = beta;
       sflag[1] = (beta <= a.tol * bn) ? 1 : 0;
@@ -987,8 +1022,8 @@ template <int DIM, int DEG, typename TK, class Sync>
 __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw, bool record) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N;
-  double* sred = (double*)smem_raw;  // [32]
-  double* sc = sred + 32;            // [16]
+  double* sred = (double*)smem_raw;  // [96]
+  double* sc = sred + 96;            // [16]
   double* sD64 = sc + 16;
   double* sDw64 = sD64 + N * N;
   double* sII64 = sDw64 + N * N;
@@ -1023,7 +1058,7 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
     if (threadIdx.x == 0) a.partial[sg.rank] = t;
   }
   sg.sync();
-  const double bn = sqrt(gather_allsum(a.partial, G, sred));
+  const double bn = gather_allnorm(a.partial, G, sred);
   if (bn == 0.0) {
     for (int64_t i = tid; i < n; i += gstride) a.x[i] = 0.0;
     if (sg.rank == 0 && threadIdx.x == 0) {
@@ -1054,7 +1089,7 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
     }
     sg.sync();
     pc.mark(PH_RESIDUAL);
-    const double beta0 = sqrt(gather_allsum(a.partial, G, sred));
+    const double beta0 = gather_allnorm(a.partial, G, sred);
     rel = beta0 / bn;
     if (sg.failed()) break;
     if (beta0 <= a.tol * bn) {
@@ -1076,9 +1111,17 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
           d0 += mi * w[i];
           e0 += ri * ri;
         }
-        const double tg = block_sum_k<TK>(g0, sred);
-        const double td = block_sum_k<TK>(d0, sred);
-        const double te = block_sum_k<TK>(e0, sred);
+        // warp sums in TK, FP64 across the warps
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          g0 += __shfl_down_sync(0xffffffffu, g0, o);
+          d0 += __shfl_down_sync(0xffffffffu, d0, o);
+          e0 += __shfl_down_sync(0xffffffffu, e0, o);
+        }
+        double tg = (threadIdx.x & 31) == 0 ? (double)g0 : 0.0;
+        double td = (threadIdx.x & 31) == 0 ? (double)d0 : 0.0;
+        double te = (threadIdx.x & 31) == 0 ? (double)e0 : 0.0;
+        block_sum3(tg, td, te, sred);
         if (threadIdx.x == 0) {
           a.partial[3 * sg.rank] = tg;
           a.partial[3 * sg.rank + 1] = td;
@@ -1087,22 +1130,43 @@ __device__ __forceinline__ void cg_body(const GmresPArgs<TK>& a, Sync& sg, unsig
       }
       sg.sync();
       pc.mark(PH_DOTS);
-      const double gnew = gather_allsum_strided(a.partial, G, 3, 0, sred);
-      const double delta = gather_allsum_strided(a.partial, G, 3, 1, sred);
-      const double rn = sqrt(gather_allsum_strided(a.partial, G, 3, 2, sred));
-      ++total;
-      rel = rn / bn;
-      if (sg.failed() || rn <= floor || total >= a.max_iters || !(delta > 0.0) || !(gnew > 0.0)) break;
-      double beta;
-      if (first) {
-        beta = 0.0;
-        alpha = gnew / delta;
-        first = false;
-      } else {
-        beta = gnew / gamma;
-        alpha = gnew / (delta - beta * gnew / alpha);
+      // the three sums of the G block partials in one block reduction; thread 0 evaluates
+      // the square root, the divisions and the stop test and broadcasts them through sc
+      {
+        double gs = 0.0, ds = 0.0, es = 0.0;
+        for (int c = threadIdx.x; c < G; c += blockDim.x) {
+          gs += a.partial[3 * c];
+          ds += a.partial[3 * c + 1];
+          es += a.partial[3 * c + 2];
+        }
+        block_sum3(gs, ds, es, sred);
+        if (threadIdx.x == 0) {
+          const double rn = sqrt(es);
+          const bool stop = rn <= floor || total + 1 >= a.max_iters || !(ds > 0.0) || !(gs > 0.0);
+          double beta = 0.0, al = alpha;
+          if (!stop) {
+            if (first) {
+              al = gs / ds;
+            } else {
+              beta = gs / gamma;
+              al = gs / (ds - beta * gs / alpha);
+            }
+          }
+          sc[0] = rn / bn;
+          sc[1] = stop ? 1.0 : 0.0;
+          sc[2] = beta;
+          sc[3] = al;
+          sc[4] = gs;
+        }
+        __syncthreads();
       }
-      gamma = gnew;
+      ++total;
+      rel = sc[0];
+      if (sg.failed() || sc[1] != 0.0) break;
+      const double beta = first ? 0.0 : sc[2];
+      alpha = sc[3];
+      gamma = sc[4];
+      first = false;
       const TK bk = (TK)beta, ak = (TK)alpha;
       for (int64_t i = tid; i < n; i += gstride) {
         const TK pi = r[i] + bk * p[i];
@@ -1522,7 +1586,7 @@ inline size_t gmres_smem_bytes(int m) {
   const size_t gm = dbl * sizeof(double) + 4 * sizeof(int) + tabs + 64;
   const size_t d1 = 2 * (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 5 * (size_t)(m + 1) + 32 + 8;
   const size_t g1 = d1 * sizeof(double) + 4 * sizeof(int) + tabs + 64;
-  const size_t cg = (size_t)(32 + 16) * sizeof(double) + tabs + 64;
+  const size_t cg = (size_t)(96 + 16) * sizeof(double) + tabs + 64;
   return std::max(gm, std::max(g1, cg));
 }
 

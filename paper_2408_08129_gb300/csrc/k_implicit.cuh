@@ -109,52 +109,88 @@ __device__ __forceinline__ unsigned batch_coarse_mask(const MeshView<T>& mv, int
   return __reduce_or_sync(0xffffffffu, m);
 }
 
-// Coarse sides of the batch's 2:1 faces.  For every cell, each of its coarse
-// faces (local face lf, first subface f) takes a slot; in rounds of
-// kCoarseSlots slots, point(f, lf, s, q, j, buf) writes the NV face values of
-// fine point q of subface s (face f + s) to buf[(lc * NV + v) * NP + j],
-// j = s * NF + q, buf being the slot's part of sJ; after one block barrier,
-// each node on those faces adds sum_s sum_q weight * value to acc[0..NV) with
-// weight = sign * It.  Called by the whole block with the batch's mask bmask
-// and largest slot count nmax (the same in every thread); contains
-// __syncthreads only when some cell of the batch has a coarse face.
-template <int DIM, int DEG, typename T, int NV, class Point>
-__device__ __forceinline__ void coarse_pass(const MeshView<T>& mv, bool active, int64_t c, int lc, int i,
-                                            const int* id, unsigned bmask, int nmax, const T* sIt, T sign, T* sJ,
-                                            T* acc, Point&& point) {
+// Coarse sides of the batch's 2:1 faces, through the batch's entry list
+// (MeshView::cb_start, ce_*).  A round takes FPR coarse faces (slots) of the
+// batch, one fine point per thread (EPR = FPR * NP threads): coarse_fill
+// writes the NV face values of each point to buf[v * EPR + k] (k = the
+// point's place in the round), reading global memory only, so that round 0
+// is filled before the batch's first barrier and its loads overlap the
+// batch's own; after a barrier, coarse_sum adds at each node on a coarse face
+// of the round sum_s sum_q sign * It * value to acc[0..NV).
+template <int DIM, int DEG>
+struct CoarseRounds {
   using S = Shape<DIM, DEG>;
-  constexpr int NF = S::NF, NC = S::NC, NP = coarse_points<DIM, DEG>();
-  constexpr int SLOT = S::CPB * NV * NP;
-  if (bmask == 0u) return;
-  const unsigned cmask = active ? (unsigned)mv.cell_cmask[c] : 0u;
-  for (int r0 = 0; r0 < nmax; r0 += kCoarseSlots) {
-    int slot = 0;
+  static constexpr int NP = coarse_points<DIM, DEG>();
+  static constexpr int FPR =
+      S::THREADS / NP < S::CPB * kCoarseSlots ? S::THREADS / NP : S::CPB * kCoarseSlots;  // slots per round
+  static constexpr int EPR = FPR * NP;                                                     // points per round
+  static_assert(FPR >= 1, "a coarse face's fine points must fit one block");
+  __device__ __forceinline__ static int rounds(int e0, int e1) { return ((e1 - e0) / NP + FPR - 1) / FPR; }
+};
+
+// point(cc, lf, s, q, node, w, val): the NV values at fine point q of subface
+// s of local face lf of batch cell cc (the fine side's node `node`, w = 1/2 |N| n there)
+template <int DIM, int DEG, typename T, int NV, class Point>
+__device__ __forceinline__ void coarse_fill(const MeshView<T>& mv, int64_t batch, int e0, int e1, int r, T* buf,
+                                            Point&& point) {
+  using R = CoarseRounds<DIM, DEG>;
+  constexpr int NF = Shape<DIM, DEG>::NF, CPB = Shape<DIM, DEG>::CPB;
+  const int k = threadIdx.x;
+  const int e = e0 + r * R::EPR + k;
+  if (k < R::EPR && e < e1) {
+    const int meta = mv.ce_meta[e];
+    const int node = mv.ce_node[e];
+    T w[DIM];
 #pragma unroll
-    for (int lf = 0; lf < 2 * DIM; ++lf) {
-      if (!((cmask >> lf) & 1u)) continue;
-      const int sl = slot++ - r0;
-      if (sl < 0 || sl >= kCoarseSlots) continue;
-      const int f = mv.cell_face[c * 2 * DIM + lf] >> 2;
-      for (int j = i; j < NP; j += NC) point(f, lf, j / NF, j % NF, j, sJ + sl * SLOT);
-    }
+    for (int b = 0; b < DIM; ++b) w[b] = mv.ce_w[(int64_t)b * mv.n_ce + e];
+    const int j = meta >> 9;
+    T val[NV];
+    point((int)batch * CPB + (meta & 63), (meta >> 6) & 7, j / NF, j % NF, node, w, val);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) buf[v * R::EPR + k] = val[v];
+  }
+}
+
+// coarse = MeshView::cell_coarse of this thread's cell (0 if none or inactive)
+template <int DIM, int DEG, typename T, int NV>
+__device__ __forceinline__ void coarse_sum(int coarse, int r, const int* id, const T* sIt, T sign, const T* buf,
+                                           T* acc) {
+  using R = CoarseRounds<DIM, DEG>;
+  using S = Shape<DIM, DEG>;
+  constexpr int NF = S::NF;
+  const unsigned cmask = (unsigned)coarse & 0xffu;
+  if (!cmask) return;
+  const int slot0 = coarse >> 8;
+#pragma unroll
+  for (int lf = 0; lf < 2 * DIM; ++lf) {
+    if (!((cmask >> lf) & 1u)) continue;
+    const int a = lf >> 1;
+    if (id[a] != ((lf & 1) ? DEG : 0)) continue;
+    const int slot = slot0 + __popc(cmask & ((1u << lf) - 1u));
+    if (slot / R::FPR != r) continue;
+    const int kt = tangential_index<DIM, DEG>(a, id);
+    const T* b = buf + (slot % R::FPR) * R::NP;
+    for (int sp = 0; sp < S::NSUB; ++sp)
+      for (int q = 0; q < NF; ++q) {
+        const T wgt = sign * coarse_weight<DIM, DEG, T>(sIt, sp, kt, q);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += wgt * b[v * R::EPR + sp * NF + q];
+      }
+  }
+}
+
+// The rounds after round 0 (rare: more coarse faces in one batch than a round
+// holds), each between block barriers; called by the whole block.
+template <int DIM, int DEG, typename T, int NV, class Point>
+__device__ __forceinline__ void coarse_more_rounds(const MeshView<T>& mv, int64_t batch, int e0, int e1, int coarse,
+                                                   const int* id, const T* sIt, T sign, T* buf, T* acc,
+                                                   Point&& point) {
+  const int nr = CoarseRounds<DIM, DEG>::rounds(e0, e1);
+  for (int r = 1; r < nr; ++r) {
     __syncthreads();
-    slot = 0;
-#pragma unroll
-    for (int lf = 0; lf < 2 * DIM; ++lf) {
-      if (!((cmask >> lf) & 1u)) continue;
-      const int sl = slot++ - r0;
-      const int a = lf >> 1;
-      if (sl < 0 || sl >= kCoarseSlots || id[a] != ((lf & 1) ? DEG : 0)) continue;
-      const int kt = tangential_index<DIM, DEG>(a, id);
-      const T* buf = sJ + sl * SLOT;
-      for (int s = 0; s < S::NSUB; ++s)
-        for (int q = 0; q < NF; ++q) {
-          const T wgt = sign * coarse_weight<DIM, DEG, T>(sIt, s, kt, q);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) acc[v] += wgt * buf[(lc * NV + v) * NP + s * NF + q];
-        }
-    }
+    coarse_fill<DIM, DEG, T, NV>(mv, batch, e0, e1, r, buf, point);
     __syncthreads();
+    coarse_sum<DIM, DEG, T, NV>(coarse, r, id, sIt, sign, buf, acc);
   }
 }
 
@@ -209,7 +245,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
                                                 const T* __restrict__ h, T* __restrict__ g, int64_t batch, T* sp,
                                                 T* sJ, const T* sD, const T* sII, T* sz = nullptr) {
   using S = Shape<DIM, DEG>;
-  constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
+  constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
   const int c = (int)batch * CPB + lc;
   const bool active = (lc < CPB) && (c < mv.n_cells);
@@ -220,12 +256,13 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   T Jl[DIM][DIM];
   T po[DIM];  // the other side's value at this node's faces
   T scale = T(0), pv = T(0);
-  int nmax = 0;
-  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch, &nmax);
+  int coarse = 0;
+  const int e0 = mv.cb_start[batch], e1 = mv.cb_start[batch + 1];
   if (active) {
     pv = p[idx];
     sp[lc * NC + i] = pv;
     load_face_links<DIM, DEG, T>(mv, c, id, links);
+    coarse = mv.cell_coarse[c];
     if (GZ) {
       sz[lc * NC + i] = mv.zdev[idx];
       scale = h ? h[idx] : T(1);
@@ -241,6 +278,16 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
     for (int a = 0; a < DIM; ++a)
       if ((links[a] & 3) < 2) other_trace<DIM, DEG, T, 1>(p, 0, links[a], a, id, sII, &po[a]);
   }
+  // coarse sides, round 0: the jump at each fine point times 1/2 |N| n, from the fine value and
+  // the coarse cell's polynomial
+  auto gpoint = [&](int cc, int lf, int s, int q, int node, const T* w, T* val) {
+    T pp;
+    coarse_interp<DIM, DEG, T, 1>(p, 0, cc * NC, lf, s, q, sII, &pp);
+    const T jmp = pp - p[node];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) val[b] = jmp * w[b];
+  };
+  if (e1 > e0) coarse_fill<DIM, DEG, T, DIM>(mv, batch, e0, e1, 0, sJ, gpoint);
   __syncthreads();
   T facc[DIM], dp[DIM];
 #pragma unroll
@@ -271,19 +318,11 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
       for (int b = 0; b < DIM; ++b) facc[b] += jmp * Jl[a][b];
     }
   }
-  // coarse sides: jump at each fine point from the fine value and the cell's own polynomial
-  const int64_t total = (int64_t)mv.nf * NF;
-  coarse_pass<DIM, DEG, T, DIM>(mv, active, c, lc, i, id, bmask, nmax, sII + 2 * N * N, T(1), sJ, facc,
-                                [&](int f, int lf, int s, int q, int j, T* buf) {
-                                  const int64_t t = (int64_t)(f + s) * NF + q;
-                                  const T pm = p[mv.fnode_m[t]];
-                                  T pp;
-                                  coarse_interp<DIM, DEG, T, 1>(sp + lc * NC, 0, 0, lf, s, q, sII, &pp);
-                                  const T jmp = T(0.5) * mv.fsj[t] * (pp - pm);
-#pragma unroll
-                                  for (int b = 0; b < DIM; ++b)
-                                    buf[(lc * DIM + b) * NP + j] = jmp * mv.fn[(int64_t)b * total + t];
-                                });
+  // coarse sides: the values of round 0 are in sJ since the barrier above
+  if (e1 > e0) {
+    coarse_sum<DIM, DEG, T, DIM>(coarse, 0, id, sII + 2 * N * N, T(1), sJ, facc);
+    coarse_more_rounds<DIM, DEG, T, DIM>(mv, batch, e0, e1, coarse, id, sII + 2 * N * N, T(1), sJ, facc, gpoint);
+  }
   if (active) {
     const T iwend = mv.tab[S::T_IWEND];
 #pragma unroll
@@ -310,7 +349,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
                                                int64_t batch, T* sF, T* sJ, const T* sDw, const T* sII,
                                                T* sz = nullptr, const T* sD = nullptr) {
   using S = Shape<DIM, DEG>;
-  constexpr int N = S::N, NC = S::NC, CPB = S::CPB, NF = S::NF, NP = coarse_points<DIM, DEG>();
+  constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
   const int c = (int)batch * CPB + lc;
   const bool active = (lc < CPB) && (c < mv.n_cells);
@@ -322,12 +361,13 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   T fv[DIM];
   T ij = T(0), pv = T(0);
   T Jl[DIM][DIM];
-  int nmax = 0;
-  const unsigned bmask = batch_coarse_mask<DIM, DEG, T>(mv, batch, &nmax);
+  int coarse = 0;
+  const int e0 = mv.cb_start[batch], e1 = mv.cb_start[batch + 1];
   if (active) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fv[b] = (fld + b * Nn)[idx];
     load_face_links<DIM, DEG, T>(mv, c, id, links);
+    coarse = mv.cell_coarse[c];
     if (HELM) pv = p[idx];
     if (GZ) {
       sz[lc * NC + i] = mv.zdev[idx];
@@ -346,6 +386,17 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       }
     }
   }
+  // coarse sides, round 0: |N| {f}.n / 2 at each fine point from the fine value and the coarse
+  // cell's polynomial
+  auto dpoint = [&](int cc, int lf, int s, int q, int node, const T* w, T* val) {
+    T fc[DIM];
+    coarse_interp<DIM, DEG, T, DIM>(fld, Nn, cc * NC, lf, s, q, sII, fc);
+    T sum = T(0);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) sum += ((fld + b * Nn)[node] + fc[b]) * w[b];
+    val[0] = sum;
+  };
+  if (e1 > e0) coarse_fill<DIM, DEG, T, 1>(mv, batch, e0, e1, 0, sJ, dpoint);
   if (GZ) {
     __syncthreads();
     if (active) {
@@ -391,20 +442,11 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       facc += half_sign<DIM, DEG, T>(a, id) * sum;
     }
   }
-  // coarse sides: |N| {f}.n at each fine point from the fine value and the cell's own polynomial
-  const int64_t total = (int64_t)mv.nf * NF;
-  coarse_pass<DIM, DEG, T, 1>(mv, active, c, lc, i, id, bmask, nmax, sII + 2 * N * N, T(-1), sJ, &facc,
-                              [&](int f, int lf, int s, int q, int j, T* buf) {
-                                const int64_t t = (int64_t)(f + s) * NF + q;
-                                const int im = mv.fnode_m[t];
-                                T fc[DIM];
-                                coarse_interp<DIM, DEG, T, DIM>(fld, Nn, c * NC, lf, s, q, sII, fc);
-                                T sum = T(0);
-#pragma unroll
-                                for (int b = 0; b < DIM; ++b)
-                                  sum += ((fld + b * Nn)[im] + fc[b]) * (mv.fn + b * total)[t];
-                                buf[lc * NP + j] = T(0.5) * mv.fsj[t] * sum;
-                              });
+  // coarse sides: the values of round 0 are in sJ since the barrier above
+  if (e1 > e0) {
+    coarse_sum<DIM, DEG, T, 1>(coarse, 0, id, sII + 2 * N * N, T(-1), sJ, &facc);
+    coarse_more_rounds<DIM, DEG, T, 1>(mv, batch, e0, e1, coarse, id, sII + 2 * N * N, T(-1), sJ, &facc, dpoint);
+  }
   if (active) {
     const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
     if (HELM)

@@ -305,7 +305,7 @@ int helmholtz_solve(dg_state* S, const dg_solver_opts* o, double alpha, dg_step_
   };
   GmresResult res;
   int rc;
-  unsigned long long* phase = S->ctx->prof ? S->ctx->d_phase : nullptr;
+  unsigned long long* phase = S->ctx->prof_clocks ? S->ctx->d_phase : nullptr;
   const int npart = (restart + 1) * kDotBlocks;
   if (o->fused || persistent_only(o->krylov)) {
     ProfScope ps(S->ctx, DG_PROF_GMRES, s);
@@ -1068,9 +1068,10 @@ extern "C" int dg_batch_plan_create(dg_ctx* ctx, int n, const dg_mesh* const* me
   P->arena.host.assign(arena_bytes, 0);
 
   // capture one step; nothing runs while the capture is open
-  const bool prof = ctx->prof;
+  const bool prof = ctx->prof, prof_clocks = ctx->prof_clocks;
   const long long launches0 = ctx->launches;
   ctx->prof = false;
+  ctx->prof_clocks = false;
   ctx->arena = &P->arena;
   int* err = ctx->d_batch_err;
   e = cudaStreamBeginCapture(P->cs, cudaStreamCaptureModeThreadLocal);
@@ -1099,6 +1100,7 @@ extern "C" int dg_batch_plan_create(dg_ctx* ctx, int n, const dg_mesh* const* me
   }
   ctx->arena = nullptr;
   ctx->prof = prof;
+  ctx->prof_clocks = prof_clocks;
   P->kernels = ctx->launches - launches0;
   ctx->launches = launches0;
   if (rc != DG_OK) return bail(rc);

@@ -51,6 +51,7 @@ class MeshInfo(ctypes.Structure):
         ("n_conforming", c_int64), ("n_subfaces", c_int64), ("n_walls", c_int64),
         ("max_level", c_int), ("min_edge", c_double), ("device_bytes", ctypes.c_size_t),
         ("solver_form", c_int * 2), ("solver_ms", (ctypes.c_float * 3) * 2),
+        ("n_batches", c_int * 2), ("solver_partition", c_int * 2), ("solver_ms_balanced", (ctypes.c_float * 3) * 2),
     ]
 
 
@@ -112,6 +113,7 @@ def _load():
         "dg_mesh_create": (c_int, [P, ctypes.POINTER(MeshDesc), ctypes.POINTER(P)]),
         "dg_mesh_destroy": (c_int, [P]),
         "dg_mesh_get_info": (c_int, [P, ctypes.POINTER(MeshInfo)]),
+        "dg_mesh_set_partition": (c_int, [P, c_int]),
         "dg_mesh_get_faces": (c_int, [P, P, P, P]),
         "dg_mesh_get_coords": (c_int, [P, P]),
         "dg_background": (c_int, [P, P, P, P]),

@@ -141,7 +141,9 @@ class Mesh:
         self.case = case
         info = B.MeshInfo()
         check(lib.dg_mesh_get_info(h, ctypes.byref(info)), "dg_mesh_get_info")
-        self.info = {k: getattr(info, k) for k, _ in B.MeshInfo._fields_ if k not in ("solver_form", "solver_ms")}
+        self.info = {k: getattr(info, k) for k, _ in B.MeshInfo._fields_
+                     if k not in ("solver_form", "solver_ms", "n_batches", "solver_partition", "solver_ms_balanced")}
+        self.n_batches = tuple(info.n_batches)
         self.dim = case.dim
         self.n_vars = info.n_vars
         self.n_cells = info.n_cells
@@ -150,13 +152,24 @@ class Mesh:
         self.n_dof = info.n_dof
 
     def autotuned(self):
-        """Autotuner outcome: per precision, the chosen Helmholtz solver form and the timed solves (ms)."""
+        """Autotuner outcome: per precision, the chosen Helmholtz solver form and cell partition
+        ("uniform": CPB consecutive cells per batch; "balanced": cost-balanced batches, one per CTA of
+        a persistent solve) and the timed solves (ms) on each partition."""
         info = B.MeshInfo()
         check(lib.dg_mesh_get_info(self.handle, ctypes.byref(info)), "dg_mesh_get_info")
         forms = {0: "gmres_multi_kernel", 1: "gmres_persistent", 2: "chebyshev", -1: None}
+        parts = ("uniform", "balanced")
         return {p: {"form": forms[info.solver_form[i]],
-                    "ms": {forms[f]: info.solver_ms[i][f] for f in range(3) if info.solver_ms[i][f] > 0}}
+                    "partition": parts[info.solver_partition[i]],
+                    "batches": {parts[k]: info.n_batches[k] for k in range(2) if info.n_batches[k] > 0},
+                    "ms": {forms[f]: info.solver_ms[i][f] for f in range(3) if info.solver_ms[i][f] > 0},
+                    "ms_balanced": {forms[f]: info.solver_ms_balanced[i][f] for f in range(3)
+                                    if info.solver_ms_balanced[i][f] > 0}}
                 for i, p in enumerate(("fp64", "fp32"))}
+
+    def set_partition(self, k):
+        """Cell partition of the implicit passes: 0 uniform batches, 1 cost-balanced (where built)."""
+        check(lib.dg_mesh_set_partition(self.handle, int(k)), "dg_mesh_set_partition")
 
     def faces(self):
         i = self.info

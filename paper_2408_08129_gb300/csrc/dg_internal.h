@@ -87,13 +87,15 @@ struct MeshView {
   const T* bg_tab;
   T bg_z0, bg_idz;
   int bg_m;
-  // Coarse sides of the 2:1 faces per cell batch of the implicit cell passes
-  // (CPB consecutive cells): batch b's entries are [cb_start[b], cb_start[b+1]),
-  // per cell in order, per coarse local face in order (a slot), per fine point
-  // j = s NF + q of the face's subfaces; ce_meta = lc | lf << 6 | j << 9,
-  // ce_node = the fine-side node, ce_w[b * n_ce + e] = 1/2 |N| n_b at it.
-  // cell_coarse[c] = coarse-face mask | (batch slot of the cell's first one) << 8.
-  const int* cb_start;
+  // Cell batches of the implicit cell passes (one CTA each; the mesh's active
+  // partition): batch b = cells [bdesc[b].x, bdesc[b].y) (at most CPB), its
+  // coarse-side entries [bdesc[b].z, bdesc[b].w): per cell in order, per
+  // coarse local face in order (a slot), per fine point j = s NF + q of the
+  // face's subfaces; ce_meta = lc | lf << 6 | j << 9, ce_node = the fine-side
+  // node, ce_w[b * n_ce + e] = 1/2 |N| n_b at it.  cell_coarse[c] =
+  // coarse-face mask | (batch slot of the cell's first one) << 8.
+  const int4* bdesc;
+  int nbat;
   const int* cell_coarse;
   const int* ce_meta;
   const int* ce_node;
@@ -165,6 +167,16 @@ struct ProfScope {
 };
 }  // namespace dg
 
+namespace dg {
+struct CellPartition {
+  void* d_int = nullptr;  // int4 bdesc[nbat], cell_coarse[K], ce_meta[E], ce_node[E]
+  void* d_f64 = nullptr;  // ce_w [dim][E]
+  void* d_f32 = nullptr;
+  int nbat = 0, n_ce = 0;
+  double cost_max = 0.0;  // the largest batch's work (nodes + face points)
+};
+}  // namespace dg
+
 struct dg_mesh {
   dg_ctx* ctx = nullptr;
   dg_mesh_desc desc{};
@@ -199,4 +211,17 @@ struct dg_mesh {
   // 2 = Chebyshev persistent; 0 ms = not timed) and the form chosen last
   mutable int tuned_form[2] = {-1, -1};
   mutable float tuned_ms[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  // cell partitions of the implicit passes: [0] CPB consecutive cells per
+  // batch, [1] (small meshes) cost-balanced batches, one per CTA of a
+  // persistent solve; the autotuner picks one per precision
+  dg::CellPartition part[2];
+  int n_parts = 0;
+  int active_part = 0;
+  mutable int tuned_part[2] = {0, 0};
+  mutable float tuned_ms_balanced[2][3] = {{0, 0, 0}, {0, 0, 0}};
 };
+
+namespace dg {
+// Make partition k (0 uniform, 1 cost-balanced) the one the mesh's implicit passes use.
+void set_partition(const dg_mesh* m, int k);
+}  // namespace dg

@@ -197,6 +197,137 @@ int check_watertight(const dg_mesh* m, const Tables1D& tab, const std::vector<in
   return DG_OK;
 }
 
+namespace {
+
+// Coarse sides of the 2:1 faces per cell (see build_mesh) and the work per cell
+struct CoarseLists {
+  int dim = 0, np = 0;
+  std::vector<int> cmask;   // [K] coarse-face mask
+  std::vector<int> off;     // [K+1] first coarse face of each cell (in units of faces)
+  std::vector<int> node;    // [faces * np] fine node of each point
+  std::vector<double> w;    // [faces * np * dim] 1/2 |N| n of each point
+  std::vector<double> cost; // [K] work of the cell's implicit passes (nodes + face points)
+};
+
+// Batches of at most cpb consecutive cells, at most nb of them, with the
+// largest batch cost as small as the greedy cut allows (bisection on the cost
+// bound: each batch is closed when the next cell would exceed it or cpb is reached).
+std::vector<int> balanced_batches(const std::vector<double>& cost, int cpb, int nb) {
+  const int64_t K = (int64_t)cost.size();
+  auto cut = [&](double bound, std::vector<int>* starts) {
+    int count = 0, cells = 0;
+    double acc = 0.0;
+    for (int64_t c = 0; c < K; ++c) {
+      if (cells > 0 && (cells == cpb || acc + cost[c] > bound)) {
+        cells = 0;
+        acc = 0.0;
+      }
+      if (cells == 0) {
+        ++count;
+        if (starts) starts->push_back((int)c);
+      }
+      acc += cost[c];
+      ++cells;
+    }
+    return count;
+  };
+  double lo = *std::max_element(cost.begin(), cost.end()), hi = 0.0;
+  for (double x : cost) hi += x;
+  for (int it = 0; it < 60 && hi - lo > 1e-9 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (cut(mid, nullptr) <= nb) hi = mid;
+    else lo = mid;
+  }
+  std::vector<int> starts;
+  cut(hi, &starts);
+  starts.push_back((int)K);
+  return starts;
+}
+
+// One partition of the cells into batches (bstart: K-terminated starts) with
+// its coarse-side entry lists, uploaded to a device block of its own.
+int build_partition(dg_mesh* m, const CoarseLists& cl, const std::vector<int>& bstart, CellPartition& P) {
+  const int dim = cl.dim, np = cl.np;
+  const int nbat = (int)bstart.size() - 1;
+  std::vector<int4> bdesc(nbat);
+  std::vector<int> cell_coarse(m->K, 0), meta, node;
+  std::vector<double> w;
+  double cmax = 0.0;
+  for (int b = 0; b < nbat; ++b) {
+    const int e0 = (int)meta.size();
+    int slot = 0;
+    double cst = 0.0;
+    for (int c = bstart[b]; c < bstart[b + 1]; ++c) {
+      const int lc = c - bstart[b];
+      cst += cl.cost[c];
+      cell_coarse[c] = cl.cmask[c] | (slot << 8);
+      for (int k = cl.off[c]; k < cl.off[c + 1]; ++k, ++slot) {
+        int lf = 0, seen = -1;  // local face of the cell's (k - off)-th coarse face
+        for (; lf < 2 * dim; ++lf)
+          if ((cl.cmask[c] >> lf) & 1)
+            if (++seen == k - cl.off[c]) break;
+        for (int j = 0; j < np; ++j) {
+          meta.push_back(lc | (lf << 6) | (j << 9));
+          node.push_back(cl.node[(size_t)k * np + j]);
+        }
+      }
+    }
+    bdesc[b] = make_int4(bstart[b], bstart[b + 1], e0, (int)meta.size());
+    cmax = std::max(cmax, cst);
+  }
+  const size_t E = meta.size();
+  w.assign((size_t)dim * E, 0.0);
+  for (int b = 0; b < nbat; ++b)
+    for (int e = bdesc[b].z; e < bdesc[b].w; ++e) {
+      // the batch's entries follow the per-cell lists in order: entry e is global point
+      // off[c0] np + (e - e0)
+      const size_t g = (size_t)cl.off[bstart[b]] * np + (size_t)(e - bdesc[b].z);
+      for (int d = 0; d < dim; ++d) w[(size_t)d * E + e] = cl.w[g * dim + d];
+    }
+  const size_t n_int = 4 * (size_t)nbat + (size_t)m->K + 2 * E;
+  DG_CUDA(cudaMalloc(&P.d_int, n_int * sizeof(int) + 64));
+  DG_CUDA(cudaMalloc(&P.d_f64, w.size() * sizeof(double) + 64));
+  DG_CUDA(cudaMalloc(&P.d_f32, w.size() * sizeof(float) + 64));
+  int* ib = (int*)P.d_int;
+  DG_CUDA(cudaMemcpy(ib, bdesc.data(), (size_t)nbat * sizeof(int4), cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(ib + 4 * (size_t)nbat, cell_coarse.data(), (size_t)m->K * sizeof(int), cudaMemcpyHostToDevice));
+  if (E) {
+    DG_CUDA(cudaMemcpy(ib + 4 * (size_t)nbat + m->K, meta.data(), E * sizeof(int), cudaMemcpyHostToDevice));
+    DG_CUDA(cudaMemcpy(ib + 4 * (size_t)nbat + m->K + E, node.data(), E * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<float> wf(w.begin(), w.end());
+    DG_CUDA(cudaMemcpy(P.d_f64, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    DG_CUDA(cudaMemcpy(P.d_f32, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  P.nbat = nbat;
+  P.n_ce = (int)E;
+  P.cost_max = cmax;
+  m->device_bytes += n_int * sizeof(int) + w.size() * (sizeof(double) + sizeof(float));
+  return DG_OK;
+}
+
+}  // namespace
+
+// Make partition k the one every implicit cell pass of the mesh uses.
+void set_partition(const dg_mesh* cm, int k) {
+  dg_mesh* m = const_cast<dg_mesh*>(cm);
+  if (k < 0 || k >= m->n_parts) k = 0;
+  const CellPartition& P = m->part[k];
+  if (!P.d_int) return;
+  const int* ib = (const int*)P.d_int;
+  auto put = [&](auto& v, auto* w) {
+    v.bdesc = (const int4*)ib;
+    v.nbat = P.nbat;
+    v.cell_coarse = ib + 4 * (size_t)P.nbat;
+    v.ce_meta = v.cell_coarse + m->K;
+    v.ce_node = v.ce_meta + P.n_ce;
+    v.ce_w = w;
+    v.n_ce = P.n_ce;
+  };
+  put(m->v64, (const double*)P.d_f64);
+  put(m->v32, (const float*)P.d_f32);
+  m->active_part = k;
+}
+
 int build_mesh(dg_mesh* m) {
   const dg_mesh_desc& d = m->desc;
   const int dim = d.dim, r = d.degree, n = r + 1;
@@ -609,54 +740,36 @@ int build_mesh(dg_mesh* m) {
   for (int64_t c = 0; c < K; ++c)
     for (int lf = 0; lf < 2 * dim; ++lf)
       if ((cell_face[c * 2 * dim + lf] & 3) == 2) cell_cmask[c] |= 1 << lf;
-  // Coarse sides of the 2:1 faces listed per cell batch (the batches of the one-thread-per-node
-  // cell passes: cpb consecutive cells), for the implicit passes: batch b's entries are
-  // [cb_start[b], cb_start[b+1]), per cell of the batch in order, per coarse local face in
-  // order (a slot), one entry per fine point j = s NF + q of the face's subfaces: ce_meta =
-  // lc | lf << 6 | j << 9, ce_node = the fine node, ce_w[b] = 1/2 |N| n_b there (fsj fn / 2).
-  // cell_coarse[c] = cmask | (batch slot of the cell's first coarse face) << 8.
-  const int cpb = nc >= 256 ? 1 : 256 / nc;
+  // Coarse sides of the 2:1 faces per cell, in cell order and local-face order: each coarse
+  // face's NSUB NF fine points (j = s NF + q), the fine node and 1/2 |N| n there (fsj fn / 2);
+  // the cell batches (partitions) index these lists.  Work per cell for the balanced partition:
+  // its nodes, plus one per coarse-side point and per fine-side face node.
   const int nsubf = 1 << (dim - 1), np_c = nsubf * NF;
-  const int64_t nbat = (K + cpb - 1) / cpb;
-  std::vector<int> cb_start((size_t)nbat + 1, 0), cell_coarse(K, 0), ce_meta, ce_node;
-  std::vector<double> ce_w;
-  for (int64_t bt = 0; bt < nbat; ++bt) {
-    cb_start[bt] = (int)ce_meta.size();
-    int slot = 0;
-    for (int lc = 0; lc < cpb && bt * cpb + lc < K; ++lc) {
-      const int64_t c = bt * cpb + lc;
-      cell_coarse[c] = cell_cmask[c] | (slot << 8);
-      for (int lf = 0; lf < 2 * dim; ++lf) {
-        if (!((cell_cmask[c] >> lf) & 1)) continue;
-        const int f = cell_face[c * 2 * dim + lf] >> 2;
-        for (int j = 0; j < np_c; ++j) {
-          const size_t t = (size_t)(f + j / NF) * NF + (size_t)(j % NF);
-          ce_meta.push_back(lc | (lf << 6) | (j << 9));
-          ce_node.push_back(fnode_m[t]);
-        }
-        ++slot;
+  CoarseLists cl;
+  cl.dim = dim;
+  cl.np = np_c;
+  cl.cmask = cell_cmask;
+  cl.off.assign(K + 1, 0);
+  cl.cost.assign(K, (double)nc);
+  for (int64_t c = 0; c < K; ++c) {
+    cl.off[c] = (int)(cl.node.size() / np_c);
+    for (int lf = 0; lf < 2 * dim; ++lf) {
+      const int link = cell_link[(size_t)c * 2 * dim + lf];
+      if ((link & 3) == 1) cl.cost[c] += NF;
+      if (!((cell_cmask[c] >> lf) & 1)) continue;
+      const int f = cell_face[c * 2 * dim + lf] >> 2;
+      for (int j = 0; j < np_c; ++j) {
+        const size_t t = (size_t)(f + j / NF) * NF + (size_t)(j % NF);
+        cl.node.push_back(fnode_m[t]);
+        for (int b = 0; b < dim; ++b) cl.w.push_back(0.5 * fsj[t] * fn[(size_t)b * nf * NF + t]);
       }
+      cl.cost[c] += np_c;
     }
   }
-  cb_start[nbat] = (int)ce_meta.size();
-  const size_t n_ce = ce_meta.size();
-  ce_w.assign((size_t)dim * n_ce, 0.0);
-  for (int64_t bt = 0, e = 0; bt < nbat; ++bt)
-    for (int lc = 0; lc < cpb && bt * cpb + lc < K; ++lc) {
-      const int64_t c = bt * cpb + lc;
-      for (int lf = 0; lf < 2 * dim; ++lf) {
-        if (!((cell_cmask[c] >> lf) & 1)) continue;
-        const int f = cell_face[c * 2 * dim + lf] >> 2;
-        for (int j = 0; j < np_c; ++j, ++e) {
-          const size_t t = (size_t)(f + j / NF) * NF + (size_t)(j % NF);
-          for (int b = 0; b < dim; ++b) ce_w[(size_t)b * n_ce + e] = 0.5 * fsj[t] * fn[(size_t)b * nf * NF + t];
-        }
-      }
-    }
-  const size_t n_int = (size_t)5 * nf + 2 * cell_face.size() + 2 * (size_t)nf * NF + 2 * (size_t)K +
-                       cb_start.size() + cell_coarse.size() + 2 * n_ce;
+  cl.off[K] = (int)(cl.node.size() / np_c);
+  const size_t n_int = (size_t)5 * nf + 2 * cell_face.size() + 2 * (size_t)nf * NF + 2 * (size_t)K;
   const size_t n_real = (size_t)dim * dim * m->Nn + 5 * (size_t)m->Nn + (size_t)(dim + 1) * nf * NF + tabp.size() +
-                        (size_t)K + bgtab.size() + ce_w.size();
+                        (size_t)K + bgtab.size();
   auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
   DG_CUDA(cudaSetDevice(m->ctx->device));
   DG_CUDA(cudaMalloc(&m->d_int, pad(n_int) * sizeof(int)));
@@ -683,8 +796,6 @@ int build_mesh(dg_mesh* m) {
   ibuf.insert(ibuf.end(), cell_cmask.begin(), cell_cmask.end());
   for (int64_t c = 0; c < K; ++c) ibuf.push_back((int)m->level[c]);
   ibuf.insert(ibuf.end(), cell_link.begin(), cell_link.end());
-  const size_t o_cb = ibuf.size();
-  for (auto* v : {&cb_start, &cell_coarse, &ce_meta, &ce_node}) ibuf.insert(ibuf.end(), v->begin(), v->end());
   DG_CUDA(cudaMemcpy(m->d_int, ibuf.data(), ibuf.size() * sizeof(int), cudaMemcpyHostToDevice));
 
   std::vector<double> rbuf;
@@ -711,8 +822,6 @@ int build_mesh(dg_mesh* m) {
   rbuf.insert(rbuf.end(), zeta0.begin(), zeta0.end());
   size_t o_bg = rbuf.size();
   rbuf.insert(rbuf.end(), bgtab.begin(), bgtab.end());
-  size_t o_cew = rbuf.size();
-  rbuf.insert(rbuf.end(), ce_w.begin(), ce_w.end());
   DG_CUDA(cudaMemcpy(m->d_f64, rbuf.data(), rbuf.size() * sizeof(double), cudaMemcpyHostToDevice));
   std::vector<float> fbuf(rbuf.begin(), rbuf.end());
   DG_CUDA(cudaMemcpy(m->d_f32, fbuf.data(), fbuf.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -753,15 +862,28 @@ int build_mesh(dg_mesh* m) {
     v.bg_z0 = (decltype(v.gravity))zlo;
     v.bg_idz = (decltype(v.gravity))(1.0 / bg_dz);
     v.bg_m = bg_m;
-    v.cb_start = ib + o_cb;
-    v.cell_coarse = v.cb_start + cb_start.size();
-    v.ce_meta = v.cell_coarse + K;
-    v.ce_node = v.ce_meta + n_ce;
-    v.ce_w = base + o_cew;
-    v.n_ce = (int)n_ce;
   };
   fill(m->v64, (const double*)m->d_f64);
   fill(m->v32, (const float*)m->d_f32);
+  const int cpb = nc >= 256 ? 1 : 256 / nc;
+  {
+    std::vector<int> bstart;
+    for (int64_t c = 0; c < K; c += cpb) bstart.push_back((int)c);
+    bstart.push_back((int)K);
+    int rc = build_partition(m, cl, bstart, m->part[0]);
+    if (rc != DG_OK) return rc;
+    m->n_parts = 1;
+    // cost-balanced batches, one per CTA of a persistent solve (two per SM), where the uniform
+    // batches do not already fill them
+    const int target = 2 * m->ctx->sm_count;
+    if ((int64_t)bstart.size() - 1 <= target && K > (int64_t)bstart.size() - 1) {
+      bstart = balanced_batches(cl.cost, cpb, (int)std::min<int64_t>(target, K));
+      rc = build_partition(m, cl, bstart, m->part[1]);
+      if (rc != DG_OK) return rc;
+      m->n_parts = 2;
+    }
+  }
+  set_partition(m, 0);
   return DG_OK;
 }
 
@@ -827,6 +949,11 @@ extern "C" int dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->d_f32);
   cudaFree(m->d_scratch);
   if (m->d_tau) cudaFree(m->d_tau);
+  for (auto& P : m->part) {
+    if (P.d_int) cudaFree(P.d_int);
+    if (P.d_f64) cudaFree(P.d_f64);
+    if (P.d_f32) cudaFree(P.d_f32);
+  }
   delete m;
   return DG_OK;
 }
@@ -848,8 +975,21 @@ extern "C" int dg_mesh_get_info(const dg_mesh* m, dg_mesh_info* info) {
   info->device_bytes = m->device_bytes;
   for (int p = 0; p < 2; ++p) {
     info->solver_form[p] = m->tuned_form[p];
-    for (int f = 0; f < 3; ++f) info->solver_ms[p][f] = m->tuned_ms[p][f];
+    info->n_batches[p] = p < m->n_parts ? m->part[p].nbat : 0;
+    info->solver_partition[p] = m->tuned_part[p];
+    for (int f = 0; f < 3; ++f) {
+      info->solver_ms[p][f] = m->tuned_ms[p][f];
+      info->solver_ms_balanced[p][f] = m->tuned_ms_balanced[p][f];
+    }
   }
+  return DG_OK;
+}
+
+extern "C" int dg_mesh_set_partition(dg_mesh* m, int k) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  if (k < 0 || k >= m->n_parts) return fail(DG_EINVAL, "cell partition not built for this mesh");
+  set_partition(m, k);
+  m->tuned_part[0] = m->tuned_part[1] = k;  // the steps' partition too, until the autotuner next runs
   return DG_OK;
 }
 

@@ -296,14 +296,14 @@ template <int DIM, int DEG, typename T, class Sync, class Epi, class Fin>
 __device__ __forceinline__ void pmatvec_epi(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p,
                                             T scale, Epi& epi, Fin& fin, T* gv, Sync& sg, T* scell, T* sJ,
                                             const T* sD, const T* sDw, const T* sII, PhaseClock& pc) {
-  using S = Shape<DIM, DEG>;
-  const int64_t nb = (mv.n_cells + S::CPB - 1) / S::CPB;
+  const int64_t nb = mv.nbat;
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-    grad_cell_batch<DIM, DEG, T>(mv, p, h, gv, bt, scell, sJ, sD, sII);
+    grad_cell_batch<DIM, DEG, T>(mv, p, h, gv, batch_range(mv, bt), scell, sJ, sD, sII);
   sg.sync();
   pc.mark(PH_GRAD_CELL);
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-    div_cell_batch<DIM, DEG, T, true, Epi>(mv, gv, p, alpha, scale, ident, epi, bt, scell, sJ, sDw, sII);
+    div_cell_batch<DIM, DEG, T, true, Epi>(mv, gv, p, alpha, scale, ident, epi, batch_range(mv, bt), scell, sJ,
+                                           sDw, sII);
   fin();
   sg.sync();
   pc.mark(PH_DIV_CELL);
@@ -1423,13 +1423,20 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     const float floor2 = fmaxf((float)sc[6], 1e-30f);
     constexpr float kGrowth2 = 1e8f;  // (1e4)^2
     double rho = rho0;
-    const int64_t nb = (a.mvk.n_cells + S::CPB - 1) / S::CPB;
+    const int64_t nb = a.mvk.nbat;
     bool have_prev = false;  // residual partials of the previous step are waiting in a.partial
+    // with at most one cell batch per CTA (the usual case on meshes that fit the launch), the
+    // CTA's batch range is read once for the whole cycle (kept in shared memory: registers are
+    // the scarce resource of this loop)
+    const bool one = nb <= sg.size;
+    __shared__ int4 s_mine;
+    if (threadIdx.x == 0) s_mine = one && sg.rank < nb ? a.mvk.bdesc[sg.rank] : make_int4(0, 0, 0, 0);
+    __syncthreads();
     // per-CTA pass clocks (profiling): own gradient and divergence work, before the grid barriers
     unsigned long long* cta_clock = a.phase ? a.phase + 16 : nullptr;
-    if (cta_clock && sg.rank < kCtaClocks) {
-      const unsigned cm = sg.rank < nb ? batch_coarse_mask<DIM, DEG, TK>(a.mvk, sg.rank) : 0u;
-      if (threadIdx.x == 0) cta_clock[2 * kCtaClocks + sg.rank] = cm ? 1ull : 0ull;
+    if (cta_clock && sg.rank < kCtaClocks && threadIdx.x == 0) {
+      const bool cm = sg.rank < nb && a.mvk.bdesc[sg.rank].w > a.mvk.bdesc[sg.rank].z;
+      cta_clock[2 * kCtaClocks + sg.rank] = cm ? 1ull : 0ull;
     }
     while (true) {
       // the next step's recurrence coefficients, by one thread, while the others start the
@@ -1450,7 +1457,9 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         for (int i = threadIdx.x; i < G; i += blockDim.x) pv += ((const float*)a.partial)[i];
       const unsigned long long tg0 = cta_clock ? PhaseClock::now() : 0ull;
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-        grad_cell_batch<DIM, DEG, TK>(a.mvk, d, a.hk, gvk, bt, scellk, sJk, sDk, sIIk);
+        grad_cell_batch<DIM, DEG, TK>(a.mvk, d, a.hk, gvk,
+                                      one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt),
+                                      scellk, sJk, sDk, sIIk);
       if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks) cta_clock[sg.rank] += PhaseClock::now() - tg0;
       if (have_prev) {
         const float rn2 = block_allsum_f(pv, sred);  // (||r|| / beta)^2
@@ -1487,8 +1496,10 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       };
       const unsigned long long td0 = cta_clock ? PhaseClock::now() : 0ull;
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-        div_cell_batch<DIM, DEG, TK, true>(a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi, bt, scellk, sJk, sDwk,
-                                           sIIk);
+        div_cell_batch<DIM, DEG, TK, true>(
+            a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi,
+            one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt), scellk, sJk, sDwk,
+            sIIk);
       if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks)
         cta_clock[kCtaClocks + sg.rank] += PhaseClock::now() - td0;
       if (want) {

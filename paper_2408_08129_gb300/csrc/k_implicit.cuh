@@ -88,56 +88,45 @@ __host__ __device__ constexpr int coarse_buffer() {
   return Shape<DIM, DEG>::CPB * NV * coarse_points<DIM, DEG>() * kCoarseSlots;
 }
 
-// OR over the cells of batch `batch` of their coarse-side face masks, and the
-// largest number of coarse faces of one cell (in *nmax), formed by every warp
-// on its own (lanes load one or two cells' masks and reduce), so that the
-// whole block agrees without a barrier
-template <int DIM, int DEG, typename T>
-__device__ __forceinline__ unsigned batch_coarse_mask(const MeshView<T>& mv, int64_t batch, int* nmax = nullptr) {
-  constexpr int CPB = Shape<DIM, DEG>::CPB;
-  const int lane = threadIdx.x & 31;
-  unsigned m = 0u, k = 0u;
-  for (int j = lane; j < CPB; j += 32) {
-    const int64_t c = batch * CPB + j;
-    if (c < mv.n_cells) {
-      const unsigned cm = (unsigned)mv.cell_cmask[c];
-      m |= cm;
-      k = max(k, (unsigned)__popc(cm));
-    }
-  }
-  if (nmax) *nmax = (int)__reduce_max_sync(0xffffffffu, k);
-  return __reduce_or_sync(0xffffffffu, m);
+// One cell batch of the mesh's active partition: cells [c0, c1) (at most
+// CPB), coarse-side entries [e0, e1) (MeshView::bdesc, one 16-byte load).
+struct BatchRange {
+  int c0, c1, e0, e1;
+};
+template <typename T>
+__device__ __forceinline__ BatchRange batch_range(const MeshView<T>& mv, int64_t b) {
+  const int4 v = mv.bdesc[b];
+  return BatchRange{v.x, v.y, v.z, v.w};
 }
 
 // Coarse sides of the batch's 2:1 faces, through the batch's entry list
-// (MeshView::cb_start, ce_*).  A round takes FPR coarse faces (slots) of the
-// batch, one fine point per thread (EPR = FPR * NP threads): coarse_fill
-// writes the NV face values of each point to buf[v * EPR + k] (k = the
-// point's place in the round), reading global memory only, so that round 0
-// is filled before the batch's first barrier and its loads overlap the
-// batch's own; after a barrier, coarse_sum adds at each node on a coarse face
-// of the round sum_s sum_q sign * It * value to acc[0..NV).
+// (MeshView::bdesc, ce_*).  A round takes FPR coarse faces (slots) of the
+// batch, EPR = FPR * NP fine points, the threads taking them in turn:
+// coarse_fill writes the NV face values of each point to buf[v * EPR + k]
+// (k = the point's place in the round), reading global memory only, so that
+// round 0 is filled before the batch's first barrier and its loads overlap
+// the batch's own; after a barrier, coarse_sum adds at each node on a coarse
+// face of the round sum_s sum_q sign * It * value to acc[0..NV).
 template <int DIM, int DEG>
 struct CoarseRounds {
   using S = Shape<DIM, DEG>;
   static constexpr int NP = coarse_points<DIM, DEG>();
-  static constexpr int FPR =
-      S::THREADS / NP < S::CPB * kCoarseSlots ? S::THREADS / NP : S::CPB * kCoarseSlots;  // slots per round
-  static constexpr int EPR = FPR * NP;                                                     // points per round
-  static_assert(FPR >= 1, "a coarse face's fine points must fit one block");
+  static constexpr int FPR = S::CPB * kCoarseSlots;  // slots per round (the buffer's capacity)
+  static constexpr int EPR = FPR * NP;               // points per round
   __device__ __forceinline__ static int rounds(int e0, int e1) { return ((e1 - e0) / NP + FPR - 1) / FPR; }
 };
 
 // point(cc, lf, s, q, node, w, val): the NV values at fine point q of subface
 // s of local face lf of batch cell cc (the fine side's node `node`, w = 1/2 |N| n there)
 template <int DIM, int DEG, typename T, int NV, class Point>
-__device__ __forceinline__ void coarse_fill(const MeshView<T>& mv, int64_t batch, int e0, int e1, int r, T* buf,
+__device__ __forceinline__ void coarse_fill(const MeshView<T>& mv, const BatchRange& br, int r, T* buf,
                                             Point&& point) {
   using R = CoarseRounds<DIM, DEG>;
-  constexpr int NF = Shape<DIM, DEG>::NF, CPB = Shape<DIM, DEG>::CPB;
-  const int k = threadIdx.x;
-  const int e = e0 + r * R::EPR + k;
-  if (k < R::EPR && e < e1) {
+  constexpr int NF = Shape<DIM, DEG>::NF;
+  const int base = br.e0 + r * R::EPR;
+  const int kend = br.e1 - base < R::EPR ? br.e1 - base : R::EPR;
+  for (int k = threadIdx.x; k < kend; k += blockDim.x) {
+    const int e = base + k;
     const int meta = mv.ce_meta[e];
     const int node = mv.ce_node[e];
     T w[DIM];
@@ -145,7 +134,7 @@ __device__ __forceinline__ void coarse_fill(const MeshView<T>& mv, int64_t batch
     for (int b = 0; b < DIM; ++b) w[b] = mv.ce_w[(int64_t)b * mv.n_ce + e];
     const int j = meta >> 9;
     T val[NV];
-    point((int)batch * CPB + (meta & 63), (meta >> 6) & 7, j / NF, j % NF, node, w, val);
+    point(br.c0 + (meta & 63), (meta >> 6) & 7, j / NF, j % NF, node, w, val);
 #pragma unroll
     for (int v = 0; v < NV; ++v) buf[v * R::EPR + k] = val[v];
   }
@@ -182,13 +171,13 @@ __device__ __forceinline__ void coarse_sum(int coarse, int r, const int* id, con
 // The rounds after round 0 (rare: more coarse faces in one batch than a round
 // holds), each between block barriers; called by the whole block.
 template <int DIM, int DEG, typename T, int NV, class Point>
-__device__ __forceinline__ void coarse_more_rounds(const MeshView<T>& mv, int64_t batch, int e0, int e1, int coarse,
+__device__ __forceinline__ void coarse_more_rounds(const MeshView<T>& mv, const BatchRange& br, int coarse,
                                                    const int* id, const T* sIt, T sign, T* buf, T* acc,
                                                    Point&& point) {
-  const int nr = CoarseRounds<DIM, DEG>::rounds(e0, e1);
+  const int nr = CoarseRounds<DIM, DEG>::rounds(br.e0, br.e1);
   for (int r = 1; r < nr; ++r) {
     __syncthreads();
-    coarse_fill<DIM, DEG, T, NV>(mv, batch, e0, e1, r, buf, point);
+    coarse_fill<DIM, DEG, T, NV>(mv, br, r, buf, point);
     __syncthreads();
     coarse_sum<DIM, DEG, T, NV>(coarse, r, id, sIt, sign, buf, acc);
   }
@@ -235,20 +224,20 @@ __device__ __forceinline__ T half_sign(int a, const int* id) {
   return id[a] == DEG ? T(0.5) : T(-0.5);
 }
 
-// Cells [batch*CPB, batch*CPB + CPB): g_b = h [sum_a Ja^a_b (D_a p) + face_b / w_end] / J.
+// Cells [br.c0, br.c1): g_b = h [sum_a Ja^a_b (D_a p) + face_b / w_end] / J.
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 // sII holds the interpolation tables I (2 N^2) followed by It (2 N^2); sJ is
 // the coarse-pass buffer (coarse_buffer<DIM, DEG, DIM>() elements).
 // GZ: metric terms from the heights (metric_from_z), staged in sz (CPB*NC).
 template <int DIM, int DEG, typename T, bool GZ = false>
 __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
-                                                const T* __restrict__ h, T* __restrict__ g, int64_t batch, T* sp,
-                                                T* sJ, const T* sD, const T* sII, T* sz = nullptr) {
+                                                const T* __restrict__ h, T* __restrict__ g, const BatchRange& br,
+                                                T* sp, T* sJ, const T* sD, const T* sII, T* sz = nullptr) {
   using S = Shape<DIM, DEG>;
-  constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
+  constexpr int N = S::N, NC = S::NC;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int c = (int)batch * CPB + lc;
-  const bool active = (lc < CPB) && (c < mv.n_cells);
+  const int c = br.c0 + lc;
+  const bool active = c < br.c1;
   const int64_t Nn = mv.n_nodes;
   const int idx = c * NC + i;
   int id[3] = {i % N, (i / N) % N, i / (N * N)};
@@ -257,7 +246,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   T po[DIM];  // the other side's value at this node's faces
   T scale = T(0), pv = T(0);
   int coarse = 0;
-  const int e0 = mv.cb_start[batch], e1 = mv.cb_start[batch + 1];
+  const bool has_coarse = br.e1 > br.e0;
   if (active) {
     pv = p[idx];
     sp[lc * NC + i] = pv;
@@ -287,7 +276,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
 #pragma unroll
     for (int b = 0; b < DIM; ++b) val[b] = jmp * w[b];
   };
-  if (e1 > e0) coarse_fill<DIM, DEG, T, DIM>(mv, batch, e0, e1, 0, sJ, gpoint);
+  if (has_coarse) coarse_fill<DIM, DEG, T, DIM>(mv, br, 0, sJ, gpoint);
   __syncthreads();
   T facc[DIM], dp[DIM];
 #pragma unroll
@@ -319,9 +308,9 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
     }
   }
   // coarse sides: the values of round 0 are in sJ since the barrier above
-  if (e1 > e0) {
+  if (has_coarse) {
     coarse_sum<DIM, DEG, T, DIM>(coarse, 0, id, sII + 2 * N * N, T(1), sJ, facc);
-    coarse_more_rounds<DIM, DEG, T, DIM>(mv, batch, e0, e1, coarse, id, sII + 2 * N * N, T(1), sJ, facc, gpoint);
+    coarse_more_rounds<DIM, DEG, T, DIM>(mv, br, coarse, id, sII + 2 * N * N, T(1), sJ, facc, gpoint);
   }
   if (active) {
     const T iwend = mv.tab[S::T_IWEND];
@@ -346,13 +335,13 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
 template <int DIM, int DEG, typename T, bool HELM, class Epi, bool GZ = false>
 __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
                                                const T* __restrict__ p, T alpha, T scale, T ident, Epi& epi,
-                                               int64_t batch, T* sF, T* sJ, const T* sDw, const T* sII,
+                                               const BatchRange& br, T* sF, T* sJ, const T* sDw, const T* sII,
                                                T* sz = nullptr, const T* sD = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
-  const int c = (int)batch * CPB + lc;
-  const bool active = (lc < CPB) && (c < mv.n_cells);
+  const int c = br.c0 + lc;
+  const bool active = c < br.c1;
   const int64_t Nn = mv.n_nodes;
   const int idx = c * NC + i;
   int id[3] = {i % N, (i / N) % N, i / (N * N)};
@@ -362,7 +351,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   T ij = T(0), pv = T(0);
   T Jl[DIM][DIM];
   int coarse = 0;
-  const int e0 = mv.cb_start[batch], e1 = mv.cb_start[batch + 1];
+  const bool has_coarse = br.e1 > br.e0;
   if (active) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fv[b] = (fld + b * Nn)[idx];
@@ -396,7 +385,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     for (int b = 0; b < DIM; ++b) sum += ((fld + b * Nn)[node] + fc[b]) * w[b];
     val[0] = sum;
   };
-  if (e1 > e0) coarse_fill<DIM, DEG, T, 1>(mv, batch, e0, e1, 0, sJ, dpoint);
+  if (has_coarse) coarse_fill<DIM, DEG, T, 1>(mv, br, 0, sJ, dpoint);
   if (GZ) {
     __syncthreads();
     if (active) {
@@ -443,9 +432,9 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     }
   }
   // coarse sides: the values of round 0 are in sJ since the barrier above
-  if (e1 > e0) {
+  if (has_coarse) {
     coarse_sum<DIM, DEG, T, 1>(coarse, 0, id, sII + 2 * N * N, T(-1), sJ, &facc);
-    coarse_more_rounds<DIM, DEG, T, 1>(mv, batch, e0, e1, coarse, id, sII + 2 * N * N, T(-1), sJ, &facc, dpoint);
+    coarse_more_rounds<DIM, DEG, T, 1>(mv, br, coarse, id, sII + 2 * N * N, T(-1), sJ, &facc, dpoint);
   }
   if (active) {
     const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
@@ -489,7 +478,7 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_cell_kernel(Mes
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sD[q] = mv.tab[S::T_D + q];
   for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
   __syncthreads();  // the fine-side traces read the interpolation tables before the batch's first barrier
-  grad_cell_batch<DIM, DEG, T, GZ>(mv, p, h, g, blockIdx.x, sp, sJ, sD, sII, sz);
+  grad_cell_batch<DIM, DEG, T, GZ>(mv, p, h, g, batch_range(mv, blockIdx.x), sp, sJ, sD, sII, sz);
 }
 
 template <int DIM, int DEG, typename T, bool HELM, bool GZ>
@@ -514,8 +503,8 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(Mesh
   for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
   __syncthreads();
   StoreOut<T> epi{out};
-  div_cell_batch<DIM, DEG, T, HELM, StoreOut<T>, GZ>(mv, f, p, alpha, T(1), T(1), epi, blockIdx.x, sF, sJ, sDw,
-                                                     sII, sz, sD);
+  div_cell_batch<DIM, DEG, T, HELM, StoreOut<T>, GZ>(mv, f, p, alpha, T(1), T(1), epi, batch_range(mv, blockIdx.x),
+                                                     sF, sJ, sDw, sII, sz, sD);
 }
 
 }  // namespace dg

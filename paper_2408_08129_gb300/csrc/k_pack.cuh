@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_pack_kernel(con
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sD[q] = mv.tab[S::T_D + q];
   for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
   __syncthreads();  // the fine-side traces read the interpolation tables before the batch's first barrier
-  grad_cell_batch<DIM, DEG, T, false>(mv, P.in[j], P.aux[j], P.out[j], blockIdx.x - P.start[j], sp, sJ, sD, sII);
+  grad_cell_batch<DIM, DEG, T, false>(mv, P.in[j], P.aux[j], P.out[j], batch_range(mv, blockIdx.x - P.start[j]), sp,
+                                      sJ, sD, sII);
 }
 
 template <int DIM, int DEG, typename T>
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_pack_kernel(cons
   __syncthreads();
   StoreOut<T> epi{P.out[j]};
   div_cell_batch<DIM, DEG, T, false, StoreOut<T>, false>(mv, P.in[j], nullptr, T(0), T(1), T(1), epi,
-                                                        blockIdx.x - P.start[j], sF, sJ, sDw, sII);
+                                                        batch_range(mv, blockIdx.x - P.start[j]), sF, sJ, sDw, sII);
 }
 
 }  // namespace dg

@@ -55,7 +55,7 @@ template <int DIM, int DEG, typename T>
 int run_grad(const dg_mesh* m, const T* p, const T* h, T* g, cudaStream_t s, const int* skip) {
   using S = Shape<DIM, DEG>;
   const MeshView<T>& mv = view<T>(m);
-  const unsigned nb = blocks_for(mv.n_cells, S::CPB);
+  const unsigned nb = (unsigned)mv.nbat;
   count_launches(m->ctx, 1);
   if (std::is_same<T, float>::value && mv.geo_z)
     grad_cell_kernel<DIM, DEG, T, true><<<nb, S::THREADS, 0, s>>>(mv, p, h, g, skip);
@@ -68,7 +68,7 @@ template <int DIM, int DEG, typename T, bool HELM>
 int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, cudaStream_t s, const int* skip) {
   using S = Shape<DIM, DEG>;
   const MeshView<T>& mv = view<T>(m);
-  const unsigned nb = blocks_for(mv.n_cells, S::CPB);
+  const unsigned nb = (unsigned)mv.nbat;
   count_launches(m->ctx, 1);
   if (std::is_same<T, float>::value && mv.geo_z)
     div_cell_kernel<DIM, DEG, T, HELM, true><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
@@ -114,7 +114,7 @@ int run_grad_pack(dg_ctx* ctx, OpPack<T>& P, cudaStream_t s) {
   int nb = 0;
   for (int j = 0; j < P.n; ++j) {
     P.start[j] = nb;
-    nb += (int)blocks_for(P.mv[j].n_cells, S::CPB);
+    nb += P.mv[j].nbat;
   }
   P.start[P.n] = nb;
   grad_pack_kernel<DIM, DEG, T><<<nb, S::THREADS, 0, s>>>(P);
@@ -128,7 +128,7 @@ int run_div_pack(dg_ctx* ctx, OpPack<T>& P, cudaStream_t s) {
   int nb = 0;
   for (int j = 0; j < P.n; ++j) {
     P.start[j] = nb;
-    nb += (int)blocks_for(P.mv[j].n_cells, S::CPB);
+    nb += P.mv[j].nbat;
   }
   P.start[P.n] = nb;
   div_pack_kernel<DIM, DEG, T><<<nb, S::THREADS, 0, s>>>(P);

@@ -696,40 +696,60 @@ int phase_solve_single(Member& M, int i, cudaStream_t s) {
   double* out = M.S->solve_out + 4 * M.nsolve;
   ++M.nsolve;
   const bool auto_k = M.o.krylov == DG_KRYLOV_AUTO;
-  if (!auto_k && (M.o.fused >= 0 || persistent_only(M.o.krylov)))
-    return helmholtz_solve(M.S, &M.o, dta * dta, &M.st, out, s);
   const int pi = M.o.precision == DG_FP32 ? 1 : 0;
+  if (!auto_k && (M.o.fused >= 0 || persistent_only(M.o.krylov))) {
+    set_partition(M.m, M.m->tuned_part[pi]);
+    return helmholtz_solve(M.S, &M.o, dta * dta, &M.st, out, s);
+  }
   const int ncand = auto_k ? 3 : 2;
-  float* ms = M.m->tuned_ms[pi];
+  const int nparts = M.m->n_parts;
+  float* ms[2] = {M.m->tuned_ms[pi], M.m->tuned_ms_balanced[pi]};
   bool timed = true;
-  for (int f = 0; f < ncand; ++f) timed = timed && ms[f] > 0.0f;
+  for (int pt = 0; pt < nparts; ++pt)
+    for (int f = 0; f < ncand; ++f) timed = timed && ms[pt][f] > 0.0f;
   dg_solver_opts o = M.o;
   if (timed) {
-    int best = 0;
-    for (int f = 1; f < ncand; ++f)
-      if (ms[f] < ms[best]) best = f;
+    int best = 0, bpart = 0;
+    for (int pt = 0; pt < nparts; ++pt)
+      for (int f = 0; f < ncand; ++f)
+        if (ms[pt][f] < ms[bpart][best]) {
+          best = f;
+          bpart = pt;
+        }
     M.m->tuned_form[pi] = best;
+    M.m->tuned_part[pi] = bpart;
+    set_partition(M.m, bpart);
     apply_form(o, best);
     return helmholtz_solve(M.S, &o, dta * dta, &M.st, out, s);
   }
   dg_state* S = M.S;
   DG_CUDA(cudaMemcpyAsync(S->p_save, S->p, S->Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  cudaEvent_t e[N_FORMS + 1];
+  constexpr int kMaxCand = 2 * N_FORMS;
+  cudaEvent_t e[kMaxCand + 1];
   for (auto& ev : e) DG_CUDA(cudaEventCreate(&ev));
   int rc = DG_OK;
   bool first = true;
   const dg_step_stats st0 = M.st;  // only the last (kept) solve counts in the step's statistics
-  // candidates in the order persistent GMRES, Chebyshev, multi-kernel GMRES (the last one's result is kept)
-  int order[N_FORMS], no = 0;
-  order[no++] = FORM_GMRES_PERSISTENT;
-  if (auto_k) order[no++] = FORM_CHEBYSHEV;
-  order[no++] = FORM_GMRES_MULTI;
+  // candidates: per cell partition, persistent GMRES, Chebyshev, multi-kernel GMRES (the last
+  // one's result is kept: multi-kernel GMRES on the uniform partition)
+  int order[kMaxCand], opart[kMaxCand], no = 0;
+  for (int pt = nparts - 1; pt >= 0; --pt) {
+    order[no] = FORM_GMRES_PERSISTENT;
+    opart[no++] = pt;
+    if (auto_k) {
+      order[no] = FORM_CHEBYSHEV;
+      opart[no++] = pt;
+    }
+    order[no] = FORM_GMRES_MULTI;
+    opart[no++] = pt;
+  }
   for (int round = 0; round < 2 && rc == DG_OK; ++round) {
     for (int c = 0; c < no && rc == DG_OK; ++c) {
       M.st = st0;
       if (!first) DG_CUDA(cudaMemcpyAsync(S->p, S->p_save, S->Nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
       first = false;
       apply_form(o, order[c]);
+      set_partition(M.m, opart[c]);
       if (round == 1) DG_CUDA(cudaEventRecord(e[c], s));
       rc = helmholtz_solve(S, &o, dta * dta, &M.st, out, s);
     }
@@ -737,15 +757,20 @@ int phase_solve_single(Member& M, int i, cudaStream_t s) {
   if (rc == DG_OK) {
     DG_CUDA(cudaEventRecord(e[no], s));
     DG_CUDA(cudaEventSynchronize(e[no]));
-    int best = -1;
+    int best = -1, bpart = 0;
     for (int c = 0; c < no; ++c) {
       float t = 0.0f;
       cudaEventElapsedTime(&t, e[c], e[c + 1]);
-      ms[order[c]] = t > 0.0f ? t : 1e-6f;
-      if (best < 0 || ms[order[c]] < ms[best]) best = order[c];
+      ms[opart[c]][order[c]] = t > 0.0f ? t : 1e-6f;
+      if (best < 0 || ms[opart[c]][order[c]] < ms[bpart][best]) {
+        best = order[c];
+        bpart = opart[c];
+      }
     }
     M.m->tuned_form[pi] = best;
+    M.m->tuned_part[pi] = bpart;
   }
+  set_partition(M.m, M.m->tuned_part[pi]);
   for (auto& ev : e) cudaEventDestroy(ev);
   return rc;
 }
@@ -799,6 +824,7 @@ int prepare_member(Member& M, dg_ctx* ctx, const dg_mesh* m, dg_state* S, double
   M.S = S;
   M.m = m;
   M.dt = dt;
+  set_partition(m, m->tuned_part[M.o.precision == DG_FP32 ? 1 : 0]);
   return DG_OK;
 }
 

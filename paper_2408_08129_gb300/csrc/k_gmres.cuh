@@ -1236,6 +1236,8 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
   TK* sIIk = sDwk + N * N;
   TK* scellk = (TK*)scell64;
   TK* sJk = (TK*)sJ64;
+  // the CTA's own batch for the Chebyshev steps (16-byte aligned, after the tables)
+  auto* bcache = (BatchCache<DIM, DEG, TK>*)(((uintptr_t)(sIIk + 4 * N * N) + 15) & ~(uintptr_t)15);
   load_tables<DIM, DEG, TK>(a, sD64, sDw64, sII64, sDk, sDwk, sIIk);
   PhaseClock pc{record ? a.phase : nullptr, PhaseClock::now()};
   const int64_t n = a.n;
@@ -1432,6 +1434,12 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     __shared__ int4 s_mine;
     if (threadIdx.x == 0) s_mine = one && sg.rank < nb ? a.mvk.bdesc[sg.rank] : make_int4(0, 0, 0, 0);
     __syncthreads();
+    // ... and its face links and coarse-side entries (BatchCache)
+    const BatchCache<DIM, DEG, TK>* bc = nullptr;
+    if (one && sg.rank < nb) {
+      batch_cache_fill<DIM, DEG, TK>(a.mvk, BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w}, bcache);
+      bc = bcache;
+    }
     // per-CTA pass clocks (profiling): own gradient and divergence work, before the grid barriers
     unsigned long long* cta_clock = a.phase ? a.phase + 16 : nullptr;
     if (cta_clock && sg.rank < kCtaClocks && threadIdx.x == 0) {
@@ -1459,7 +1467,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         grad_cell_batch<DIM, DEG, TK>(a.mvk, d, a.hk, gvk,
                                       one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt),
-                                      scellk, sJk, sDk, sIIk);
+                                      scellk, sJk, sDk, sIIk, nullptr, bc);
       if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks) cta_clock[sg.rank] += PhaseClock::now() - tg0;
       if (have_prev) {
         const float rn2 = block_allsum_f(pv, sred);  // (||r|| / beta)^2
@@ -1499,7 +1507,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         div_cell_batch<DIM, DEG, TK, true>(
             a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi,
             one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt), scellk, sJk, sDwk,
-            sIIk);
+            sIIk, nullptr, nullptr, bc);
       if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks)
         cta_clock[kCtaClocks + sg.rank] += PhaseClock::now() - td0;
       if (want) {
@@ -1593,7 +1601,7 @@ inline size_t gmres_smem_bytes(int m) {
   const size_t dbl = (size_t)(m + 1) + 2 * (size_t)(m + 2) + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m +
                      (m + 1) + 32 + 8 + 512;
   const size_t tabs = (size_t)(6 * N * N + DIM * S::CPB * S::NC + coarse_buffer<DIM, DEG, DIM>()) * sizeof(double) +
-                      (size_t)(6 * N * N) * sizeof(TK);
+                      (size_t)(6 * N * N) * sizeof(TK) + sizeof(BatchCache<DIM, DEG, TK>) + 16;
   const size_t gm = dbl * sizeof(double) + 4 * sizeof(int) + tabs + 64;
   const size_t d1 = 2 * (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 5 * (size_t)(m + 1) + 32 + 8;
   const size_t g1 = d1 * sizeof(double) + 4 * sizeof(int) + tabs + 64;

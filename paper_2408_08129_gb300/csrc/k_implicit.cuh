@@ -116,22 +116,39 @@ struct CoarseRounds {
   __device__ __forceinline__ static int rounds(int e0, int e1) { return ((e1 - e0) / NP + FPR - 1) / FPR; }
 };
 
+// A CTA's own cell batch, read once for a whole Krylov cycle of a persistent
+// solve when the CTA has exactly one batch: the face links and coarse-face
+// word of each thread's node, and the batch's round-0 coarse-side entries.
+// The passes then read these from shared memory instead of global memory,
+// which takes one dependent global load off each pass's critical path.
+template <int DIM, int DEG, typename T>
+struct BatchCache {
+  using S = Shape<DIM, DEG>;
+  static constexpr int EPR = CoarseRounds<DIM, DEG>::EPR;
+  int links[DIM * S::THREADS];
+  int coarse[S::THREADS];
+  int meta[EPR];
+  int node[EPR];
+  T w[DIM * EPR];
+};
+
 // point(cc, lf, s, q, node, w, val): the NV values at fine point q of subface
 // s of local face lf of batch cell cc (the fine side's node `node`, w = 1/2 |N| n there)
 template <int DIM, int DEG, typename T, int NV, class Point>
 __device__ __forceinline__ void coarse_fill(const MeshView<T>& mv, const BatchRange& br, int r, T* buf,
-                                            Point&& point) {
+                                            Point&& point, const BatchCache<DIM, DEG, T>* bc = nullptr) {
   using R = CoarseRounds<DIM, DEG>;
   constexpr int NF = Shape<DIM, DEG>::NF;
   const int base = br.e0 + r * R::EPR;
   const int kend = br.e1 - base < R::EPR ? br.e1 - base : R::EPR;
+  const bool cached = bc && r == 0;
   for (int k = threadIdx.x; k < kend; k += blockDim.x) {
     const int e = base + k;
-    const int meta = mv.ce_meta[e];
-    const int node = mv.ce_node[e];
+    const int meta = cached ? bc->meta[k] : mv.ce_meta[e];
+    const int node = cached ? bc->node[k] : mv.ce_node[e];
     T w[DIM];
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) w[b] = mv.ce_w[(int64_t)b * mv.n_ce + e];
+    for (int b = 0; b < DIM; ++b) w[b] = cached ? bc->w[b * R::EPR + k] : mv.ce_w[(int64_t)b * mv.n_ce + e];
     const int j = meta >> 9;
     T val[NV];
     point(br.c0 + (meta & 63), (meta >> 6) & 7, j / NF, j % NF, node, w, val);
@@ -224,6 +241,41 @@ __device__ __forceinline__ T half_sign(int a, const int* id) {
   return id[a] == DEG ? T(0.5) : T(-0.5);
 }
 
+// Fill bc for batch br (whole block; ends with a block barrier).
+template <int DIM, int DEG, typename T>
+__device__ __forceinline__ void batch_cache_fill(const MeshView<T>& mv, const BatchRange& br,
+                                                 BatchCache<DIM, DEG, T>* bc) {
+  using S = Shape<DIM, DEG>;
+  using R = CoarseRounds<DIM, DEG>;
+  constexpr int N = S::N, NC = S::NC;
+  const int t = threadIdx.x;
+  if (t < S::THREADS) {
+    const int lc = t / NC, i = t % NC;
+    const int c = br.c0 + lc;
+    int id[3] = {i % N, (i / N) % N, i / (N * N)};
+    int links[DIM];
+    if (c < br.c1) {
+      load_face_links<DIM, DEG, T>(mv, c, id, links);
+      bc->coarse[t] = mv.cell_coarse[c];
+    } else {
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) links[a] = 3;
+      bc->coarse[t] = 0;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) bc->links[a * S::THREADS + t] = links[a];
+  }
+  const int kend = br.e1 - br.e0 < R::EPR ? br.e1 - br.e0 : R::EPR;
+  for (int k = t; k < kend; k += blockDim.x) {
+    const int e = br.e0 + k;
+    bc->meta[k] = mv.ce_meta[e];
+    bc->node[k] = mv.ce_node[e];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) bc->w[b * R::EPR + k] = mv.ce_w[(int64_t)b * mv.n_ce + e];
+  }
+  __syncthreads();
+}
+
 // Cells [br.c0, br.c1): g_b = h [sum_a Ja^a_b (D_a p) + face_b / w_end] / J.
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 // sII holds the interpolation tables I (2 N^2) followed by It (2 N^2); sJ is
@@ -232,7 +284,8 @@ __device__ __forceinline__ T half_sign(int a, const int* id) {
 template <int DIM, int DEG, typename T, bool GZ = false>
 __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
                                                 const T* __restrict__ h, T* __restrict__ g, const BatchRange& br,
-                                                T* sp, T* sJ, const T* sD, const T* sII, T* sz = nullptr) {
+                                                T* sp, T* sJ, const T* sD, const T* sII, T* sz = nullptr,
+                                                const BatchCache<DIM, DEG, T>* bc = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
@@ -250,8 +303,14 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   if (active) {
     pv = p[idx];
     sp[lc * NC + i] = pv;
-    load_face_links<DIM, DEG, T>(mv, c, id, links);
-    coarse = mv.cell_coarse[c];
+    if (bc) {
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) links[a] = bc->links[a * S::THREADS + threadIdx.x];
+      coarse = bc->coarse[threadIdx.x];
+    } else {
+      load_face_links<DIM, DEG, T>(mv, c, id, links);
+      coarse = mv.cell_coarse[c];
+    }
     if (GZ) {
       sz[lc * NC + i] = mv.zdev[idx];
       scale = h ? h[idx] : T(1);
@@ -276,7 +335,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
 #pragma unroll
     for (int b = 0; b < DIM; ++b) val[b] = jmp * w[b];
   };
-  if (has_coarse) coarse_fill<DIM, DEG, T, DIM>(mv, br, 0, sJ, gpoint);
+  if (has_coarse) coarse_fill<DIM, DEG, T, DIM>(mv, br, 0, sJ, gpoint, bc);
   __syncthreads();
   T facc[DIM], dp[DIM];
 #pragma unroll
@@ -336,7 +395,8 @@ template <int DIM, int DEG, typename T, bool HELM, class Epi, bool GZ = false>
 __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
                                                const T* __restrict__ p, T alpha, T scale, T ident, Epi& epi,
                                                const BatchRange& br, T* sF, T* sJ, const T* sDw, const T* sII,
-                                               T* sz = nullptr, const T* sD = nullptr) {
+                                               T* sz = nullptr, const T* sD = nullptr,
+                                               const BatchCache<DIM, DEG, T>* bc = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
@@ -355,8 +415,14 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
   if (active) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) fv[b] = (fld + b * Nn)[idx];
-    load_face_links<DIM, DEG, T>(mv, c, id, links);
-    coarse = mv.cell_coarse[c];
+    if (bc) {
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) links[a] = bc->links[a * S::THREADS + threadIdx.x];
+      coarse = bc->coarse[threadIdx.x];
+    } else {
+      load_face_links<DIM, DEG, T>(mv, c, id, links);
+      coarse = mv.cell_coarse[c];
+    }
     if (HELM) pv = p[idx];
     if (GZ) {
       sz[lc * NC + i] = mv.zdev[idx];
@@ -385,7 +451,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     for (int b = 0; b < DIM; ++b) sum += ((fld + b * Nn)[node] + fc[b]) * w[b];
     val[0] = sum;
   };
-  if (has_coarse) coarse_fill<DIM, DEG, T, 1>(mv, br, 0, sJ, dpoint);
+  if (has_coarse) coarse_fill<DIM, DEG, T, 1>(mv, br, 0, sJ, dpoint, bc);
   if (GZ) {
     __syncthreads();
     if (active) {

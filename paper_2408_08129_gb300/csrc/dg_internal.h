@@ -92,7 +92,8 @@ struct MeshView {
   // coarse-side entries [bdesc[b].z, bdesc[b].w): per cell in order, per
   // coarse local face in order (a slot), per fine point j = s NF + q of the
   // face's subfaces; ce_meta = lc | lf << 6 | j << 9, ce_node = the fine-side
-  // node, ce_w[b * n_ce + e] = 1/2 |N| n_b at it.  cell_coarse[c] =
+  // node, ce_w[b * n_ce + e] = 1/2 |N| n_b / w_end at it (w_end the GLL end
+  // weight: the face terms enter the cell passes divided by it).  cell_coarse[c] =
   // coarse-face mask | (batch slot of the cell's first one) << 8.
   const int4* bdesc;
   int nbat;

@@ -741,10 +741,12 @@ int build_mesh(dg_mesh* m) {
     for (int lf = 0; lf < 2 * dim; ++lf)
       if ((cell_face[c * 2 * dim + lf] & 3) == 2) cell_cmask[c] |= 1 << lf;
   // Coarse sides of the 2:1 faces per cell, in cell order and local-face order: each coarse
-  // face's NSUB NF fine points (j = s NF + q), the fine node and 1/2 |N| n there (fsj fn / 2);
+  // face's NSUB NF fine points (j = s NF + q), the fine node and 1/2 |N| n / w_end there
+  // (fsj fn / (2 w_end), w_end the GLL end weight);
   // the cell batches (partitions) index these lists.  Work per cell for the balanced partition:
   // its nodes, plus one per coarse-side point and per fine-side face node.
   const int nsubf = 1 << (dim - 1), np_c = nsubf * NF;
+  const double iwend = 1.0 / tab.w[0];  // the face terms enter the cell passes divided by the end weight
   CoarseLists cl;
   cl.dim = dim;
   cl.np = np_c;
@@ -761,7 +763,7 @@ int build_mesh(dg_mesh* m) {
       for (int j = 0; j < np_c; ++j) {
         const size_t t = (size_t)(f + j / NF) * NF + (size_t)(j % NF);
         cl.node.push_back(fnode_m[t]);
-        for (int b = 0; b < dim; ++b) cl.w.push_back(0.5 * fsj[t] * fn[(size_t)b * nf * NF + t]);
+        for (int b = 0; b < dim; ++b) cl.w.push_back(0.5 * fsj[t] * fn[(size_t)b * nf * NF + t] * iwend);
       }
       cl.cost[c] += np_c;
     }

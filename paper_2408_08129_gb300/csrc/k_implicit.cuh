@@ -133,7 +133,7 @@ struct BatchCache {
 };
 
 // point(cc, lf, s, q, node, w, val): the NV values at fine point q of subface
-// s of local face lf of batch cell cc (the fine side's node `node`, w = 1/2 |N| n there)
+// s of local face lf of batch cell cc (the fine side's node `node`, w = 1/2 |N| n / w_end there)
 template <int DIM, int DEG, typename T, int NV, class Point>
 __device__ __forceinline__ void coarse_fill(const MeshView<T>& mv, const BatchRange& br, int r, T* buf,
                                             Point&& point, const BatchCache<DIM, DEG, T>* bc = nullptr) {
@@ -233,12 +233,13 @@ __device__ __forceinline__ void other_trace(const T* __restrict__ X, int64_t vst
   }
 }
 
-// Outward face normal |N| n of node id on its face along axis a, times 1/2:
-// the node's own metric row +-Ja[a] / 2 (the same face seen from either side
-// of a conforming face; on a 2:1 face the fine side's).
+// Outward face normal |N| n of node id on its face along axis a, times
+// 1/(2 w_end): the node's own metric row +-Ja[a] / 2 (the same face seen from
+// either side of a conforming face; on a 2:1 face the fine side's), with the
+// lifting factor 1/w_end of the face term folded in (hw = 1/(2 w_end)).
 template <int DIM, int DEG, typename T>
-__device__ __forceinline__ T half_sign(int a, const int* id) {
-  return id[a] == DEG ? T(0.5) : T(-0.5);
+__device__ __forceinline__ T half_sign(int a, const int* id, T hw) {
+  return id[a] == DEG ? hw : -hw;
 }
 
 // Fill bc for batch br (whole block; ends with a block barrier).
@@ -326,7 +327,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
     for (int a = 0; a < DIM; ++a)
       if ((links[a] & 3) < 2) other_trace<DIM, DEG, T, 1>(p, 0, links[a], a, id, sII, &po[a]);
   }
-  // coarse sides, round 0: the jump at each fine point times 1/2 |N| n, from the fine value and
+  // coarse sides, round 0: the jump at each fine point times 1/2 |N| n / w_end, from the fine value and
   // the coarse cell's polynomial
   auto gpoint = [&](int cc, int lf, int s, int q, int node, const T* w, T* val) {
     T pp;
@@ -337,7 +338,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   };
   if (has_coarse) coarse_fill<DIM, DEG, T, DIM>(mv, br, 0, sJ, gpoint, bc);
   __syncthreads();
-  T facc[DIM], dp[DIM];
+  T facc[DIM], dp[DIM];  // facc: the face terms, already divided by w_end
 #pragma unroll
   for (int b = 0; b < DIM; ++b) facc[b] = dp[b] = T(0);
   if (GZ && active) {
@@ -356,12 +357,13 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
       for (int kk = 0; kk < N; ++kk) s += D[kk] * sp[i0 + kk * stride];
       dp[a] = s;
     }
-    // face terms: 1/2 (p_other - p_own) |N| n on conforming and fine-side faces (zero jump on
-    // walls, p^ = p-; coarse sides in the coarse pass)
+    // face terms: 1/2 (p_other - p_own) |N| n / w_end on conforming and fine-side faces (zero
+    // jump on walls, p^ = p-; coarse sides in the coarse pass)
+    const T hw = T(0.5) * mv.tab[S::T_IWEND];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if ((links[a] & 3) >= 2) continue;
-      const T jmp = half_sign<DIM, DEG, T>(a, id) * (po[a] - pv);
+      const T jmp = half_sign<DIM, DEG, T>(a, id, hw) * (po[a] - pv);
 #pragma unroll
       for (int b = 0; b < DIM; ++b) facc[b] += jmp * Jl[a][b];
     }
@@ -372,10 +374,9 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
     coarse_more_rounds<DIM, DEG, T, DIM>(mv, br, coarse, id, sII + 2 * N * N, T(1), sJ, facc, gpoint);
   }
   if (active) {
-    const T iwend = mv.tab[S::T_IWEND];
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
-      T s = facc[b] * iwend;
+      T s = facc[b];
 #pragma unroll
       for (int a = 0; a < DIM; ++a) s += Jl[a][b] * dp[a];
       (g + b * Nn)[idx] = s * scale;
@@ -441,7 +442,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       }
     }
   }
-  // coarse sides, round 0: |N| {f}.n / 2 at each fine point from the fine value and the coarse
+  // coarse sides, round 0: |N| {f}.n / (2 w_end) at each fine point from the fine value and the coarse
   // cell's polynomial
   auto dpoint = [&](int cc, int lf, int s, int q, int node, const T* w, T* val) {
     T fc[DIM];
@@ -482,19 +483,21 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       for (int kk = 0; kk < N; ++kk) acc -= Dw[kk] * sF[i0 + kk * stride];
     }
   }
-  T facc = T(0);
-  // face terms: 1/2 (f_own + f_other).|N| n on conforming and fine-side faces (zero normal
-  // flux on walls; coarse sides in the coarse pass)
+  T facc = T(0);  // the face terms, already divided by w_end
+  // face terms: 1/2 (f_own + f_other).|N| n / w_end on conforming and fine-side faces (zero
+  // normal flux on walls; coarse sides in the coarse pass); f_own.|N| n is the node's own
+  // contravariant component ft[a]
   if (active) {
+    const T hw = T(0.5) * mv.tab[S::T_IWEND];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if ((links[a] & 3) >= 2) continue;
       T fo[DIM];
       other_trace<DIM, DEG, T, DIM>(fld, Nn, links[a], a, id, sII, fo);
-      T sum = T(0);
+      T sum = ft[a];
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) sum += (fv[b] + fo[b]) * Jl[a][b];
-      facc += half_sign<DIM, DEG, T>(a, id) * sum;
+      for (int b = 0; b < DIM; ++b) sum += fo[b] * Jl[a][b];
+      facc += half_sign<DIM, DEG, T>(a, id, hw) * sum;
     }
   }
   // coarse sides: the values of round 0 are in sJ since the barrier above
@@ -503,7 +506,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     coarse_more_rounds<DIM, DEG, T, 1>(mv, br, coarse, id, sII + 2 * N * N, T(-1), sJ, &facc, dpoint);
   }
   if (active) {
-    const T dv = (acc + facc * mv.tab[S::T_IWEND]) * ij;
+    const T dv = (acc + facc) * ij;
     if (HELM)
       epi(idx, scale * (ident * pv * inv_gm1<T>() - alpha * dv));
     else

@@ -637,6 +637,16 @@ int build_mesh(dg_mesh* m) {
       background(d, m->X[((size_t)(dim - 1) * K + c) * nc + q], &rhob[idx], &pb[idx]);
     }
   }
+  // the metric entries outside the diagonal and the last row vanish on cells affine in the
+  // horizontal coordinates up to the rounding of the derivative of constant node coordinates;
+  // the FP64 implicit passes skip them where they are below 1e-13 of their row's diagonal
+  bool aff = geo_z;
+  for (int64_t i = 0; aff && i < m->Nn; ++i)
+    for (int a = 0; a < dim - 1; ++a)
+      for (int b = 0; b < dim; ++b)
+        if (b != a && std::fabs(Ja[(size_t)(a * dim + b) * m->Nn + i]) >
+                          1e-13 * std::fabs(Ja[(size_t)(a * dim + a) * m->Nn + i]))
+          aff = false;
   // face-node normals from the minus (fine) side
   std::vector<double> fn((size_t)dim * nf * NF), fsj((size_t)nf * NF);
   for (int f = 0; f < nf; ++f) {
@@ -859,6 +869,7 @@ int build_mesh(dg_mesh* m) {
     v.cell_link = v.cell_level + K;
     for (int a = 0; a < 3; ++a) v.hb[a] = (decltype(v.gravity))(a < dim ? 0.5 * hb[a] : 0.0);
     v.geo_z = geo_z ? 1 : 0;
+    v.aff = aff ? 1 : 0;
     v.cell_zeta0 = base + o_zeta0;
     v.bg_tab = base + o_bg;
     v.bg_z0 = (decltype(v.gravity))zlo;

@@ -88,6 +88,16 @@ __host__ __device__ constexpr int coarse_buffer() {
   return Shape<DIM, DEG>::CPB * NV * coarse_points<DIM, DEG>() * kCoarseSlots;
 }
 
+// Whether the pass uses metric entry J d xi^a / d x_b: all of them in
+// general; on meshes whose cells are affine in the horizontal coordinates
+// (aff: MeshView::aff, or the metric recomputed from the heights) only the
+// diagonal and the last row (xi depends on x alone, eta on y alone).  The
+// test is warp-uniform, and a compile-time true for those entries.
+template <int DIM>
+__device__ __forceinline__ bool metric_used(int a, int b, bool aff) {
+  return a == b || a == DIM - 1 || !aff;
+}
+
 // One cell batch of the mesh's active partition: cells [c0, c1) (at most
 // CPB), coarse-side entries [e0, e1) (MeshView::bdesc, one 16-byte load).
 struct BatchRange {
@@ -289,6 +299,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
                                                 const BatchCache<DIM, DEG, T>* bc = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC;
+  const bool aff = GZ || mv.aff;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
   const int c = br.c0 + lc;
   const bool active = c < br.c1;
@@ -319,7 +330,7 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) Jl[a][b] = (mv.Ja + (a * DIM + b) * Nn)[idx];
+        for (int b = 0; b < DIM; ++b) Jl[a][b] = metric_used<DIM>(a, b, aff) ? (mv.Ja + (a * DIM + b) * Nn)[idx] : T(0);
       scale = mv.invJ[idx] * (h ? h[idx] : T(1));
     }
     // neighbour traces: issued before the barrier, their latency overlaps it
@@ -365,7 +376,8 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
       if ((links[a] & 3) >= 2) continue;
       const T jmp = half_sign<DIM, DEG, T>(a, id, hw) * (po[a] - pv);
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) facc[b] += jmp * Jl[a][b];
+      for (int b = 0; b < DIM; ++b)
+        if (metric_used<DIM>(a, b, aff)) facc[b] += jmp * Jl[a][b];
     }
   }
   // coarse sides: the values of round 0 are in sJ since the barrier above
@@ -378,7 +390,8 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
     for (int b = 0; b < DIM; ++b) {
       T s = facc[b];
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) s += Jl[a][b] * dp[a];
+      for (int a = 0; a < DIM; ++a)
+        if (metric_used<DIM>(a, b, aff)) s += Jl[a][b] * dp[a];
       (g + b * Nn)[idx] = s * scale;
     }
   }
@@ -400,6 +413,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
                                                const BatchCache<DIM, DEG, T>* bc = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
+  const bool aff = GZ || mv.aff;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
   const int c = br.c0 + lc;
   const bool active = c < br.c1;
@@ -432,12 +446,13 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) Jl[a][b] = (mv.Ja + (a * DIM + b) * Nn)[idx];
+        for (int b = 0; b < DIM; ++b) Jl[a][b] = metric_used<DIM>(a, b, aff) ? (mv.Ja + (a * DIM + b) * Nn)[idx] : T(0);
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         T s = T(0);
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) s += Jl[a][b] * fv[b];
+        for (int b = 0; b < DIM; ++b)
+          if (metric_used<DIM>(a, b, aff)) s += Jl[a][b] * fv[b];
         ft[a] = s;
       }
     }
@@ -461,7 +476,8 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       for (int a = 0; a < DIM; ++a) {
         T s = T(0);
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) s += Jl[a][b] * fv[b];
+        for (int b = 0; b < DIM; ++b)
+          if (metric_used<DIM>(a, b, aff)) s += Jl[a][b] * fv[b];
         ft[a] = s;
       }
     }
@@ -496,7 +512,8 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       other_trace<DIM, DEG, T, DIM>(fld, Nn, links[a], a, id, sII, fo);
       T sum = ft[a];
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) sum += fo[b] * Jl[a][b];
+      for (int b = 0; b < DIM; ++b)
+        if (metric_used<DIM>(a, b, aff)) sum += fo[b] * Jl[a][b];
       facc += half_sign<DIM, DEG, T>(a, id, hw) * sum;
     }
   }

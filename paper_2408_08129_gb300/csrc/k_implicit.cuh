@@ -85,7 +85,7 @@ __host__ __device__ constexpr int coarse_points() {
 }
 template <int DIM, int DEG, int NV>
 __host__ __device__ constexpr int coarse_buffer() {
-  return Shape<DIM, DEG>::CPB * NV * coarse_points<DIM, DEG>() * kCoarseSlots;
+  return Shape<DIM, DEG>::CPB * kCoarseSlots * NV * (coarse_points<DIM, DEG>() + Shape<DIM, DEG>::NF);
 }
 
 // Whether the pass uses metric entry J d xi^a / d x_b: all of them in
@@ -115,14 +115,18 @@ __device__ __forceinline__ BatchRange batch_range(const MeshView<T>& mv, int64_t
 // coarse_fill writes the NV face values of each point to buf[v * EPR + k]
 // (k = the point's place in the round), reading global memory only, so that
 // round 0 is filled before the batch's first barrier and its loads overlap
-// the batch's own; after a barrier, coarse_sum adds at each node on a coarse
-// face of the round sum_s sum_q sign * It * value to acc[0..NV).
+// the batch's own; after that barrier, coarse_reduce forms at every node kt
+// of every coarse face of the round sum_s sum_q sign * It * value, one
+// thread per (face, node) (out[v * OPR + slot * NF + kt], all lanes busy);
+// after one more barrier, coarse_sum adds each node's values to acc[0..NV).
+// The buffer (coarse_buffer) holds the points' values, then the sums.
 template <int DIM, int DEG>
 struct CoarseRounds {
   using S = Shape<DIM, DEG>;
   static constexpr int NP = coarse_points<DIM, DEG>();
   static constexpr int FPR = S::CPB * kCoarseSlots;  // slots per round (the buffer's capacity)
   static constexpr int EPR = FPR * NP;               // points per round
+  static constexpr int OPR = FPR * S::NF;            // coarse face nodes per round
   __device__ __forceinline__ static int rounds(int e0, int e1) { return ((e1 - e0) / NP + FPR - 1) / FPR; }
 };
 
@@ -167,16 +171,43 @@ __device__ __forceinline__ void coarse_fill(const MeshView<T>& mv, const BatchRa
   }
 }
 
-// coarse = MeshView::cell_coarse of this thread's cell (0 if none or inactive)
+// The sums of round r at the coarse face nodes (whole block, after the
+// barrier that follows the round's fill; another barrier must follow before
+// coarse_sum reads them)
 template <int DIM, int DEG, typename T, int NV>
-__device__ __forceinline__ void coarse_sum(int coarse, int r, const int* id, const T* sIt, T sign, const T* buf,
-                                           T* acc) {
+__device__ __forceinline__ void coarse_reduce(const BatchRange& br, int r, const T* sIt, T sign, T* buf) {
   using R = CoarseRounds<DIM, DEG>;
   using S = Shape<DIM, DEG>;
   constexpr int NF = S::NF;
+  const int left = (br.e1 - br.e0) / R::NP - r * R::FPR;
+  const int nsl = left < R::FPR ? left : R::FPR;
+  T* out = buf + NV * R::EPR;
+  for (int t = threadIdx.x; t < nsl * NF; t += blockDim.x) {
+    const int sl = t / NF, kt = t % NF;
+    const T* b = buf + sl * R::NP;
+    T o[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) o[v] = T(0);
+    for (int sp = 0; sp < S::NSUB; ++sp)
+      for (int q = 0; q < NF; ++q) {
+        const T wgt = sign * coarse_weight<DIM, DEG, T>(sIt, sp, kt, q);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) o[v] += wgt * b[v * R::EPR + sp * NF + q];
+      }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * R::OPR + t] = o[v];
+  }
+}
+
+// coarse = MeshView::cell_coarse of this thread's cell (0 if none or inactive)
+template <int DIM, int DEG, typename T, int NV>
+__device__ __forceinline__ void coarse_sum(int coarse, int r, const int* id, const T* buf, T* acc) {
+  using R = CoarseRounds<DIM, DEG>;
+  constexpr int NF = Shape<DIM, DEG>::NF;
   const unsigned cmask = (unsigned)coarse & 0xffu;
   if (!cmask) return;
   const int slot0 = coarse >> 8;
+  const T* out = buf + NV * R::EPR;
 #pragma unroll
   for (int lf = 0; lf < 2 * DIM; ++lf) {
     if (!((cmask >> lf) & 1u)) continue;
@@ -184,14 +215,9 @@ __device__ __forceinline__ void coarse_sum(int coarse, int r, const int* id, con
     if (id[a] != ((lf & 1) ? DEG : 0)) continue;
     const int slot = slot0 + __popc(cmask & ((1u << lf) - 1u));
     if (slot / R::FPR != r) continue;
-    const int kt = tangential_index<DIM, DEG>(a, id);
-    const T* b = buf + (slot % R::FPR) * R::NP;
-    for (int sp = 0; sp < S::NSUB; ++sp)
-      for (int q = 0; q < NF; ++q) {
-        const T wgt = sign * coarse_weight<DIM, DEG, T>(sIt, sp, kt, q);
+    const int o = (slot % R::FPR) * NF + tangential_index<DIM, DEG>(a, id);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += wgt * b[v * R::EPR + sp * NF + q];
-      }
+    for (int v = 0; v < NV; ++v) acc[v] += out[v * R::OPR + o];
   }
 }
 
@@ -206,7 +232,9 @@ __device__ __forceinline__ void coarse_more_rounds(const MeshView<T>& mv, const 
     __syncthreads();
     coarse_fill<DIM, DEG, T, NV>(mv, br, r, buf, point);
     __syncthreads();
-    coarse_sum<DIM, DEG, T, NV>(coarse, r, id, sIt, sign, buf, acc);
+    coarse_reduce<DIM, DEG, T, NV>(br, r, sIt, sign, buf);
+    __syncthreads();
+    coarse_sum<DIM, DEG, T, NV>(coarse, r, id, buf, acc);
   }
 }
 
@@ -349,6 +377,8 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   };
   if (has_coarse) coarse_fill<DIM, DEG, T, DIM>(mv, br, 0, sJ, gpoint, bc);
   __syncthreads();
+  // round 0's sums at the coarse face nodes, while the cells' own work follows
+  if (has_coarse) coarse_reduce<DIM, DEG, T, DIM>(br, 0, sII + 2 * N * N, T(1), sJ);
   T facc[DIM], dp[DIM];  // facc: the face terms, already divided by w_end
 #pragma unroll
   for (int b = 0; b < DIM; ++b) facc[b] = dp[b] = T(0);
@@ -380,9 +410,10 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
         if (metric_used<DIM>(a, b, aff)) facc[b] += jmp * Jl[a][b];
     }
   }
-  // coarse sides: the values of round 0 are in sJ since the barrier above
+  // coarse sides: round 0's sums are in sJ after this barrier
   if (has_coarse) {
-    coarse_sum<DIM, DEG, T, DIM>(coarse, 0, id, sII + 2 * N * N, T(1), sJ, facc);
+    __syncthreads();
+    coarse_sum<DIM, DEG, T, DIM>(coarse, 0, id, sJ, facc);
     coarse_more_rounds<DIM, DEG, T, DIM>(mv, br, coarse, id, sII + 2 * N * N, T(1), sJ, facc, gpoint);
   }
   if (active) {
@@ -488,6 +519,8 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     for (int a = 0; a < DIM; ++a) sF[(a * CPB + lc) * NC + i] = ft[a];
   }
   __syncthreads();
+  // round 0's sums at the coarse face nodes, while the cells' own work follows
+  if (has_coarse) coarse_reduce<DIM, DEG, T, 1>(br, 0, sII + 2 * N * N, T(-1), sJ);
   T acc = T(0);
   if (active) {
 #pragma unroll
@@ -517,9 +550,10 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       facc += half_sign<DIM, DEG, T>(a, id, hw) * sum;
     }
   }
-  // coarse sides: the values of round 0 are in sJ since the barrier above
+  // coarse sides: round 0's sums are in sJ after this barrier
   if (has_coarse) {
-    coarse_sum<DIM, DEG, T, 1>(coarse, 0, id, sII + 2 * N * N, T(-1), sJ, &facc);
+    __syncthreads();
+    coarse_sum<DIM, DEG, T, 1>(coarse, 0, id, sJ, &facc);
     coarse_more_rounds<DIM, DEG, T, 1>(mv, br, coarse, id, sII + 2 * N * N, T(-1), sJ, &facc, dpoint);
   }
   if (active) {

@@ -240,7 +240,7 @@ typedef struct {
                                         /* (0 where a form was not timed)       */
   int n_batches[2];                     /* cell batches of the implicit passes: */
                                         /* [0] CPB consecutive cells each, [1]  */
-                                        /* cost-balanced (0 if not built)       */
+                                        /* balanced (0 if not built)            */
   int solver_partition[2];              /* autotuned partition per precision    */
   float solver_ms_balanced[2][3];       /* the timed solves on partition 1      */
 } dg_mesh_info;
@@ -254,11 +254,13 @@ int dg_mesh_destroy(dg_mesh* mesh);
 int dg_mesh_get_info(const dg_mesh* mesh, dg_mesh_info* info);
 /* Choose the cell partition of the implicit cell passes (gradient,
  * divergence, Helmholtz, the persistent solves): 0 = batches of CPB
- * consecutive cells (CPB = 256 / nodes per cell), 1 = cost-balanced batches of
- * at most CPB consecutive cells, as many as a persistent solve has CTAs, cut
- * so that the largest batch's work (nodes plus 2:1 face points) is as small as
- * the greedy cut allows (built only when the mesh has no more uniform batches
- * than that).  The operators' values do not depend on it (each node's
+ * consecutive cells (CPB = 256 / nodes per cell), 1 = balanced for the
+ * persistent solves (two CTAs per SM): on meshes with no more uniform batches
+ * than CTAs, cost-balanced batches of at most CPB consecutive cells, one per
+ * CTA, cut so that the largest batch's work (nodes plus 2:1 face points) is as
+ * small as the greedy cut allows; on larger meshes, the uniform batches in an
+ * order that gives every CTA about the same work.  The operators' values do
+ * not depend on it (each node's
  * arithmetic is the same); only the launch shapes do.  Steps use the
  * partition chosen last, here or by the autotuner: the first step with
  * krylov = DG_KRYLOV_AUTO times both (dg_mesh_info.solver_partition).

@@ -216,8 +216,9 @@ struct dg_mesh {
   mutable int tuned_form[2] = {-1, -1};
   mutable float tuned_ms[2][3] = {{0, 0, 0}, {0, 0, 0}};
   // cell partitions of the implicit passes: [0] CPB consecutive cells per
-  // batch, [1] (small meshes) cost-balanced batches, one per CTA of a
-  // persistent solve; the autotuner picks one per precision
+  // batch, [1] balanced for the persistent solves (small meshes: cost-balanced
+  // batches, one per CTA; large meshes: the uniform batches in a cost-balanced
+  // order over the CTAs); the autotuner picks one per precision
   dg::CellPartition part[2];
   int n_parts = 0;
   int active_part = 0;

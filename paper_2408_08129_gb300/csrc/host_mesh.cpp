@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <queue>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -244,9 +245,37 @@ std::vector<int> balanced_batches(const std::vector<double>& cost, int cpb, int 
   return starts;
 }
 
+// An order of nb batches of costs bcost for G CTAs that take positions r,
+// r + G, r + 2G, ...: the batches, largest first, each go to the least
+// loaded CTA with a position left (order[position] = batch).
+std::vector<int> balanced_order(const std::vector<double>& bcost, int G) {
+  const int nb = (int)bcost.size();
+  std::vector<int> idx(nb);
+  for (int b = 0; b < nb; ++b) idx[b] = b;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return bcost[a] > bcost[b]; });
+  using Slot = std::pair<double, int>;  // (load, CTA)
+  std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+  std::vector<int> cap(G), used(G, 0);
+  for (int r = 0; r < G; ++r) {
+    cap[r] = nb / G + (r < nb % G ? 1 : 0);
+    if (cap[r] > 0) heap.push({0.0, r});
+  }
+  std::vector<int> order(nb, -1);
+  for (int b : idx) {
+    const Slot sl = heap.top();
+    heap.pop();
+    const int r = sl.second;
+    order[r + used[r] * G] = b;
+    if (++used[r] < cap[r]) heap.push({sl.first + bcost[b], r});
+  }
+  return order;
+}
+
 // One partition of the cells into batches (bstart: K-terminated starts) with
-// its coarse-side entry lists, uploaded to a device block of its own.
-int build_partition(dg_mesh* m, const CoarseLists& cl, const std::vector<int>& bstart, CellPartition& P) {
+// its coarse-side entry lists, uploaded to a device block of its own; order
+// (optional) places batch order[p] at position p.
+int build_partition(dg_mesh* m, const CoarseLists& cl, const std::vector<int>& bstart, CellPartition& P,
+                    const std::vector<int>* order = nullptr) {
   const int dim = cl.dim, np = cl.np;
   const int nbat = (int)bstart.size() - 1;
   std::vector<int4> bdesc(nbat);
@@ -284,6 +313,11 @@ int build_partition(dg_mesh* m, const CoarseLists& cl, const std::vector<int>& b
       const size_t g = (size_t)cl.off[bstart[b]] * np + (size_t)(e - bdesc[b].z);
       for (int d = 0; d < dim; ++d) w[(size_t)d * E + e] = cl.w[g * dim + d];
     }
+  if (order) {
+    std::vector<int4> placed(nbat);
+    for (int p = 0; p < nbat; ++p) placed[p] = bdesc[(*order)[p]];
+    bdesc.swap(placed);
+  }
   const size_t n_int = 4 * (size_t)nbat + (size_t)m->K + 2 * E;
   DG_CUDA(cudaMalloc(&P.d_int, n_int * sizeof(int) + 64));
   DG_CUDA(cudaMalloc(&P.d_f64, w.size() * sizeof(double) + 64));
@@ -763,11 +797,15 @@ int build_mesh(dg_mesh* m) {
   cl.cmask = cell_cmask;
   cl.off.assign(K + 1, 0);
   cl.cost.assign(K, (double)nc);
+  // work per cell in units of a node's work (about 14 d FP64 operations per node and pass pair):
+  // a coarse-side point costs its interpolation (NF (1 + d) operations) and its share of the
+  // sums at the coarse face nodes (NF more); a fine-side face node its interpolation
+  const double k_coarse = (2.0 + dim) * NF / (14.0 * dim), k_fine = (1.0 + dim) * NF / (14.0 * dim);
   for (int64_t c = 0; c < K; ++c) {
     cl.off[c] = (int)(cl.node.size() / np_c);
     for (int lf = 0; lf < 2 * dim; ++lf) {
       const int link = cell_link[(size_t)c * 2 * dim + lf];
-      if ((link & 3) == 1) cl.cost[c] += NF;
+      if ((link & 3) == 1) cl.cost[c] += k_fine * NF;
       if (!((cell_cmask[c] >> lf) & 1)) continue;
       const int f = cell_face[c * 2 * dim + lf] >> 2;
       for (int j = 0; j < np_c; ++j) {
@@ -775,7 +813,7 @@ int build_mesh(dg_mesh* m) {
         cl.node.push_back(fnode_m[t]);
         for (int b = 0; b < dim; ++b) cl.w.push_back(0.5 * fsj[t] * fn[(size_t)b * nf * NF + t] * iwend);
       }
-      cl.cost[c] += np_c;
+      cl.cost[c] += k_coarse * np_c;
     }
   }
   cl.off[K] = (int)(cl.node.size() / np_c);
@@ -886,12 +924,23 @@ int build_mesh(dg_mesh* m) {
     int rc = build_partition(m, cl, bstart, m->part[0]);
     if (rc != DG_OK) return rc;
     m->n_parts = 1;
-    // cost-balanced batches, one per CTA of a persistent solve (two per SM), where the uniform
-    // batches do not already fill them
+    // balanced partition for the persistent solves (two CTAs per SM, CTA r taking batches r,
+    // r + G, ...): where the uniform batches do not fill the CTAs, cost-balanced batches, one per
+    // CTA; where there are more batches than CTAs, the uniform batches ordered so that every
+    // CTA's share of the work is about the same (largest first to the least loaded CTA)
     const int target = 2 * m->ctx->sm_count;
-    if ((int64_t)bstart.size() - 1 <= target && K > (int64_t)bstart.size() - 1) {
+    const int64_t nbu = (int64_t)bstart.size() - 1;
+    if (nbu <= target && K > nbu) {
       bstart = balanced_batches(cl.cost, cpb, (int)std::min<int64_t>(target, K));
       rc = build_partition(m, cl, bstart, m->part[1]);
+      if (rc != DG_OK) return rc;
+      m->n_parts = 2;
+    } else if (nbu > target) {
+      std::vector<double> bcost(nbu, 0.0);
+      for (int64_t b = 0; b < nbu; ++b)
+        for (int c = bstart[b]; c < bstart[b + 1]; ++c) bcost[b] += cl.cost[c];
+      const std::vector<int> order = balanced_order(bcost, target);
+      rc = build_partition(m, cl, bstart, m->part[1], &order);
       if (rc != DG_OK) return rc;
       m->n_parts = 2;
     }

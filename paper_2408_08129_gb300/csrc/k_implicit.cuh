@@ -199,6 +199,44 @@ __device__ __forceinline__ void coarse_reduce(const BatchRange& br, int r, const
   }
 }
 
+// The same sums formed by each coarse face node's own thread, straight from
+// the round's point values (no barrier after the fill's; the lanes of the
+// other nodes idle meanwhile): the cheaper form in FP32, where the passes are
+// bound by latency rather than by arithmetic.
+template <int DIM, int DEG, typename T, int NV>
+__device__ __forceinline__ void coarse_sum_direct(int coarse, int r, const int* id, const T* sIt, T sign,
+                                                  const T* buf, T* acc) {
+  using R = CoarseRounds<DIM, DEG>;
+  using S = Shape<DIM, DEG>;
+  constexpr int NF = S::NF;
+  const unsigned cmask = (unsigned)coarse & 0xffu;
+  if (!cmask) return;
+  const int slot0 = coarse >> 8;
+#pragma unroll
+  for (int lf = 0; lf < 2 * DIM; ++lf) {
+    if (!((cmask >> lf) & 1u)) continue;
+    const int a = lf >> 1;
+    if (id[a] != ((lf & 1) ? DEG : 0)) continue;
+    const int slot = slot0 + __popc(cmask & ((1u << lf) - 1u));
+    if (slot / R::FPR != r) continue;
+    const int kt = tangential_index<DIM, DEG>(a, id);
+    const T* b = buf + (slot % R::FPR) * R::NP;
+    for (int sp = 0; sp < S::NSUB; ++sp)
+      for (int q = 0; q < NF; ++q) {
+        const T wgt = sign * coarse_weight<DIM, DEG, T>(sIt, sp, kt, q);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += wgt * b[v * R::EPR + sp * NF + q];
+      }
+  }
+}
+
+// Which form a pass takes: the dense reduction in FP64 (arithmetic-bound),
+// the direct sums in FP32 (latency-bound)
+template <typename T>
+__host__ __device__ constexpr bool coarse_dense() {
+  return sizeof(T) == 8;
+}
+
 // coarse = MeshView::cell_coarse of this thread's cell (0 if none or inactive)
 template <int DIM, int DEG, typename T, int NV>
 __device__ __forceinline__ void coarse_sum(int coarse, int r, const int* id, const T* buf, T* acc) {
@@ -232,9 +270,13 @@ __device__ __forceinline__ void coarse_more_rounds(const MeshView<T>& mv, const 
     __syncthreads();
     coarse_fill<DIM, DEG, T, NV>(mv, br, r, buf, point);
     __syncthreads();
-    coarse_reduce<DIM, DEG, T, NV>(br, r, sIt, sign, buf);
-    __syncthreads();
-    coarse_sum<DIM, DEG, T, NV>(coarse, r, id, buf, acc);
+    if (coarse_dense<T>()) {
+      coarse_reduce<DIM, DEG, T, NV>(br, r, sIt, sign, buf);
+      __syncthreads();
+      coarse_sum<DIM, DEG, T, NV>(coarse, r, id, buf, acc);
+    } else {
+      coarse_sum_direct<DIM, DEG, T, NV>(coarse, r, id, sIt, sign, buf, acc);
+    }
   }
 }
 
@@ -377,8 +419,8 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
   };
   if (has_coarse) coarse_fill<DIM, DEG, T, DIM>(mv, br, 0, sJ, gpoint, bc);
   __syncthreads();
-  // round 0's sums at the coarse face nodes, while the cells' own work follows
-  if (has_coarse) coarse_reduce<DIM, DEG, T, DIM>(br, 0, sII + 2 * N * N, T(1), sJ);
+  // FP64: round 0's sums at the coarse face nodes, while the cells' own work follows
+  if (coarse_dense<T>() && has_coarse) coarse_reduce<DIM, DEG, T, DIM>(br, 0, sII + 2 * N * N, T(1), sJ);
   T facc[DIM], dp[DIM];  // facc: the face terms, already divided by w_end
 #pragma unroll
   for (int b = 0; b < DIM; ++b) facc[b] = dp[b] = T(0);
@@ -410,10 +452,14 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
         if (metric_used<DIM>(a, b, aff)) facc[b] += jmp * Jl[a][b];
     }
   }
-  // coarse sides: round 0's sums are in sJ after this barrier
+  // coarse sides (FP64: round 0's sums are in sJ after this barrier)
   if (has_coarse) {
-    __syncthreads();
-    coarse_sum<DIM, DEG, T, DIM>(coarse, 0, id, sJ, facc);
+    if (coarse_dense<T>()) {
+      __syncthreads();
+      coarse_sum<DIM, DEG, T, DIM>(coarse, 0, id, sJ, facc);
+    } else {
+      coarse_sum_direct<DIM, DEG, T, DIM>(coarse, 0, id, sII + 2 * N * N, T(1), sJ, facc);
+    }
     coarse_more_rounds<DIM, DEG, T, DIM>(mv, br, coarse, id, sII + 2 * N * N, T(1), sJ, facc, gpoint);
   }
   if (active) {
@@ -519,8 +565,8 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     for (int a = 0; a < DIM; ++a) sF[(a * CPB + lc) * NC + i] = ft[a];
   }
   __syncthreads();
-  // round 0's sums at the coarse face nodes, while the cells' own work follows
-  if (has_coarse) coarse_reduce<DIM, DEG, T, 1>(br, 0, sII + 2 * N * N, T(-1), sJ);
+  // FP64: round 0's sums at the coarse face nodes, while the cells' own work follows
+  if (coarse_dense<T>() && has_coarse) coarse_reduce<DIM, DEG, T, 1>(br, 0, sII + 2 * N * N, T(-1), sJ);
   T acc = T(0);
   if (active) {
 #pragma unroll
@@ -550,10 +596,14 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       facc += half_sign<DIM, DEG, T>(a, id, hw) * sum;
     }
   }
-  // coarse sides: round 0's sums are in sJ after this barrier
+  // coarse sides (FP64: round 0's sums are in sJ after this barrier)
   if (has_coarse) {
-    __syncthreads();
-    coarse_sum<DIM, DEG, T, 1>(coarse, 0, id, sJ, &facc);
+    if (coarse_dense<T>()) {
+      __syncthreads();
+      coarse_sum<DIM, DEG, T, 1>(coarse, 0, id, sJ, &facc);
+    } else {
+      coarse_sum_direct<DIM, DEG, T, 1>(coarse, 0, id, sII + 2 * N * N, T(-1), sJ, &facc);
+    }
     coarse_more_rounds<DIM, DEG, T, 1>(mv, br, coarse, id, sII + 2 * N * N, T(-1), sJ, &facc, dpoint);
   }
   if (active) {

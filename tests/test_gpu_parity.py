@@ -147,17 +147,21 @@ def test_implicit_operators_fp32(dg, ctx, name, dim, r):
 
 
 @pytest.mark.parametrize("name,dim,r", [("tiny", 2, 1), ("tiny", 2, 4), ("tiny", 3, 2), ("tiny", 3, 3),
-                                        ("bubble2d", 2, 2), ("hill2d", 2, 4)])
+                                        ("bubble2d", 2, 2), ("hill2d", 2, 4), ("hill3d", 3, 3)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_cell_partitions_give_identical_operators(dg, ctx, name, dim, r, precision):
-    """The cost-balanced cell partition (batches of at most CPB consecutive cells, one per CTA of a
-    persistent solve; one cell each on the tiny meshes) changes only which CTA computes which cell:
-    gradient, divergence and Helmholtz operator are bitwise equal to those on the uniform batches,
-    and match the oracle."""
+    """The balanced cell partition (on small meshes, cost-balanced batches of at most CPB consecutive
+    cells, one per CTA of a persistent solve, one cell each on the tiny meshes; on hill3d, the
+    uniform batches in a cost-balanced order over the CTAs) changes only which CTA computes which
+    cell: gradient, divergence and Helmholtz operator are bitwise equal to those on the uniform
+    batches, and match the oracle."""
     case = _case(name, dim, r)
     ref = DG(case)
     mesh = dg.Mesh(ctx, case)
-    assert mesh.n_batches[1] > mesh.n_batches[0] > 0
+    if name == "hill3d":
+        assert mesh.n_batches[1] == mesh.n_batches[0] > 0
+    else:
+        assert mesh.n_batches[1] > mesh.n_batches[0] > 0
     rng = np.random.default_rng(13)
     shp = (ref.mesh.K, ref.mesh.nc)
     p0 = 100.0 * rng.standard_normal(shp)

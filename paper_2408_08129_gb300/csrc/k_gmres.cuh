@@ -288,6 +288,46 @@ struct NoFin {
   __device__ __forceinline__ void operator()() const {}
 };
 
+// The Chebyshev step's update fused into the divergence pass: x += d,
+// r -= A d, d = c1 d + c2 r, and the stop test's sum of (r / beta)^2.  pre()
+// loads the node's d, r and x (or the cycle's correction) before the pass's
+// first barrier, so that their latency is off the pass's critical path.
+template <typename TK>
+struct ChebStepEpi {
+  TK* d;
+  TK* r;
+  TK* dx;
+  double* x;
+  bool fold;  // TK = float: the correction is summed in dx, added to x once per cycle
+  TK c1, c2;
+  bool want;  // this step's residual is tested
+  float ibeta;
+  float* racc;
+  TK di, ri0, dxi;
+  double xi;
+  __device__ __forceinline__ void pre(int64_t i) {
+    di = d[i];
+    ri0 = r[i];
+    if (fold)
+      dxi = dx[i];
+    else
+      xi = x[i];
+  }
+  __device__ __forceinline__ void operator()(int64_t i, TK ad) {
+    const TK ri = ri0 - ad;
+    r[i] = ri;
+    if (fold)
+      dx[i] = dxi + di;
+    else
+      x[i] = xi + (double)di;
+    d[i] = c1 * di + c2 * ri;
+    if (want) {
+      const float rs = (float)ri * ibeta;  // FP32: no FP64 instruction for the stop test
+      *racc += rs * rs;
+    }
+  }
+};
+
 // scale * (ident p/(gamma-1) - alpha div(h grad p)) (two phases, two grid
 // barriers; the face terms are computed inside the cell passes), handed node
 // by node to epi(i, value); fin() runs on every thread of every CTA after its
@@ -1488,20 +1528,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       const double rho1 = sc[0];
       const TK c1 = (TK)sc[1], c2 = (TK)sc[2];
       float racc = 0.0f;
-      auto epi = [&](int64_t i, TK ad) {
-        const TK di = d[i];
-        const TK ri = r[i] - ad;
-        r[i] = ri;
-        if (fold)
-          dx[i] += di;
-        else
-          a.x[i] += (double)di;
-        d[i] = c1 * di + c2 * ri;
-        if (want) {
-          const float rs = (float)ri * ibeta;  // FP32: no FP64 instruction for the stop test
-          racc += rs * rs;
-        }
-      };
+      ChebStepEpi<TK> epi{d, r, dx, a.x, fold, c1, c2, want, ibeta, &racc};
       const unsigned long long td0 = cta_clock ? PhaseClock::now() : 0ull;
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
         div_cell_batch<DIM, DEG, TK, true>(

@@ -477,6 +477,15 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
 
 // ---------------------------------------------------------------- divergence
 
+// An epilogue with a pre(i) method has it called for the node before the
+// divergence pass's first barrier (to load the operands of its update early)
+template <class E>
+__device__ __forceinline__ auto epi_pre(E& e, int64_t i, int) -> decltype(e.pre(i), void()) {
+  e.pre(i);
+}
+template <class E>
+__device__ __forceinline__ void epi_pre(E&, int64_t, long) {}
+
 // Cells of one batch: epi(idx, v) receives v = HELM ? scale * (ident p/(gamma-1) - alpha div) : div
 // at every node of the batch (the caller stores it, or fuses further pointwise work).
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
@@ -516,6 +525,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
       coarse = mv.cell_coarse[c];
     }
     if (HELM) pv = p[idx];
+    epi_pre(epi, idx, 0);
     if (GZ) {
       sz[lc * NC + i] = mv.zdev[idx];
     } else {

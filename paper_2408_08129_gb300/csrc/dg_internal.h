@@ -80,9 +80,9 @@ struct MeshView {
   const int* cell_level;  // [n_cells] refinement level
   T hb[3];                // half width of a base cell per axis
   int geo_z;              // 1 if every cell is affine in x (and y)
-  int aff;                // 1 if, moreover, the stored metric entries outside the diagonal and the
-                          // last row are negligible (below 1e-13 of the diagonal): the FP64 implicit
-                          // passes skip them
+  int aff;                // 1 if every cell is affine in x (and y) to rounding: the metric entries
+                          // outside the diagonal and the last row are stored as zeros and the
+                          // implicit passes skip them
   const T* cell_zeta0;    // [n_cells] computational height of the cell's lower face
   // Hydrostatic background as a function of height: cubic Hermite data at
   // bg_m + 1 equally spaced heights from bg_z0 (spacing 1/bg_idz), four values

@@ -612,6 +612,7 @@ int build_mesh(dg_mesh* m) {
   // follow from these heights)
   std::vector<double> zdev(m->Nn);
   bool geo_z = true;
+  bool aff = true;  // affine in x (and y) to rounding
   for (int64_t c = 0; c < K; ++c) {
     const int l = m->level[c];
     for (int q = 0; q < nc; ++q) {
@@ -621,6 +622,7 @@ int build_mesh(dg_mesh* m) {
         const double xv = m->X[((size_t)a * K + c) * nc + q];
         if (a < dim - 1) {
           if (std::fabs(xv - comp) > 1e-9 * d.extent[a]) geo_z = false;
+          if (std::fabs(xv - comp) > 1e-12 * d.extent[a]) aff = false;
         } else {
           zdev[(size_t)c * nc + q] = xv - comp;
         }
@@ -671,16 +673,15 @@ int build_mesh(dg_mesh* m) {
       background(d, m->X[((size_t)(dim - 1) * K + c) * nc + q], &rhob[idx], &pb[idx]);
     }
   }
-  // the metric entries outside the diagonal and the last row vanish on cells affine in the
-  // horizontal coordinates up to the rounding of the derivative of constant node coordinates;
-  // the FP64 implicit passes skip them where they are below 1e-13 of their row's diagonal
-  bool aff = geo_z;
-  for (int64_t i = 0; aff && i < m->Nn; ++i)
-    for (int a = 0; a < dim - 1; ++a)
-      for (int b = 0; b < dim; ++b)
-        if (b != a && std::fabs(Ja[(size_t)(a * dim + b) * m->Nn + i]) >
-                          1e-13 * std::fabs(Ja[(size_t)(a * dim + a) * m->Nn + i]))
-          aff = false;
+  // on cells affine in the horizontal coordinates (node positions within 1e-12 of the domain
+  // size of the affine ones) the metric entries outside the diagonal and the last row vanish;
+  // what the differentiation leaves there is rounding of the derivative of constant
+  // coordinates, set to zero here, and the implicit passes skip those entries
+  if (aff)
+    for (int64_t i = 0; i < m->Nn; ++i)
+      for (int a = 0; a < dim - 1; ++a)
+        for (int b = 0; b < dim; ++b)
+          if (b != a) Ja[(size_t)(a * dim + b) * m->Nn + i] = 0.0;
   // face-node normals from the minus (fine) side
   std::vector<double> fn((size_t)dim * nf * NF), fsj((size_t)nf * NF);
   for (int f = 0; f < nf; ++f) {

@@ -362,14 +362,17 @@ __device__ __forceinline__ void batch_cache_fill(const MeshView<T>& mv, const Ba
 // sII holds the interpolation tables I (2 N^2) followed by It (2 N^2); sJ is
 // the coarse-pass buffer (coarse_buffer<DIM, DEG, DIM>() elements).
 // GZ: metric terms from the heights (metric_from_z), staged in sz (CPB*NC).
-template <int DIM, int DEG, typename T, bool GZ = false>
+// AFF: the mesh is known to be horizontally affine (MeshView::aff) at compile
+// time, so the vanishing metric entries drop out of the code; otherwise the
+// runtime flag only predicates them off.
+template <int DIM, int DEG, typename T, bool GZ = false, bool AFF = false>
 __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
                                                 const T* __restrict__ h, T* __restrict__ g, const BatchRange& br,
                                                 T* sp, T* sJ, const T* sD, const T* sII, T* sz = nullptr,
                                                 const BatchCache<DIM, DEG, T>* bc = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC;
-  const bool aff = GZ || mv.aff;
+  const bool aff = GZ || AFF || mv.aff;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
   const int c = br.c0 + lc;
   const bool active = c < br.c1;
@@ -491,7 +494,8 @@ __device__ __forceinline__ void epi_pre(E&, int64_t, long) {}
 // Called by a whole block with blockDim >= CPB*NC; contains __syncthreads.
 // sF: DIM * CPB * NC elements; sJ: coarse-pass buffer (coarse_buffer<DIM, DEG, 1>() elements).
 // GZ: metric terms from the heights (metric_from_z with sD), staged in sz (CPB*NC).
-template <int DIM, int DEG, typename T, bool HELM, class Epi, bool GZ = false>
+// AFF: as for the gradient.
+template <int DIM, int DEG, typename T, bool HELM, class Epi, bool GZ = false, bool AFF = false>
 __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
                                                const T* __restrict__ p, T alpha, T scale, T ident, Epi& epi,
                                                const BatchRange& br, T* sF, T* sJ, const T* sDw, const T* sII,
@@ -499,7 +503,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
                                                const BatchCache<DIM, DEG, T>* bc = nullptr) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
-  const bool aff = GZ || mv.aff;
+  const bool aff = GZ || AFF || mv.aff;
   const int lc = threadIdx.x / NC, i = threadIdx.x % NC;
   const int c = br.c0 + lc;
   const bool active = c < br.c1;
@@ -641,7 +645,7 @@ struct StoreOut {
   __device__ __forceinline__ void operator()(int64_t i, T v) const { out[i] = v; }
 };
 
-template <int DIM, int DEG, typename T, bool GZ>
+template <int DIM, int DEG, typename T, bool GZ, bool AFF>
 __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_cell_kernel(MeshView<T> mv,
                                                                            const T* __restrict__ p,
                                                                            const T* __restrict__ h,
@@ -658,10 +662,10 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_cell_kernel(Mes
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sD[q] = mv.tab[S::T_D + q];
   for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
   __syncthreads();  // the fine-side traces read the interpolation tables before the batch's first barrier
-  grad_cell_batch<DIM, DEG, T, GZ>(mv, p, h, g, batch_range(mv, blockIdx.x), sp, sJ, sD, sII, sz);
+  grad_cell_batch<DIM, DEG, T, GZ, AFF>(mv, p, h, g, batch_range(mv, blockIdx.x), sp, sJ, sD, sII, sz);
 }
 
-template <int DIM, int DEG, typename T, bool HELM, bool GZ>
+template <int DIM, int DEG, typename T, bool HELM, bool GZ, bool AFF>
 __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(MeshView<T> mv,
                                                                           const T* __restrict__ f,
                                                                           const T* __restrict__ p, T alpha,
@@ -683,8 +687,8 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_cell_kernel(Mesh
   for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
   __syncthreads();
   StoreOut<T> epi{out};
-  div_cell_batch<DIM, DEG, T, HELM, StoreOut<T>, GZ>(mv, f, p, alpha, T(1), T(1), epi, batch_range(mv, blockIdx.x),
-                                                     sF, sJ, sDw, sII, sz, sD);
+  div_cell_batch<DIM, DEG, T, HELM, StoreOut<T>, GZ, AFF>(mv, f, p, alpha, T(1), T(1), epi,
+                                                          batch_range(mv, blockIdx.x), sF, sJ, sDw, sII, sz, sD);
 }
 
 }  // namespace dg

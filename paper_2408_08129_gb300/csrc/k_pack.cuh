@@ -59,8 +59,11 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) grad_pack_kernel(con
   for (int q = threadIdx.x; q < N * N; q += blockDim.x) sD[q] = mv.tab[S::T_D + q];
   for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
   __syncthreads();  // the fine-side traces read the interpolation tables before the batch's first barrier
-  grad_cell_batch<DIM, DEG, T, false>(mv, P.in[j], P.aux[j], P.out[j], batch_range(mv, blockIdx.x - P.start[j]), sp,
-                                      sJ, sD, sII);
+  const BatchRange br = batch_range(mv, blockIdx.x - P.start[j]);
+  if (mv.aff)  // block-uniform: the horizontally affine form without the vanishing metric terms
+    grad_cell_batch<DIM, DEG, T, false, true>(mv, P.in[j], P.aux[j], P.out[j], br, sp, sJ, sD, sII);
+  else
+    grad_cell_batch<DIM, DEG, T, false, false>(mv, P.in[j], P.aux[j], P.out[j], br, sp, sJ, sD, sII);
 }
 
 template <int DIM, int DEG, typename T>
@@ -77,8 +80,13 @@ __global__ void __launch_bounds__(Shape<DIM, DEG>::THREADS) div_pack_kernel(cons
   for (int q = threadIdx.x; q < 4 * N * N; q += blockDim.x) sII[q] = mv.tab[S::T_I + q];
   __syncthreads();
   StoreOut<T> epi{P.out[j]};
-  div_cell_batch<DIM, DEG, T, false, StoreOut<T>, false>(mv, P.in[j], nullptr, T(0), T(1), T(1), epi,
-                                                        batch_range(mv, blockIdx.x - P.start[j]), sF, sJ, sDw, sII);
+  const BatchRange br = batch_range(mv, blockIdx.x - P.start[j]);
+  if (mv.aff)
+    div_cell_batch<DIM, DEG, T, false, StoreOut<T>, false, true>(mv, P.in[j], nullptr, T(0), T(1), T(1), epi, br,
+                                                                 sF, sJ, sDw, sII);
+  else
+    div_cell_batch<DIM, DEG, T, false, StoreOut<T>, false, false>(mv, P.in[j], nullptr, T(0), T(1), T(1), epi, br,
+                                                                  sF, sJ, sDw, sII);
 }
 
 }  // namespace dg

@@ -58,9 +58,11 @@ int run_grad(const dg_mesh* m, const T* p, const T* h, T* g, cudaStream_t s, con
   const unsigned nb = (unsigned)mv.nbat;
   count_launches(m->ctx, 1);
   if (std::is_same<T, float>::value && mv.geo_z)
-    grad_cell_kernel<DIM, DEG, T, true><<<nb, S::THREADS, 0, s>>>(mv, p, h, g, skip);
+    grad_cell_kernel<DIM, DEG, T, true, true><<<nb, S::THREADS, 0, s>>>(mv, p, h, g, skip);
+  else if (mv.aff)
+    grad_cell_kernel<DIM, DEG, T, false, true><<<nb, S::THREADS, 0, s>>>(mv, p, h, g, skip);
   else
-    grad_cell_kernel<DIM, DEG, T, false><<<nb, S::THREADS, 0, s>>>(mv, p, h, g, skip);
+    grad_cell_kernel<DIM, DEG, T, false, false><<<nb, S::THREADS, 0, s>>>(mv, p, h, g, skip);
   return check_launch("gradient launch");
 }
 
@@ -71,9 +73,11 @@ int run_div(const dg_mesh* m, const T* f, const T* p, T alpha, T* out, cudaStrea
   const unsigned nb = (unsigned)mv.nbat;
   count_launches(m->ctx, 1);
   if (std::is_same<T, float>::value && mv.geo_z)
-    div_cell_kernel<DIM, DEG, T, HELM, true><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
+    div_cell_kernel<DIM, DEG, T, HELM, true, true><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
+  else if (mv.aff)
+    div_cell_kernel<DIM, DEG, T, HELM, false, true><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
   else
-    div_cell_kernel<DIM, DEG, T, HELM, false><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
+    div_cell_kernel<DIM, DEG, T, HELM, false, false><<<nb, S::THREADS, 0, s>>>(mv, f, p, alpha, out, skip);
   return check_launch("divergence launch");
 }
 

@@ -1260,7 +1260,9 @@ __device__ __noinline__ void gmres_fallback(const GmresPArgs<TK>& a, Sync& sg, u
   gmres_body<DIM, DEG, TK, Sync>(a, sg, smem_raw, record);
 }
 
-template <int DIM, int DEG, typename TK, class Sync>
+// AFF: the mesh is horizontally affine (MeshView::aff), known at compile time
+// for the Chebyshev steps' passes (the vanishing metric terms drop out).
+template <int DIM, int DEG, typename TK, class Sync, bool AFF = false>
 __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, unsigned char* smem_raw, bool record) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N;
@@ -1505,7 +1507,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         for (int i = threadIdx.x; i < G; i += blockDim.x) pv += ((const float*)a.partial)[i];
       const unsigned long long tg0 = cta_clock ? PhaseClock::now() : 0ull;
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-        grad_cell_batch<DIM, DEG, TK>(a.mvk, d, a.hk, gvk,
+        grad_cell_batch<DIM, DEG, TK, false, AFF>(a.mvk, d, a.hk, gvk,
                                       one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt),
                                       scellk, sJk, sDk, sIIk, nullptr, bc);
       if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks) cta_clock[sg.rank] += PhaseClock::now() - tg0;
@@ -1531,7 +1533,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       ChebStepEpi<TK> epi{d, r, dx, a.x, fold, c1, c2, want, ibeta, &racc};
       const unsigned long long td0 = cta_clock ? PhaseClock::now() : 0ull;
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-        div_cell_batch<DIM, DEG, TK, true>(
+        div_cell_batch<DIM, DEG, TK, true, ChebStepEpi<TK>, false, AFF>(
             a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi,
             one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt), scellk, sJk, sDwk,
             sIIk, nullptr, nullptr, bc);
@@ -1573,8 +1575,9 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
 }
 
 // One kernel per method (each allocates registers for its own body only; the
-// Chebyshev one holds the GMRES body too, its fallback).
-template <int DIM, int DEG, typename TK, int METHOD>
+// Chebyshev one holds the GMRES body too, its fallback); AFF: the Chebyshev
+// form for horizontally affine meshes.
+template <int DIM, int DEG, typename TK, int METHOD, bool AFF = false>
 __global__ void __launch_bounds__(256, 2) gmres_persistent_kernel(GmresPArgs<TK> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GridSync sg;
@@ -1583,7 +1586,7 @@ __global__ void __launch_bounds__(256, 2) gmres_persistent_kernel(GmresPArgs<TK>
   else if (METHOD == 2)
     gmres_cgs2_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
   else if (METHOD == 3)
-    cheb_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
+    cheb_body<DIM, DEG, TK, GridSync, AFF>(a, sg, smem_raw, blockIdx.x == 0);
   else
     gmres_body<DIM, DEG, TK, GridSync>(a, sg, smem_raw, blockIdx.x == 0);
 }

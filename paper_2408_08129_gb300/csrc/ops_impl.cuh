@@ -170,9 +170,11 @@ int run_gmres(const dg_mesh* m, const double* h64, const TK* hk, const double* b
   a.method = method;
   if (method == 1 && restart < 2) return fail(DG_EINVAL, "CG needs restart >= 2 (three work vectors)");
   if (method == 3 && !lmax) return fail(DG_EINVAL, "Chebyshev needs a bound buffer");
+  const bool aff = a.mvk.aff && a.mv64.aff;
   void (*kern)(GmresPArgs<TK>) = method == 1   ? gmres_persistent_kernel<DIM, DEG, TK, 1>
                                  : method == 2 ? gmres_persistent_kernel<DIM, DEG, TK, 2>
-                                 : method == 3 ? gmres_persistent_kernel<DIM, DEG, TK, 3>
+                                 : method == 3 ? (aff ? gmres_persistent_kernel<DIM, DEG, TK, 3, true>
+                                                      : gmres_persistent_kernel<DIM, DEG, TK, 3>)
                                                : gmres_persistent_kernel<DIM, DEG, TK, 0>;
   const size_t smem = gmres_smem_bytes<DIM, DEG, TK>(restart);
   if (smem > 48 * 1024) {

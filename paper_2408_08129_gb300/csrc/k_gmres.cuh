@@ -332,31 +332,32 @@ struct ChebStepEpi {
 // barriers; the face terms are computed inside the cell passes), handed node
 // by node to epi(i, value); fin() runs on every thread of every CTA after its
 // last divergence batch, before the closing barrier.
-template <int DIM, int DEG, typename T, class Sync, class Epi, class Fin>
+template <int DIM, int DEG, typename T, class Sync, class Epi, class Fin, bool AFF = false>
 __device__ __forceinline__ void pmatvec_epi(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p,
                                             T scale, Epi& epi, Fin& fin, T* gv, Sync& sg, T* scell, T* sJ,
                                             const T* sD, const T* sDw, const T* sII, PhaseClock& pc) {
   const int64_t nb = mv.nbat;
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-    grad_cell_batch<DIM, DEG, T>(mv, p, h, gv, batch_range(mv, bt), scell, sJ, sD, sII);
+    grad_cell_batch<DIM, DEG, T, false, AFF>(mv, p, h, gv, batch_range(mv, bt), scell, sJ, sD, sII);
   sg.sync();
   pc.mark(PH_GRAD_CELL);
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-    div_cell_batch<DIM, DEG, T, true, Epi>(mv, gv, p, alpha, scale, ident, epi, batch_range(mv, bt), scell, sJ,
-                                           sDw, sII);
+    div_cell_batch<DIM, DEG, T, true, Epi, false, AFF>(mv, gv, p, alpha, scale, ident, epi, batch_range(mv, bt),
+                                                        scell, sJ, sDw, sII);
   fin();
   sg.sync();
   pc.mark(PH_DIV_CELL);
 }
 
 // out = scale * (ident p/(gamma-1) - alpha div(h grad p))
-template <int DIM, int DEG, typename T, class Sync>
+template <int DIM, int DEG, typename T, class Sync, bool AFF = false>
 __device__ __forceinline__ void pmatvec(const MeshView<T>& mv, const T* h, T alpha, T ident, const T* p, T scale,
                                         T* out, T* gv, Sync& sg, T* scell, T* sJ, const T* sD, const T* sDw,
                                         const T* sII, PhaseClock& pc) {
   StoreEpi<T> epi{out};
   NoFin fin;
-  pmatvec_epi<DIM, DEG, T, Sync>(mv, h, alpha, ident, p, scale, epi, fin, gv, sg, scell, sJ, sD, sDw, sII, pc);
+  pmatvec_epi<DIM, DEG, T, Sync, StoreEpi<T>, NoFin, AFF>(mv, h, alpha, ident, p, scale, epi, fin, gv, sg, scell, sJ, sD,
+                                                          sDw, sII, pc);
 }
 
 // partial[j*C + c] = sum over chunk c of v_j . w for j < nv, where v_j = Q_j for
@@ -1370,7 +1371,8 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         const double t = block_sum(nacc, sred);
         if (threadIdx.x == 0) a.partial[sg.rank] = t;
       };
-      pmatvec_epi<DIM, DEG, TK, Sync>(a.mvk, a.hk, (TK)a.alpha, TK(1), pin, (TK)inv, epi, fin, gvk, sg, scellk, sJk,
+      pmatvec_epi<DIM, DEG, TK, Sync, decltype(epi), decltype(fin), AFF>(a.mvk, a.hk, (TK)a.alpha, TK(1), pin, (TK)inv, epi,
+                                                                        fin, gvk, sg, scellk, sJk,
                                       sDk, sDwk, sIIk, pc);
       {
         const double s1 = gather_sum();
@@ -1414,7 +1416,7 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
   bool converged = false, diverged = false;
   while (!sg.failed()) {
     // FP64 residual r = b - A x; d = r / theta in the same pass
-    pmatvec<DIM, DEG, double, Sync>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.gv, sg, scell64, sJ64, sD64,
+    pmatvec<DIM, DEG, double, Sync, AFF>(a.mv64, a.h64, a.alpha, 1.0, a.x, 1.0, a.w64, a.gv, sg, scell64, sJ64, sD64,
                                     sDw64, sII64, pc);
     acc = 0.0;
     const TK ith = (TK)itheta;

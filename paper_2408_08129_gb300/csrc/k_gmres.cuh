@@ -100,6 +100,10 @@ struct GridSync {
   int rank, size;
   __device__ GridSync() : grid(cooperative_groups::this_grid()), rank(blockIdx.x), size(gridDim.x) {}
   __device__ __forceinline__ void sync() { grid.sync(); }
+  // the barrier in two halves (whole block each): arrive after this CTA's
+  // writes of the phase, wait before its first read of other CTAs' writes
+  __device__ __forceinline__ unsigned int arrive() { return grid.barrier_arrive(); }
+  __device__ __forceinline__ void wait(unsigned int token) { grid.barrier_wait(std::move(token)); }
   __device__ __forceinline__ bool failed() const { return false; }
 };
 
@@ -140,6 +144,12 @@ struct SubSync {
     }
     __syncthreads();
   }
+  // no split form: arrive is the whole barrier
+  __device__ __forceinline__ unsigned int arrive() {
+    sync();
+    return 0u;
+  }
+  __device__ __forceinline__ void wait(unsigned int) {}
   __device__ __forceinline__ bool failed() const { return *(volatile int*)sfail != 0; }
 };
 
@@ -1471,6 +1481,8 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
     double rho = rho0;
     const int64_t nb = a.mvk.nbat;
     bool have_prev = false;  // residual partials of the previous step are waiting in a.partial
+    unsigned int token = 0u;  // the split grid barrier's arrival
+    bool pending = false;
     // with at most one cell batch per CTA (the usual case on meshes that fit the launch), the
     // CTA's batch range is read once for the whole cycle (kept in shared memory: registers are
     // the scarce resource of this loop)
@@ -1500,20 +1512,30 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
         sc[1] = rho1 * rho;
         sc[2] = rho1 * two_idelta;
       }
-      // gradient pass of A d_k; the previous step's residual norm is summed meanwhile
-      // (its partial loads are issued before the pass, the sum after it)
-      // The stop test needs the residual norm to a few digits only: its sums run in FP32 on
-      // the residual scaled by 1/beta (no FP64 shuffle trees on the step's critical path)
-      float pv = 0.0f;
-      if (have_prev)
-        for (int i = threadIdx.x; i < G; i += blockDim.x) pv += ((const float*)a.partial)[i];
-      const unsigned long long tg0 = cta_clock ? PhaseClock::now() : 0ull;
+      // gradient pass of A d_k; the grid barrier after the previous divergence pass is split:
+      // this CTA arrived after its own writes, and waits inside the pass once its own loads
+      // are in flight (pending: an arrival not yet waited for; the same in every CTA)
+      unsigned long long tg0 = 0ull;
+      auto wait_div = [&]() {
+        if (pending) sg.wait(token);
+        pending = false;
+        if (cta_clock) tg0 = PhaseClock::now();
+      };
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-        grad_cell_batch<DIM, DEG, TK, false, AFF>(a.mvk, d, a.hk, gvk,
-                                      one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt),
-                                      scellk, sJk, sDk, sIIk, nullptr, bc);
-      if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks) cta_clock[sg.rank] += PhaseClock::now() - tg0;
+        grad_cell_batch<DIM, DEG, TK, false, AFF, decltype(wait_div)>(
+            a.mvk, d, a.hk, gvk, one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt),
+            scellk, sJk, sDk, sIIk, nullptr, bc, wait_div);
+      if (pending) {  // a CTA without a batch still meets the barrier
+        sg.wait(token);
+        pending = false;
+      }
+      if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks && tg0) cta_clock[sg.rank] += PhaseClock::now() - tg0;
       if (have_prev) {
+        // the previous step's residual norm.  The stop test needs it to a few digits only: its
+        // sums run in FP32 on the residual scaled by 1/beta (no FP64 shuffle trees on the step's
+        // critical path)
+        float pv = 0.0f;
+        for (int i = threadIdx.x; i < G; i += blockDim.x) pv += ((const float*)a.partial)[i];
         const float rn2 = block_allsum_f(pv, sred);  // (||r|| / beta)^2
         pc.mark(PH_UPDATE);
         if (!(rn2 <= kGrowth2) || (cycle_its > cycle_cap && rn2 > floor2)) {  // growth, stall or NaN: bound too low
@@ -1524,7 +1546,8 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       } else if (total >= a.max_iters || sg.failed()) {
         break;
       }
-      sg.sync();
+      token = sg.arrive();
+      pending = true;
       pc.mark(PH_GRAD_CELL);
       // whether the next step tests this step's residual (the same in every CTA)
       const bool want = cycle_its + 1 >= kskip;
@@ -1533,24 +1556,38 @@ __device__ __forceinline__ void cheb_body(const GmresPArgs<TK>& a, Sync& sg, uns
       const TK c1 = (TK)sc[1], c2 = (TK)sc[2];
       float racc = 0.0f;
       ChebStepEpi<TK> epi{d, r, dx, a.x, fold, c1, c2, want, ibeta, &racc};
-      const unsigned long long td0 = cta_clock ? PhaseClock::now() : 0ull;
+      unsigned long long td0 = 0ull;
+      auto wait_grad = [&]() {
+        if (pending) sg.wait(token);
+        pending = false;
+        if (cta_clock) td0 = PhaseClock::now();
+      };
       for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-        div_cell_batch<DIM, DEG, TK, true, ChebStepEpi<TK>, false, AFF>(
+        div_cell_batch<DIM, DEG, TK, true, ChebStepEpi<TK>, false, AFF, decltype(wait_grad)>(
             a.mvk, gvk, d, (TK)a.alpha, TK(1), TK(1), epi,
             one ? BatchRange{s_mine.x, s_mine.y, s_mine.z, s_mine.w} : batch_range(a.mvk, bt), scellk, sJk, sDwk,
-            sIIk, nullptr, nullptr, bc);
-      if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks)
+            sIIk, nullptr, nullptr, bc, wait_grad);
+      if (pending) {
+        sg.wait(token);
+        pending = false;
+      }
+      if (cta_clock && threadIdx.x == 0 && sg.rank < kCtaClocks && td0)
         cta_clock[kCtaClocks + sg.rank] += PhaseClock::now() - td0;
       if (want) {
         const float t = block_sum_f(racc, sred);
         if (threadIdx.x == 0) ((float*)a.partial)[sg.rank] = t;  // FP32 partials for the stop test
       }
-      sg.sync();
+      token = sg.arrive();
+      pending = true;
       pc.mark(PH_DIV_CELL);
       rho = rho1;
       ++total;
       ++cycle_its;
       have_prev = want;
+    }
+    if (pending) {  // (the loop leaves only after a gradient pass, which has waited)
+      sg.wait(token);
+      pending = false;
     }
     if (fold)
       for (int64_t i = tid; i < n; i += gstride) a.x[i] += (double)dx[i];

@@ -280,6 +280,14 @@ __device__ __forceinline__ void coarse_more_rounds(const MeshView<T>& mv, const 
   }
 }
 
+// A pass's hook between the loads of the batch's own data and the first read
+// of data other CTAs wrote in the previous phase: the persistent solves wait
+// there for the grid barrier they arrived at (a split barrier), so that the
+// own loads' latency overlaps the barrier's; called by the whole block.
+struct NoWait {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // Face links of node id of cell c, one per axis: the link of the cell face the
 // node lies on along that axis (MeshView::cell_link), or kind 3 (no face
 // term) where the node is interior along the axis.  Loaded early so that
@@ -365,11 +373,11 @@ __device__ __forceinline__ void batch_cache_fill(const MeshView<T>& mv, const Ba
 // AFF: the mesh is known to be horizontally affine (MeshView::aff) at compile
 // time, so the vanishing metric entries drop out of the code; otherwise the
 // runtime flag only predicates them off.
-template <int DIM, int DEG, typename T, bool GZ = false, bool AFF = false>
+template <int DIM, int DEG, typename T, bool GZ = false, bool AFF = false, class Wait = NoWait>
 __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* __restrict__ p,
                                                 const T* __restrict__ h, T* __restrict__ g, const BatchRange& br,
                                                 T* sp, T* sJ, const T* sD, const T* sII, T* sz = nullptr,
-                                                const BatchCache<DIM, DEG, T>* bc = nullptr) {
+                                                const BatchCache<DIM, DEG, T>* bc = nullptr, Wait wait = Wait{}) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC;
   const bool aff = GZ || AFF || mv.aff;
@@ -406,7 +414,10 @@ __device__ __forceinline__ void grad_cell_batch(const MeshView<T>& mv, const T* 
         for (int b = 0; b < DIM; ++b) Jl[a][b] = metric_used<DIM>(a, b, aff) ? (mv.Ja + (a * DIM + b) * Nn)[idx] : T(0);
       scale = mv.invJ[idx] * (h ? h[idx] : T(1));
     }
-    // neighbour traces: issued before the barrier, their latency overlaps it
+  }
+  wait();  // from here on, other CTAs' values of p
+  if (active) {
+    // neighbour traces: issued before the batch's barrier, their latency overlaps it
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
       if ((links[a] & 3) < 2) other_trace<DIM, DEG, T, 1>(p, 0, links[a], a, id, sII, &po[a]);
@@ -495,12 +506,13 @@ __device__ __forceinline__ void epi_pre(E&, int64_t, long) {}
 // sF: DIM * CPB * NC elements; sJ: coarse-pass buffer (coarse_buffer<DIM, DEG, 1>() elements).
 // GZ: metric terms from the heights (metric_from_z with sD), staged in sz (CPB*NC).
 // AFF: as for the gradient.
-template <int DIM, int DEG, typename T, bool HELM, class Epi, bool GZ = false, bool AFF = false>
+template <int DIM, int DEG, typename T, bool HELM, class Epi, bool GZ = false, bool AFF = false,
+          class Wait = NoWait>
 __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* __restrict__ fld,
                                                const T* __restrict__ p, T alpha, T scale, T ident, Epi& epi,
                                                const BatchRange& br, T* sF, T* sJ, const T* sDw, const T* sII,
                                                T* sz = nullptr, const T* sD = nullptr,
-                                               const BatchCache<DIM, DEG, T>* bc = nullptr) {
+                                               const BatchCache<DIM, DEG, T>* bc = nullptr, Wait wait = Wait{}) {
   using S = Shape<DIM, DEG>;
   constexpr int N = S::N, NC = S::NC, CPB = S::CPB;
   const bool aff = GZ || AFF || mv.aff;
@@ -558,6 +570,7 @@ __device__ __forceinline__ void div_cell_batch(const MeshView<T>& mv, const T* _
     for (int b = 0; b < DIM; ++b) sum += ((fld + b * Nn)[node] + fc[b]) * w[b];
     val[0] = sum;
   };
+  wait();  // from here on, other CTAs' values of f
   if (has_coarse) coarse_fill<DIM, DEG, T, 1>(mv, br, 0, sJ, dpoint, bc);
   if (GZ) {
     __syncthreads();

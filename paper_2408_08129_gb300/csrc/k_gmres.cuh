@@ -339,7 +339,7 @@ struct ChebStepEpi {
 };
 
 // scale * (ident p/(gamma-1) - alpha div(h grad p)) (two phases, two grid
-// barriers; the face terms are computed inside the cell passes), handed node
+// barriers, the first split; the face terms are computed inside the cell passes), handed node
 // by node to epi(i, value); fin() runs on every thread of every CTA after its
 // last divergence batch, before the closing barrier.
 template <int DIM, int DEG, typename T, class Sync, class Epi, class Fin, bool AFF = false>
@@ -349,11 +349,19 @@ __device__ __forceinline__ void pmatvec_epi(const MeshView<T>& mv, const T* h, T
   const int64_t nb = mv.nbat;
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
     grad_cell_batch<DIM, DEG, T, false, AFF>(mv, p, h, gv, batch_range(mv, bt), scell, sJ, sD, sII);
-  sg.sync();
+  // split barrier: arrive after the gradient's writes, wait inside the divergence pass once its
+  // own loads are in flight
+  unsigned int token = sg.arrive();
+  bool pending = true;
   pc.mark(PH_GRAD_CELL);
+  auto wait = [&]() {
+    if (pending) sg.wait(token);
+    pending = false;
+  };
   for (int64_t bt = sg.rank; bt < nb; bt += sg.size)
-    div_cell_batch<DIM, DEG, T, true, Epi, false, AFF>(mv, gv, p, alpha, scale, ident, epi, batch_range(mv, bt),
-                                                        scell, sJ, sDw, sII);
+    div_cell_batch<DIM, DEG, T, true, Epi, false, AFF, decltype(wait)>(
+        mv, gv, p, alpha, scale, ident, epi, batch_range(mv, bt), scell, sJ, sDw, sII, nullptr, nullptr, nullptr, wait);
+  if (pending) sg.wait(token);  // a CTA without a batch still meets the barrier
   fin();
   sg.sync();
   pc.mark(PH_DIV_CELL);

@@ -18,6 +18,7 @@
 #include <unordered_set>
 
 #include "dg_internal.h"
+#include "partition.h"
 
 namespace dg {
 
@@ -209,67 +210,6 @@ struct CoarseLists {
   std::vector<double> w;    // [faces * np * dim] 1/2 |N| n of each point
   std::vector<double> cost; // [K] work of the cell's implicit passes (nodes + face points)
 };
-
-// Batches of at most cpb consecutive cells, at most nb of them, with the
-// largest batch cost as small as the greedy cut allows (bisection on the cost
-// bound: each batch is closed when the next cell would exceed it or cpb is reached).
-std::vector<int> balanced_batches(const std::vector<double>& cost, int cpb, int nb) {
-  const int64_t K = (int64_t)cost.size();
-  auto cut = [&](double bound, std::vector<int>* starts) {
-    int count = 0, cells = 0;
-    double acc = 0.0;
-    for (int64_t c = 0; c < K; ++c) {
-      if (cells > 0 && (cells == cpb || acc + cost[c] > bound)) {
-        cells = 0;
-        acc = 0.0;
-      }
-      if (cells == 0) {
-        ++count;
-        if (starts) starts->push_back((int)c);
-      }
-      acc += cost[c];
-      ++cells;
-    }
-    return count;
-  };
-  double lo = *std::max_element(cost.begin(), cost.end()), hi = 0.0;
-  for (double x : cost) hi += x;
-  for (int it = 0; it < 60 && hi - lo > 1e-9 * hi; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (cut(mid, nullptr) <= nb) hi = mid;
-    else lo = mid;
-  }
-  std::vector<int> starts;
-  cut(hi, &starts);
-  starts.push_back((int)K);
-  return starts;
-}
-
-// An order of nb batches of costs bcost for G CTAs that take positions r,
-// r + G, r + 2G, ...: the batches, largest first, each go to the least
-// loaded CTA with a position left (order[position] = batch).
-std::vector<int> balanced_order(const std::vector<double>& bcost, int G) {
-  const int nb = (int)bcost.size();
-  std::vector<int> idx(nb);
-  for (int b = 0; b < nb; ++b) idx[b] = b;
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return bcost[a] > bcost[b]; });
-  using Slot = std::pair<double, int>;  // (load, CTA)
-  std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
-  std::vector<int> cap(G), used(G, 0);
-  for (int r = 0; r < G; ++r) {
-    cap[r] = nb / G + (r < nb % G ? 1 : 0);
-    if (cap[r] > 0) heap.push({0.0, r});
-  }
-  std::vector<int> order(nb, -1);
-  for (int b : idx) {
-    const Slot sl = heap.top();
-    heap.pop();
-    const int r = sl.second;
-    order[r + used[r] * G] = b;
-    if (++used[r] < cap[r]) heap.push({sl.first + bcost[b], r});
-  }
-  return order;
-}
 
 // One partition of the cells into batches (bstart: K-terminated starts) with
 // its coarse-side entry lists, uploaded to a device block of its own; order

@@ -71,13 +71,15 @@ __device__ __forceinline__ T coarse_weight(const T* sIt, int s, int kt, int q) {
 // node on a fine subface interpolates the coarse neighbour's face polynomial
 // at its point.  Both sides evaluate the same expression on the same values,
 // so the face value is the same on both sides.  The coarse side of a 2:1 face
-// needs the face values at all fine points of its subfaces: the threads of the
-// coarse cell compute them once, one fine point each, into shared memory
-// (coarse_pass below), and each coarse face node then sums them through It.
+// needs the face values at all fine points of its subfaces: the batch's
+// threads compute them once, one fine point each, into shared memory (the
+// batch's coarse-side entry list, coarse_fill below), and the sums through It
+// at the coarse face nodes follow (coarse_reduce / coarse_sum).
 
 // Number of fine points behind one coarse face, and the shared-memory buffer
-// (elements) the coarse pass needs per cell batch for NV values per point:
-// kCoarseSlots coarse faces per cell are handled in one round.
+// (elements) the coarse sides need per cell batch for NV values per point and
+// per coarse face node: kCoarseSlots coarse faces per cell of the batch fit
+// one round.
 constexpr int kCoarseSlots = 2;
 template <int DIM, int DEG>
 __host__ __device__ constexpr int coarse_points() {

@@ -119,9 +119,10 @@ int dg_profile_read_gmres_phases(dg_ctx* ctx, double* ns);
 /* Per-CTA clocks of the Chebyshev solves while profiling was on at level 2: for CTA i <
  * max_ctas (at most 512) of the persistent launch, the nanoseconds of its own
  * gradient passes (grad_ns[i]) and divergence passes (div_ns[i]), summed over
- * the steps and solves, before the grid barriers; coarse[i] = 1 if its cell
- * batch holds the coarse side of a 2:1 face.  Host arrays.  Synchronises the
- * device. */
+ * the steps and solves, each from the end of the CTA's wait for the grid
+ * barrier inside the pass to the pass's end (the barriers' own time is not
+ * counted); coarse[i] = 1 if its cell batch holds the coarse side of a 2:1
+ * face.  Host arrays.  Synchronises the device. */
 int dg_profile_read_cta_passes(dg_ctx* ctx, double* grad_ns, double* div_ns, int* coarse, int max_ctas);
 /* Self-test of the library's own FP64 math on the device (no counterpart in
  * the paper): op 0 writes y[i] = 1/sqrt(x[i]) as computed by the Newton
